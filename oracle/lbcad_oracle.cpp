@@ -1,0 +1,653 @@
+// lbcad_oracle.cpp -- plain FP64 CPU oracle for one hybrid lattice-Boltzmann step
+// of a 3D active cholesteric droplet (Carenza, Gonnella & Negro, arXiv:2011.00287).
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, import or call
+// this file; it is used by tests/, by __graft_entry__.smoke() (as the checker) and by
+// bench.py's cpu_baseline / --impl reference legs.  It shares no code, header, table
+// or constant with the CUDA library: the D3Q19 table, the stencils, the free energy,
+// the stresses and the seeded initial state are written out again here.
+//
+// Everything is a plain loop in double precision, one stage after another, in the
+// order of the paper's model (Sec. 2, Eqs. 1-5) and scheme (Sec. 3, Eqs. 6-11):
+//   1. stencils on Q and psi                 (Sec. 3: finite differences for the order parameters)
+//   2. molecular field H = -dF/dQ            (Eq. 2, Eq. 5)
+//   3. chemical potential mu = dF/dphi       (Eq. 1, Eq. 5)
+//   4. stress sigma = passive + active       (Eq. 3, Eq. 4)
+//   5. body force F = div sigma              (Eq. 3, Eq. 10 read as the whole div sigma)
+//   6. BGK collision with Guo forcing, then streaming  (Eqs. 6-8; Eq. 7 read as BGK + Guo)
+//   7. Beris-Edwards update of Q (Eq. 2) and Cahn-Hilliard update of psi (Eq. 1),
+//      first-order upwind advection (Sec. 3), Euler or Heun predictor-corrector.
+// Readings of the parts the paper leaves open (all are parameters):
+//   * lattice D3Q19 (the paper used D3Q15); whole sigma enters as a body force, f^eq has
+//     no stress term (G_i = 0 in Eq. 11).
+//   * psi = phi - 1 in [-1, 1] (phi0 = 2, phi_cr = 1), so the bulk term of Eq. 5 is
+//     -a psi^2/2 + b psi^4/4 with a = b; chi(phi) = chi0 + chis*phi with phi = 1 + psi.
+//   * H is the symmetric traceless part of -dF/dQ and multiplies Gamma_Q (Eq. 2 read as
+//     dQ/dt = ... + Gamma_Q H).
+//   * the elastic energy (K/2)[(div Q)^2 + (curl Q + 2 q0 Q)^2] is used in its
+//     one-constant form (K/2)(dQ)^2 + 2 K q0 Q:(curl Q) + 2 K q0^2 Q:Q, which differs by a
+//     null Lagrangian: identical H, it only fixes the elastic stress Pi.
+//   * active stress -zeta phi_c Q with phi_c = (1 + psi)/2 (Eq. 4 restricted to the droplet).
+//   * stencils: isotropic D3Q19 gradient and Laplacian (radius 1); Hessian of psi from
+//     the three-point and the four-corner differences.
+//   * isotropic pressure P0 = psi*mu - f, f the free-energy density of Eq. 5.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+extern "C" {
+
+// Parameters of Eqs. 1-11 (plus the readings above).  Layout mirrored by oracle/oracle.py.
+typedef struct {
+  double tau, rho0;
+  double A0, chi0, chis, K, q0, gammaQ, xi;
+  double a, b, kphi, M, W, zeta;
+  double R, cx, cy, cz;   // droplet radius and centre
+  double S0, noise;       // initial scalar order inside the droplet and noise amplitude
+  int integrator;         // 0 = Euler, 1 = Heun predictor-corrector (Sec. 3)
+  int coupling;           // 0 = advect with u(t-1), 1 = advect with u(t) of this step
+} orc_params;
+
+}  // extern "C"
+
+namespace {
+
+const int NQ = 19;
+// D3Q19 velocity set: rest, six faces, twelve edges.
+const int CV[NQ][3] = {
+    {0, 0, 0},
+    {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+    {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0},
+    {1, 0, 1}, {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+    {0, 1, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+double wgt(int i) {
+  int s = CV[i][0] * CV[i][0] + CV[i][1] * CV[i][1] + CV[i][2] * CV[i][2];
+  if (s == 0) return 1.0 / 3.0;
+  if (s == 1) return 1.0 / 18.0;
+  return 1.0 / 36.0;
+}
+
+struct Box {
+  int nx, ny, nz;
+  long n() const { return (long)nx * ny * nz; }
+  long at(int x, int y, int z) const {
+    x %= nx; if (x < 0) x += nx;
+    y %= ny; if (y < 0) y += ny;
+    z %= nz; if (z < 0) z += nz;
+    return x + (long)nx * (y + (long)ny * z);
+  }
+};
+
+typedef double M3[3][3];
+
+int eps(int a, int b, int c) {
+  if (a == b || b == c || a == c) return 0;
+  // even permutations of (0,1,2)
+  if ((a == 0 && b == 1 && c == 2) || (a == 1 && b == 2 && c == 0) || (a == 2 && b == 0 && c == 1)) return 1;
+  return -1;
+}
+
+// The five stored components are xx, xy, xz, yy, yz; zz = -xx - yy.
+void q_full(const double* q5, long N, long s, M3 Q) {
+  double xx = q5[0 * N + s], xy = q5[1 * N + s], xz = q5[2 * N + s];
+  double yy = q5[3 * N + s], yz = q5[4 * N + s];
+  Q[0][0] = xx; Q[0][1] = xy; Q[0][2] = xz;
+  Q[1][0] = xy; Q[1][1] = yy; Q[1][2] = yz;
+  Q[2][0] = xz; Q[2][1] = yz; Q[2][2] = -xx - yy;
+}
+
+void q_store(const M3 Q, double* q5, long N, long s) {
+  q5[0 * N + s] = Q[0][0]; q5[1 * N + s] = Q[0][1]; q5[2 * N + s] = Q[0][2];
+  q5[3 * N + s] = Q[1][1]; q5[4 * N + s] = Q[1][2];
+}
+
+// Symmetric traceless projection.
+void sym_traceless(const M3 A, M3 out) {
+  double tr = (A[0][0] + A[1][1] + A[2][2]) / 3.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) out[i][j] = 0.5 * (A[i][j] + A[j][i]) - (i == j ? tr : 0.0);
+}
+
+void matmul(const M3 A, const M3 B, M3 C) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += A[i][k] * B[k][j];
+      C[i][j] = s;
+    }
+}
+
+double trace_prod(const M3 A, const M3 B) {  // tr(A B) = A_ij B_ji
+  double s = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) s += A[i][j] * B[j][i];
+  return s;
+}
+
+// Per-site stencil results (Sec. 3: finite differences on Q and psi).
+struct Derivs {
+  double dQ[3][3][3];  // dQ[a][i][j] = d_a Q_ij
+  double lapQ[3][3];
+  double dpsi[3];
+  double lappsi;
+  double hpsi[3][3];
+};
+
+// Isotropic D3Q19 gradient 3 sum_i w_i c_ia f(x+c_i) and Laplacian 6 sum_i w_i (f(x+c_i)-f(x));
+// Hessian of psi: three-point second difference on the diagonal, four corners off it.
+void derivs_at(const Box& B, const double* q5, const double* psi, int x, int y, int z, Derivs& d) {
+  long N = B.n();
+  long s = B.at(x, y, z);
+  M3 Q0;
+  q_full(q5, N, s, Q0);
+  double p0 = psi[s];
+  std::memset(&d, 0, sizeof(d));
+  for (int i = 1; i < NQ; ++i) {
+    long n = B.at(x + CV[i][0], y + CV[i][1], z + CV[i][2]);
+    M3 Qn;
+    q_full(q5, N, n, Qn);
+    double w = wgt(i);
+    for (int a = 0; a < 3; ++a) {
+      if (CV[i][a] == 0) continue;
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) d.dQ[a][p][q] += 3.0 * w * CV[i][a] * Qn[p][q];
+      d.dpsi[a] += 3.0 * w * CV[i][a] * psi[n];
+    }
+    for (int p = 0; p < 3; ++p)
+      for (int q = 0; q < 3; ++q) d.lapQ[p][q] += 6.0 * w * (Qn[p][q] - Q0[p][q]);
+    d.lappsi += 6.0 * w * (psi[n] - p0);
+  }
+  for (int a = 0; a < 3; ++a) {
+    int ea[3] = {0, 0, 0};
+    ea[a] = 1;
+    d.hpsi[a][a] = psi[B.at(x + ea[0], y + ea[1], z + ea[2])] - 2.0 * p0 +
+                   psi[B.at(x - ea[0], y - ea[1], z - ea[2])];
+    for (int b = 0; b < 3; ++b) {
+      if (b == a) continue;
+      int eb[3] = {0, 0, 0};
+      eb[b] = 1;
+      double spp = psi[B.at(x + ea[0] + eb[0], y + ea[1] + eb[1], z + ea[2] + eb[2])];
+      double spm = psi[B.at(x + ea[0] - eb[0], y + ea[1] - eb[1], z + ea[2] - eb[2])];
+      double smp = psi[B.at(x - ea[0] + eb[0], y - ea[1] + eb[1], z - ea[2] + eb[2])];
+      double smm = psi[B.at(x - ea[0] - eb[0], y - ea[1] - eb[1], z - ea[2] - eb[2])];
+      d.hpsi[a][b] = 0.25 * (spp - spm - smp + smm);
+    }
+  }
+}
+
+// Local quantities at one site: H (Eq. 2, Eq. 5), mu (Eq. 1, Eq. 5), free-energy density
+// (Eq. 5) and the three parts of the stress (Eq. 3, Eq. 4).
+struct Local {
+  M3 H;
+  double mu;
+  double fden;
+  M3 sE;  // pressure + elastic + interfacial (Ericksen) stress
+  M3 sR;  // reactive Beris-Edwards stress: flow-aligning xi terms + antisymmetric part
+  M3 sA;  // active stress
+};
+
+void local_at(const orc_params& P, const M3 Q, double psi, const Derivs& d, Local& L) {
+  const double chi = P.chi0 + P.chis * (1.0 + psi);
+  M3 QQ;
+  matmul(Q, Q, QQ);
+  const double trQ2 = trace_prod(Q, Q);
+  const double trQ3 = trace_prod(QQ, Q);
+  // C_ab = eps_amn d_m Q_nb  (the curl of Q)
+  M3 C;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double s = 0.0;
+      for (int m = 0; m < 3; ++m)
+        for (int n = 0; n < 3; ++n) {
+          int e = eps(a, m, n);
+          if (e) s += e * d.dQ[m][n][b];
+        }
+      C[a][b] = s;
+    }
+  double g2 = d.dpsi[0] * d.dpsi[0] + d.dpsi[1] * d.dpsi[1] + d.dpsi[2] * d.dpsi[2];
+  // -dF/dQ before projection
+  M3 Hraw;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double dij = (i == j) ? 1.0 : 0.0;
+      Hraw[i][j] = -P.A0 * (1.0 - chi / 3.0) * Q[i][j] + P.A0 * chi * (QQ[i][j] - dij * trQ2 / 3.0) -
+                   P.A0 * chi * trQ2 * Q[i][j] + P.K * d.lapQ[i][j] - 2.0 * P.K * P.q0 * (C[i][j] + C[j][i]) -
+                   4.0 * P.K * P.q0 * P.q0 * Q[i][j] - P.W * (d.dpsi[i] * d.dpsi[j] - dij * g2 / 3.0);
+    }
+  sym_traceless(Hraw, L.H);
+
+  // mu = dF/dpsi
+  double divQ_dpsi = 0.0, Q_hess = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      divQ_dpsi += d.dQ[a][a][b] * d.dpsi[b];
+      Q_hess += Q[a][b] * d.hpsi[a][b];
+    }
+  L.mu = -P.a * psi + P.b * psi * psi * psi - P.kphi * d.lappsi +
+         P.A0 * P.chis * (-trQ2 / 6.0 - trQ3 / 3.0 + trQ2 * trQ2 / 4.0) - 2.0 * P.W * (divQ_dpsi + Q_hess);
+
+  // free-energy density of Eq. 5
+  double grad2 = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) grad2 += d.dQ[a][i][j] * d.dQ[a][i][j];
+  double QC = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) QC += Q[i][j] * C[i][j];
+  double anch = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) anch += d.dpsi[i] * Q[i][j] * d.dpsi[j];
+  L.fden = -0.5 * P.a * psi * psi + 0.25 * P.b * psi * psi * psi * psi + 0.5 * P.kphi * g2 +
+           P.A0 * (0.5 * (1.0 - chi / 3.0) * trQ2 - chi / 3.0 * trQ3 + chi / 4.0 * trQ2 * trQ2) +
+           0.5 * P.K * grad2 + 2.0 * P.K * P.q0 * QC + 2.0 * P.K * P.q0 * P.q0 * trQ2 + P.W * anch;
+  const double P0 = psi * L.mu - L.fden;
+
+  // Pi_bgn = dF/d(d_b Q_gn) = K d_b Q_gn + 2 K q0 eps_mbg Q_mn
+  double Pi[3][3][3];
+  for (int b = 0; b < 3; ++b)
+    for (int g = 0; g < 3; ++g)
+      for (int n = 0; n < 3; ++n) {
+        double s = P.K * d.dQ[b][g][n];
+        for (int m = 0; m < 3; ++m) {
+          int e = eps(m, b, g);
+          if (e) s += 2.0 * P.K * P.q0 * e * Q[m][n];
+        }
+        Pi[b][g][n] = s;
+      }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double s = -(a == b ? P0 : 0.0);
+      for (int g = 0; g < 3; ++g)
+        for (int n = 0; n < 3; ++n) s -= d.dQ[a][g][n] * Pi[b][g][n];
+      double Qdpsi = 0.0;
+      for (int g = 0; g < 3; ++g) Qdpsi += Q[b][g] * d.dpsi[g];
+      s -= d.dpsi[a] * (P.kphi * d.dpsi[b] + 2.0 * P.W * Qdpsi);
+      L.sE[a][b] = s;
+    }
+
+  // reactive stress with Qt = Q + I/3
+  M3 Qt;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Qt[i][j] = Q[i][j] + (i == j ? 1.0 / 3.0 : 0.0);
+  M3 HQt, QtH, QH, HQ;
+  matmul(L.H, Qt, HQt);
+  matmul(Qt, L.H, QtH);
+  matmul(Q, L.H, QH);
+  matmul(L.H, Q, HQ);
+  const double trQH = trace_prod(Q, L.H);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      L.sR[a][b] = -P.xi * HQt[a][b] - P.xi * QtH[a][b] + 2.0 * P.xi * Qt[a][b] * trQH + QH[a][b] - HQ[a][b];
+
+  const double phic = 0.5 * (1.0 + psi);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) L.sA[a][b] = -P.zeta * phic * Q[a][b];
+}
+
+// Co-rotation term of Beris-Edwards (Eq. 2's strain-rotational part); Wg[a][b] = d_b u_a.
+void corotation(const M3 Wg, const M3 Q, double xi, M3 S) {
+  M3 D, Om, Qt;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      D[i][j] = 0.5 * (Wg[i][j] + Wg[j][i]);
+      Om[i][j] = 0.5 * (Wg[i][j] - Wg[j][i]);
+      Qt[i][j] = Q[i][j] + (i == j ? 1.0 / 3.0 : 0.0);
+    }
+  M3 A, Bm;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      A[i][j] = xi * D[i][j] + Om[i][j];
+      Bm[i][j] = xi * D[i][j] - Om[i][j];
+    }
+  M3 T1, T2;
+  matmul(A, Qt, T1);
+  matmul(Qt, Bm, T2);
+  const double trQW = trace_prod(Q, Wg);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) S[i][j] = T1[i][j] + T2[i][j] - 2.0 * xi * Qt[i][j] * trQW;
+}
+
+// Isotropic gradient of a vector field at a site: Wg[a][b] = d_b u_a.
+void vec_grad_at(const Box& B, const double* u, int x, int y, int z, M3 Wg) {
+  long N = B.n();
+  std::memset(Wg, 0, sizeof(M3));
+  for (int i = 1; i < NQ; ++i) {
+    long n = B.at(x + CV[i][0], y + CV[i][1], z + CV[i][2]);
+    double w = wgt(i);
+    for (int b = 0; b < 3; ++b) {
+      if (CV[i][b] == 0) continue;
+      for (int a = 0; a < 3; ++a) Wg[a][b] += 3.0 * w * CV[i][b] * u[a * N + n];
+    }
+  }
+}
+
+struct Work {
+  std::vector<double> H, mu, sig, F, unew, fnew, rhsQ, rhsP, Qp, Pp;
+};
+
+// Stage 1-4 over the whole box: H (5), mu, total stress (9) per site.
+void fields_all(const Box& B, const orc_params& P, const double* q5, const double* psi, double* H5, double* mu,
+                double* sig9, double* sE9, double* sR9, double* sA9, double* fden) {
+  long N = B.n();
+  for (int z = 0; z < B.nz; ++z)
+    for (int y = 0; y < B.ny; ++y)
+      for (int x = 0; x < B.nx; ++x) {
+        long s = B.at(x, y, z);
+        Derivs d;
+        derivs_at(B, q5, psi, x, y, z, d);
+        M3 Q;
+        q_full(q5, N, s, Q);
+        Local L;
+        local_at(P, Q, psi[s], d, L);
+        if (H5) q_store(L.H, H5, N, s);
+        if (mu) mu[s] = L.mu;
+        if (fden) fden[s] = L.fden;
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) {
+            int k = 3 * a + b;
+            if (sig9) sig9[k * N + s] = L.sE[a][b] + L.sR[a][b] + L.sA[a][b];
+            if (sE9) sE9[k * N + s] = L.sE[a][b];
+            if (sR9) sR9[k * N + s] = L.sR[a][b];
+            if (sA9) sA9[k * N + s] = L.sA[a][b];
+          }
+      }
+}
+
+// Stage 5: F_a = d_b sigma_ab with the isotropic gradient.
+void force_all(const Box& B, const double* sig9, double* F3) {
+  long N = B.n();
+  for (int z = 0; z < B.nz; ++z)
+    for (int y = 0; y < B.ny; ++y)
+      for (int x = 0; x < B.nx; ++x) {
+        long s = B.at(x, y, z);
+        double F[3] = {0, 0, 0};
+        for (int i = 1; i < NQ; ++i) {
+          long n = B.at(x + CV[i][0], y + CV[i][1], z + CV[i][2]);
+          double w = wgt(i);
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+              if (CV[i][b]) F[a] += 3.0 * w * CV[i][b] * sig9[(3 * a + b) * N + n];
+        }
+        for (int a = 0; a < 3; ++a) F3[a * N + s] = F[a];
+      }
+}
+
+// Stage 6: BGK + Guo forcing (Eq. 7 as read), moments (Eq. 8), streaming (Eq. 6).
+void lb_all(const Box& B, const orc_params& P, const double* f, const double* F3, double* fnew, double* unew) {
+  long N = B.n();
+  const double tau = P.tau;
+  for (int z = 0; z < B.nz; ++z)
+    for (int y = 0; y < B.ny; ++y)
+      for (int x = 0; x < B.nx; ++x) {
+        long s = B.at(x, y, z);
+        double rho = 0.0, j[3] = {0, 0, 0};
+        for (int i = 0; i < NQ; ++i) {
+          double fi = f[i * N + s];
+          rho += fi;
+          for (int a = 0; a < 3; ++a) j[a] += fi * CV[i][a];
+        }
+        double F[3] = {F3[0 * N + s], F3[1 * N + s], F3[2 * N + s]};
+        double u[3];
+        for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * F[a]) / rho;
+        double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        for (int i = 0; i < NQ; ++i) {
+          double cu = CV[i][0] * u[0] + CV[i][1] * u[1] + CV[i][2] * u[2];
+          double cF = CV[i][0] * F[0] + CV[i][1] * F[1] + CV[i][2] * F[2];
+          double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+          double feq = wgt(i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * u2);
+          double Fi = (1.0 - 0.5 / tau) * wgt(i) * (3.0 * (cF - uF) + 9.0 * cu * cF);
+          double fstar = f[i * N + s] - (f[i * N + s] - feq) / tau + Fi;
+          long d = B.at(x + CV[i][0], y + CV[i][1], z + CV[i][2]);
+          fnew[i * N + d] = fstar;
+        }
+        for (int a = 0; a < 3; ++a) unew[a * N + s] = u[a];
+      }
+}
+
+// Stage 7 right-hand sides: -upwind advection + co-rotation + Gamma_Q H for Q;
+// -div(upwind flux) + M lap mu for psi.
+void op_rhs(const Box& B, const orc_params& P, const double* q5, const double* psi, const double* uadv,
+            const double* H5, const double* mu, double* rq5, double* rp) {
+  long N = B.n();
+  for (int z = 0; z < B.nz; ++z)
+    for (int y = 0; y < B.ny; ++y)
+      for (int x = 0; x < B.nx; ++x) {
+        long s = B.at(x, y, z);
+        int r[3] = {x, y, z};
+        M3 Q, H, Wg, S;
+        q_full(q5, N, s, Q);
+        q_full(H5, N, s, H);
+        vec_grad_at(B, uadv, x, y, z, Wg);
+        corotation(Wg, Q, P.xi, S);
+        M3 adv;
+        std::memset(adv, 0, sizeof(adv));
+        double div = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          int rp1[3] = {r[0], r[1], r[2]}, rm1[3] = {r[0], r[1], r[2]};
+          rp1[a] += 1;
+          rm1[a] -= 1;
+          long sp = B.at(rp1[0], rp1[1], rp1[2]);
+          long sm = B.at(rm1[0], rm1[1], rm1[2]);
+          double ua = uadv[a * N + s];
+          M3 Qp, Qm;
+          q_full(q5, N, sp, Qp);
+          q_full(q5, N, sm, Qm);
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+              adv[i][j] += std::fmax(ua, 0.0) * (Q[i][j] - Qm[i][j]) + std::fmin(ua, 0.0) * (Qp[i][j] - Q[i][j]);
+          // upwind face fluxes of psi at x + e_a/2 and x - e_a/2
+          double ubp = 0.5 * (ua + uadv[a * N + sp]);
+          double Jp = ubp * (ubp > 0.0 ? psi[s] : psi[sp]);
+          double ubm = 0.5 * (uadv[a * N + sm] + ua);
+          double Jm = ubm * (ubm > 0.0 ? psi[sm] : psi[s]);
+          div += Jp - Jm;
+        }
+        double lapmu = 0.0;
+        for (int i = 1; i < NQ; ++i) {
+          long n = B.at(x + CV[i][0], y + CV[i][1], z + CV[i][2]);
+          lapmu += 6.0 * wgt(i) * (mu[n] - mu[s]);
+        }
+        M3 R;
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) R[i][j] = -adv[i][j] + S[i][j] + P.gammaQ * H[i][j];
+        // Q' = ST(Q + R) with ST the symmetric traceless projection; Q is already
+        // symmetric traceless and ST is linear, so Q' = Q + ST(R).
+        M3 Rp;
+        sym_traceless(R, Rp);
+        q_store(Rp, rq5, N, s);
+        rp[s] = -div + P.M * lapmu;
+      }
+}
+
+void step_one(const Box& B, const orc_params& P, double* f, double* q5, double* psi, double* uprev, Work& w) {
+  const long N = B.n();
+  w.H.resize(5 * N); w.mu.resize(N); w.sig.resize(9 * N); w.F.resize(3 * N);
+  w.unew.resize(3 * N); w.fnew.resize(19 * N); w.rhsQ.resize(5 * N); w.rhsP.resize(N);
+  fields_all(B, P, q5, psi, w.H.data(), w.mu.data(), w.sig.data(), nullptr, nullptr, nullptr, nullptr);
+  force_all(B, w.sig.data(), w.F.data());
+  lb_all(B, P, f, w.F.data(), w.fnew.data(), w.unew.data());
+  const double* uadv = (P.coupling == 1) ? w.unew.data() : uprev;
+  op_rhs(B, P, q5, psi, uadv, w.H.data(), w.mu.data(), w.rhsQ.data(), w.rhsP.data());
+  if (P.integrator == 1) {
+    // Heun: predictor Q* = Q + R(Q), corrector Q' = Q + (R(Q) + R(Q*))/2, u held fixed.
+    w.Qp.resize(5 * N); w.Pp.resize(N);
+    for (long k = 0; k < 5 * N; ++k) w.Qp[k] = q5[k] + w.rhsQ[k];
+    for (long k = 0; k < N; ++k) w.Pp[k] = psi[k] + w.rhsP[k];
+    std::vector<double> H2(5 * N), mu2(N), rq2(5 * N), rp2(N);
+    fields_all(B, P, w.Qp.data(), w.Pp.data(), H2.data(), mu2.data(), nullptr, nullptr, nullptr, nullptr, nullptr);
+    op_rhs(B, P, w.Qp.data(), w.Pp.data(), uadv, H2.data(), mu2.data(), rq2.data(), rp2.data());
+    for (long k = 0; k < 5 * N; ++k) q5[k] += 0.5 * (w.rhsQ[k] + rq2[k]);
+    for (long k = 0; k < N; ++k) psi[k] += 0.5 * (w.rhsP[k] + rp2[k]);
+  } else {
+    for (long k = 0; k < 5 * N; ++k) q5[k] += w.rhsQ[k];
+    for (long k = 0; k < N; ++k) psi[k] += w.rhsP[k];
+  }
+  std::memcpy(f, w.fnew.data(), sizeof(double) * 19 * N);
+  std::memcpy(uprev, w.unew.data(), sizeof(double) * 3 * N);
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): the stream seeded with `seed` returns, at
+// position k >= 1, mix(seed + k * 0x9E3779B97F4A7C15).
+uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + k * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+}  // namespace
+
+extern "C" {
+
+// D3Q19 table as used here (for index matching in tests).
+void orc_lattice(int* c57, double* w19) {
+  for (int i = 0; i < NQ; ++i) {
+    for (int a = 0; a < 3; ++a) c57[3 * i + a] = CV[i][a];
+    w19[i] = wgt(i);
+  }
+}
+
+// Uniform variate in [-1, 1) for (seed, instance, site, component): counter
+// k = 1 + (instance << 40) + 5*site + component in the SplitMix64 stream of `seed`.
+double orc_noise(uint64_t seed, int inst, long site, int comp) {
+  uint64_t k = 1ULL + ((uint64_t)inst << 40) + 5ULL * (uint64_t)site + (uint64_t)comp;
+  uint64_t r = splitmix64_at(seed, k);
+  double u01 = (double)(r >> 11) * (1.0 / 9007199254740992.0);
+  return 2.0 * u01 - 1.0;
+}
+
+// Initial state: rho = rho0, u = 0, psi = tanh((R - r)/2); inside r < R a cholesteric
+// helix about z, n = (cos q0 (z - cz), sin q0 (z - cz), 0), Q = S0 (n n - I/3) plus
+// noise * U[-1, 1) on each stored component; outside Q = 0.
+void orc_init(int nx, int ny, int nz, const orc_params* P, uint64_t seed, int inst, double* f, double* q5,
+              double* psi, double* u) {
+  Box B{nx, ny, nz};
+  long N = B.n();
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        long s = B.at(x, y, z);
+        double dx = x - P->cx, dy = y - P->cy, dz = z - P->cz;
+        double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+        psi[s] = std::tanh((P->R - r) / 2.0);
+        M3 Q;
+        std::memset(Q, 0, sizeof(Q));
+        if (r < P->R) {
+          double n[3] = {std::cos(P->q0 * dz), std::sin(P->q0 * dz), 0.0};
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) Q[i][j] = P->S0 * (n[i] * n[j] - (i == j ? 1.0 / 3.0 : 0.0));
+        }
+        q_store(Q, q5, N, s);
+        if (r < P->R) {
+          for (int c = 0; c < 5; ++c) q5[c * N + s] += P->noise * orc_noise(seed, inst, s, c);
+        }
+        for (int i = 0; i < NQ; ++i) f[i * N + s] = wgt(i) * P->rho0;
+        for (int a = 0; a < 3; ++a) u[a * N + s] = 0.0;
+      }
+}
+
+// Stages 1-4 over the box.  Any output pointer may be null.
+void orc_fields(int nx, int ny, int nz, const orc_params* P, const double* q5, const double* psi, double* H5,
+                double* mu, double* sig9, double* sE9, double* sR9, double* sA9, double* fden) {
+  Box B{nx, ny, nz};
+  fields_all(B, *P, q5, psi, H5, mu, sig9, sE9, sR9, sA9, fden);
+}
+
+void orc_force(int nx, int ny, int nz, const double* sig9, double* F3) {
+  Box B{nx, ny, nz};
+  force_all(B, sig9, F3);
+}
+
+// Stencils on a scalar field (for the stencil pins).
+void orc_stencils(int nx, int ny, int nz, const double* s, double* grad3, double* lap, double* hess9) {
+  Box B{nx, ny, nz};
+  long N = B.n();
+  std::vector<double> zero(5 * N, 0.0);
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        long k = B.at(x, y, z);
+        Derivs d;
+        derivs_at(B, zero.data(), s, x, y, z, d);
+        for (int a = 0; a < 3; ++a) grad3[a * N + k] = d.dpsi[a];
+        lap[k] = d.lappsi;
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) hess9[(3 * a + b) * N + k] = d.hpsi[a][b];
+      }
+}
+
+// Per-site co-rotation S(W, Q) (full 3x3 in and out; Wg[a][b] = d_b u_a).
+void orc_corotation(const double* Wg9, const double* Q9, double xi, double* S9) {
+  M3 W, Q, S;
+  for (int i = 0; i < 9; ++i) { W[i / 3][i % 3] = Wg9[i]; Q[i / 3][i % 3] = Q9[i]; }
+  corotation(W, Q, xi, S);
+  for (int i = 0; i < 9; ++i) S9[i] = S[i / 3][i % 3];
+}
+
+// Per-site Q update pieces over the box for a given advecting velocity: the projected
+// right-hand sides of Q (5) and psi (1), and the velocity gradient W (9).
+void orc_op_rhs(int nx, int ny, int nz, const orc_params* P, const double* q5, const double* psi,
+                const double* uadv, const double* H5, const double* mu, double* rq5, double* rp, double* W9) {
+  Box B{nx, ny, nz};
+  op_rhs(B, *P, q5, psi, uadv, H5, mu, rq5, rp);
+  if (W9) {
+    long N = B.n();
+    for (int z = 0; z < nz; ++z)
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+          long s = B.at(x, y, z);
+          M3 Wg;
+          vec_grad_at(B, uadv, x, y, z, Wg);
+          for (int k = 0; k < 9; ++k) W9[k * N + s] = Wg[k / 3][k % 3];
+        }
+  }
+}
+
+// nsteps full hybrid steps in place.  f: 19*N pre-collision populations (unshifted),
+// q5: 5*N, psi: N, uprev: 3*N = u of the previous step (0 at t = 0).
+void orc_step(int nx, int ny, int nz, const orc_params* P, double* f, double* q5, double* psi, double* uprev,
+              long nsteps) {
+  Box B{nx, ny, nz};
+  Work w;
+  for (long t = 0; t < nsteps; ++t) step_one(B, *P, f, q5, psi, uprev, w);
+}
+
+// Stage 6 alone (for LB pins): collide with a given force and stream.
+void orc_lb(int nx, int ny, int nz, const orc_params* P, const double* f, const double* F3, double* fnew,
+            double* unew) {
+  Box B{nx, ny, nz};
+  lb_all(B, *P, f, F3, fnew, unew);
+}
+
+// Conserved sums and centroid moments (FP64):
+// out[0] = sum rho, out[1] = sum psi, out[2..4] = sum_i f_i c_i, out[5..7] = sum phi_c cos(2 pi x_a/L_a),
+// out[8..10] = sum phi_c sin(2 pi x_a/L_a), out[11] = sum phi_c; phi_c = (1 + psi)/2.
+void orc_observables(int nx, int ny, int nz, const double* f, const double* psi, double* out) {
+  Box B{nx, ny, nz};
+  long N = B.n();
+  for (int k = 0; k < 12; ++k) out[k] = 0.0;
+  const double PI = 3.14159265358979323846;
+  int L[3] = {nx, ny, nz};
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        long s = B.at(x, y, z);
+        for (int i = 0; i < NQ; ++i) {
+          double fi = f[i * N + s];
+          out[0] += fi;
+          for (int a = 0; a < 3; ++a) out[2 + a] += fi * CV[i][a];
+        }
+        out[1] += psi[s];
+        double pc = 0.5 * (1.0 + psi[s]);
+        int r[3] = {x, y, z};
+        for (int a = 0; a < 3; ++a) {
+          out[5 + a] += pc * std::cos(2.0 * PI * r[a] / L[a]);
+          out[8 + a] += pc * std::sin(2.0 * PI * r[a] / L[a]);
+        }
+        out[11] += pc;
+      }
+}
+
+}  // extern "C"

@@ -1,0 +1,548 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: closed forms of the
+stencils, conservation laws of Eqs. 6-8, the Guo forcing moments, the viscosity of the
+BGK scheme, the Landau-de Gennes transition at chi = 2.7 printed in Sec. 2, variational
+derivatives of the free energy of Eq. 5 computed by sympy, the Ericksen (Noether)
+identity for the passive stress, the Onsager reciprocity between the co-rotation term
+of Eq. 2 and the reactive stress, and the symmetries of the model.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests import oracle_helpers as OH
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        k, v = line.split()
+        out[k] = float(v)
+    return out
+
+
+# ---------------------------------------------------------------- stencils (Sec. 3)
+
+@pytest.mark.parametrize("shape", [(4, 4, 4), (5, 6, 7)])
+def test_stencil_fourier_symbols(shape):
+    """On exp(i k.x) the isotropic D3Q19 stencils act as their Fourier symbols:
+    grad_a -> i (sin k_a / 3)(1 + sum_{b != a} cos k_b),
+    lap    -> (2/3) sum_a (cos k_a - 1) + (2/3) sum_{a<b} (cos k_a cos k_b - 1),
+    hess_aa -> 2 cos k_a - 2, hess_ab -> -sin k_a sin k_b."""
+    nx, ny, nz = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    for m in [(1, 0, 0), (0, 1, 1), (1, 2, 3), (2, -1, 1)]:
+        k = [2 * np.pi * m[0] / nx, 2 * np.pi * m[1] / ny, 2 * np.pi * m[2] / nz]
+        arg = k[0] * x + k[1] * y + k[2] * z
+        for part, fn in (("re", np.cos), ("im", np.sin)):
+            s = fn(arg)
+            g, lap, h = O.stencils(s)
+            c = [np.cos(v) for v in k]
+            sn = [np.sin(v) for v in k]
+            # derivative of e^{i arg} is i*symbol*e^{i arg}; real/imag parts accordingly
+            ds = -np.sin(arg) if part == "re" else np.cos(arg)
+            for a in range(3):
+                sym = sn[a] / 3.0 * (1 + sum(c[b] for b in range(3) if b != a))
+                np.testing.assert_allclose(g[a], sym * ds, atol=1e-13)
+            lsym = (2 / 3) * sum(ci - 1 for ci in c) + (2 / 3) * sum(
+                c[a] * c[b] - 1 for a in range(3) for b in range(a + 1, 3))
+            np.testing.assert_allclose(lap, lsym * s, atol=1e-13)
+            for a in range(3):
+                for b in range(3):
+                    hs = (2 * c[a] - 2) if a == b else -sn[a] * sn[b]
+                    np.testing.assert_allclose(h[3 * a + b], hs * s, atol=1e-13)
+
+
+def test_stencils_exact_on_quadratics():
+    """Away from the periodic seam, gradient/Laplacian/Hessian are exact on quadratics."""
+    n = 9
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    s = 0.3 * x * x - 0.7 * x * y + 0.2 * z * z + 1.1 * y * z + 0.5 * x - 2 * y + 0.25 * z + 3.0
+    g, lap, h = O.stencils(s.astype(np.float64))
+    sl = (slice(1, n - 1),) * 3
+    np.testing.assert_allclose(g[0][sl], (0.6 * x - 0.7 * y + 0.5)[sl], atol=1e-12)
+    np.testing.assert_allclose(g[1][sl], (-0.7 * x + 1.1 * z - 2)[sl], atol=1e-12)
+    np.testing.assert_allclose(g[2][sl], (0.4 * z + 1.1 * y + 0.25)[sl], atol=1e-12)
+    np.testing.assert_allclose(lap[sl], 0.6 + 0.4, atol=1e-12)
+    H = np.array([[0.6, -0.7, 0.0], [-0.7, 0.0, 1.1], [0.0, 1.1, 0.4]])
+    for a in range(3):
+        for b in range(3):
+            np.testing.assert_allclose(h[3 * a + b][sl], H[a, b], atol=1e-12)
+
+
+# ---------------------------------------------------------------- LB (Eqs. 6-8, Guo forcing)
+
+def _feq(rho, v, c, w):
+    cu = np.einsum("ia,a...->i...", c, v)
+    v2 = (v * v).sum(0)
+    return w.reshape((19,) + (1,) * rho.ndim) * rho * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * v2)
+
+
+def test_lb_conservation_unforced():
+    c, w = O.lattice()
+    rng = np.random.default_rng(3)
+    shp = (6, 5, 7)
+    nx, ny, nz = shp
+    f = w.reshape(19, 1, 1, 1) * (1 + 0.05 * rng.standard_normal((19, nz, ny, nx)))
+    p = O.default_params(shp, tau=0.8)
+    F = np.zeros((3, nz, ny, nx))
+    fn, un = O.lb(f, F, p)
+    assert abs(fn.sum() - f.sum()) < 1e-12 * f.sum()
+    for a in range(3):
+        m0 = np.tensordot(c[:, a].astype(float), f, axes=(0, 0)).sum()
+        m1 = np.tensordot(c[:, a].astype(float), fn, axes=(0, 0)).sum()
+        assert abs(m1 - m0) < 1e-12
+
+
+def test_lb_rest_state_exact():
+    c, w = O.lattice()
+    shp = (4, 5, 6)
+    f = np.broadcast_to(w.reshape(19, 1, 1, 1), (19, 6, 5, 4)).copy() * 1.3
+    p = O.default_params(shp)
+    fn, un = O.lb(f, np.zeros((3, 6, 5, 4)), p)
+    assert np.abs(fn - f).max() < 4e-16  # one rounding of rho
+    assert np.abs(un).max() == 0.0
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.8, 1.7])
+def test_guo_forcing_moments(tau):
+    """Uniform fluid, uniform force F: the collision adds exactly F to the momentum,
+    u = (j + F/2)/rho, and the second moment of the forcing is (1 - 1/2tau)(uF + Fu)."""
+    c, w = O.lattice()
+    shp = (4, 4, 4)
+    rho = 1.2 * np.ones((4, 4, 4))
+    v = np.array([0.01, -0.02, 0.005]).reshape(3, 1, 1, 1) * np.ones((3, 4, 4, 4))
+    F = np.array([1e-3, 2e-4, -5e-4]).reshape(3, 1, 1, 1) * np.ones((3, 4, 4, 4))
+    f = _feq(rho, v, c, w)
+    p = O.default_params(shp, tau=tau)
+    fn, un = O.lb(f, F, p)
+    u = v + F / (2 * rho)
+    np.testing.assert_allclose(un, u, atol=1e-15)
+    cf = c.astype(float)
+    j1 = np.einsum("ia,i...->a...", cf, fn)
+    np.testing.assert_allclose(j1, rho * v + F, atol=1e-15)
+    np.testing.assert_allclose(fn.sum(0), rho, atol=1e-14)
+    Pi1 = np.einsum("ia,ib,i...->ab...", cf, cf, fn)[:, :, 0, 0, 0]
+    r, vv, uu, FF = rho[0, 0, 0], v[:, 0, 0, 0], u[:, 0, 0, 0], F[:, 0, 0, 0]
+    expect = (r * (np.outer(vv, vv) + np.eye(3) / 3) - r * (np.outer(vv, vv) - np.outer(uu, uu)) / tau
+              + (1 - 0.5 / tau) * (np.outer(uu, FF) + np.outer(FF, uu)))
+    np.testing.assert_allclose(Pi1, expect, atol=1e-15)
+
+
+def test_shear_wave_decay_matches_viscosity():
+    """u_x = U sin(2 pi z / L) decays at nu k^2 with nu = (tau - 1/2)/3 (BGK)."""
+    c, w = O.lattice()
+    L = 32
+    for tau in (1.0, 0.7):
+        p = O.default_params((4, 4, L), tau=tau)
+        z = np.arange(L).reshape(L, 1, 1) * np.ones((L, 4, 4))
+        U = 1e-4
+        v = np.zeros((3, L, 4, 4))
+        v[0] = U * np.sin(2 * np.pi * z / L)
+        f = _feq(np.ones((L, 4, 4)), v, c, w)
+        F = np.zeros((3, L, 4, 4))
+        amps = []
+        nsteps = 200
+        for t in range(nsteps + 1):
+            fn, un = O.lb(f, F, p)
+            amps.append(2 * np.mean(un[0] * np.sin(2 * np.pi * z / L)))
+            f = fn
+        amps = np.array(amps)
+        ts = np.arange(nsteps + 1)
+        rate = -np.polyfit(ts[20:], np.log(amps[20:]), 1)[0]
+        nu = (tau - 0.5) / 3
+        assert abs(rate / (nu * (2 * np.pi / L) ** 2) - 1) < 0.01
+
+
+def test_full_step_reduces_to_lb_without_order():
+    """With Q = 0, uniform psi and xi = 0 the hybrid step is the plain BGK LB step."""
+    c, w = O.lattice()
+    L = 16
+    shp = (4, 4, L)
+    p = O.default_params(shp, xi=0.0)
+    s = O.State(shp, p)
+    z = np.arange(L).reshape(L, 1, 1) * np.ones((L, 4, 4))
+    v = np.zeros((3, L, 4, 4))
+    v[0] = 1e-3 * np.sin(2 * np.pi * z / L)
+    s.f = _feq(np.ones((L, 4, 4)), v, c, w)
+    s.q[:] = 0.0
+    s.psi[:] = 0.3
+    s.u[:] = 0.0
+    f_ref = s.f.copy()
+    for _ in range(5):
+        f_ref, _ = O.lb(f_ref, np.zeros((3, L, 4, 4)), p)
+    s.step(5)
+    np.testing.assert_allclose(s.f, f_ref, atol=1e-15)
+    assert np.abs(s.q).max() == 0.0
+    np.testing.assert_allclose(s.psi, 0.3, atol=1e-15)
+
+
+# ---------------------------------------------------------------- Landau-de Gennes bulk (Eq. 5)
+
+def _uniform_uniaxial(S, shp):
+    n = np.array([0.6, 0.0, 0.8])
+    Q = S * (np.outer(n, n) - np.eye(3) / 3)
+    nx, ny, nz = shp
+    q5 = np.array([Q[0, 0], Q[0, 1], Q[0, 2], Q[1, 1], Q[1, 2]]).reshape(5, 1, 1, 1) * np.ones((5, nz, ny, nx))
+    return q5
+
+
+@pytest.mark.parametrize("chi", [2.7, 2.8, 3.0, 3.5])
+def test_ldg_equilibrium_order(chi):
+    """With no gradients and no chirality, H = 0 at S = 0 and at
+    S_eq = 1/4 + 3/4 sqrt(1 - 8/(3 chi)), the stationary points of the LdG bulk term."""
+    shp = (4, 4, 4)
+    p = O.default_params(shp, q0=0.0, chi0=chi - 0.5, chis=0.25)
+    psi = np.ones((4, 4, 4))
+    Seq = 0.25 + 0.75 * np.sqrt(1 - 8 / (3 * chi))
+    for S, zero in ((0.0, True), (Seq, True), (Seq + 0.02, False), (0.7 * Seq, False)):
+        out = O.fields(_uniform_uniaxial(S, shp), psi, p)
+        hmax = np.abs(out["H"]).max()
+        if zero:
+            assert hmax < 1e-14, (chi, S, hmax)
+        else:
+            assert hmax > 1e-4
+
+
+def test_ldg_transition_at_paper_threshold():
+    """Sec. 2 states the LC phase is confined where chi > 2.7.  For the LdG bulk term this
+    is the first-order transition: at chi = 2.7 the ordered stationary state (S = 1/3)
+    has the same free energy as the isotropic one; above it, it is lower; below, higher."""
+    thr = _golden("paper_constants.txt")["chi_threshold"]
+    shp = (4, 4, 4)
+    psi = np.ones((4, 4, 4))
+    for chi, sign in ((thr, 0), (thr + 0.05, -1), (thr - 0.02, +1)):
+        p = O.default_params(shp, q0=0.0, chi0=chi - 0.5, chis=0.25)
+        Seq = 0.25 + 0.75 * np.sqrt(1 - 8 / (3 * chi))
+        out = O.fields(_uniform_uniaxial(Seq, shp), psi, p)
+        fd = out["fden"][0, 0, 0]
+        f0 = O.fields(_uniform_uniaxial(0.0, shp), psi, p)["fden"][0, 0, 0]
+        if sign == 0:
+            assert abs(Seq - 1 / 3) < 1e-12
+            assert abs(fd - f0) < 1e-14
+            assert np.abs(out["H"]).max() < 1e-14
+        else:
+            assert np.sign(fd - f0) == sign
+
+
+# ---------------------------------------------------------------- H and mu = variational derivatives of Eq. 5
+
+def _scaled_params(base, h):
+    """Lattice parameters that represent grid spacing h in lattice units (dx = 1)."""
+    p = O.default_params((4, 4, 4))
+    for k, v in base.items():
+        setattr(p, k, v)
+    p.K = base["K"] / h ** 2
+    p.q0 = base["q0"] * h
+    p.W = base["W"] / h ** 2
+    p.kphi = base["kphi"] / h ** 2
+    return p
+
+
+BASE = dict(a=0.07, b=0.07, kphi=0.14, A0=1.0, chi0=2.5, chis=0.25, K=0.04, q0=2 * np.pi / 16,
+            W=0.1, xi=0.7, zeta=0.0)
+
+
+def test_H_mu_are_variational_derivatives_of_eq5():
+    """The oracle's H and mu converge at second order to -dF/dQ (traceless-symmetric) and
+    dF/dpsi of the free energy of Eq. 5 as written in the paper (curl form of the chiral
+    term, binary term in phi with phi0 = 2), differentiated by sympy."""
+    Lp = 16.0
+    errs_H, errs_mu = [], []
+    for n in (16, 32, 64):
+        h = Lp / n
+        st_ = OH.smooth_state((n, n, n), h=h, seed=5)
+        H_a, mu_a = OH.analytic_H_mu(st_, BASE)
+        out = O.fields(np.ascontiguousarray(st_["q5"]), np.ascontiguousarray(st_["psi"]), _scaled_params(BASE, h))
+        H_o = OH.full_from5(out["H"])
+        errs_H.append(np.abs(H_o - H_a).max() / np.abs(H_a).max())
+        errs_mu.append(np.abs(out["mu"] - mu_a).max() / np.abs(mu_a).max())
+    # second order: each halving of h cuts the error ~4x
+    for e in (errs_H, errs_mu):
+        assert e[2] < 0.02, e
+        assert e[1] / e[2] > 3.2 and e[0] / e[1] > 3.0, e
+
+
+def test_helix_minimises_chiral_energy():
+    """The sign of q0: n = (cos q0 z, sin q0 z, 0) has no oscillating curl-energy
+    (curl Q + 2 q0 Q has no 2q0 Fourier component), the opposite twist does."""
+    n = 64
+    h = 16.0 / n
+    q0 = BASE["q0"]
+    z = np.arange(n) * h
+    for sgn, small in ((1, True), (-1, False)):
+        th = sgn * q0 * z
+        S = 0.5
+        nn = np.array([np.cos(th), np.sin(th), 0 * th])
+        Q = S * (np.einsum("a...,b...->ab...", nn, nn) - np.eye(3).reshape(3, 3, 1) / 3)
+        q5 = np.array([Q[0, 0], Q[0, 1], Q[0, 2], Q[1, 1], Q[1, 2]]).reshape(5, n, 1, 1) * np.ones((5, n, 4, 4))
+        q5 = np.ascontiguousarray(q5)
+        p = _scaled_params(dict(BASE, W=0.0), h)
+        p.chi0, p.chis = 2.5, 0.25
+        out = O.fields(q5, np.ones((n, 4, 4)), p)
+        # oscillating (xx-yy, xy) part of H at the helix wavevector
+        osc = np.abs(out["H"][1]).max()
+        if small:
+            assert osc < 2e-3 * 4 * BASE["K"] * q0 ** 2 * S * 1e2
+        else:
+            assert osc > 0.5 * 4 * BASE["K"] * (2 * q0) ** 2 * S * 0.5
+
+
+# ---------------------------------------------------------------- stresses (Eq. 3, Eq. 4)
+
+def test_ericksen_identity_for_passive_stress():
+    """Translation invariance of Eq. 5 (Noether): div of the pressure + elastic + interface
+    stress equals -psi grad mu - H : grad Q, at second order in the grid spacing."""
+    Lp = 16.0
+    errs = []
+    for n in (16, 32, 64):
+        h = Lp / n
+        st_ = OH.smooth_state((n, n, n), h=h, seed=11)
+        out = O.fields(np.ascontiguousarray(st_["q5"]), np.ascontiguousarray(st_["psi"]), _scaled_params(BASE, h))
+        sE = out["sE"].reshape(3, 3, n, n, n)
+        div = np.zeros((3, n, n, n))
+        for a in range(3):
+            for b in range(3):
+                div[a] += OH.spectral_grad(sE[a, b], h)[b]
+        gmu = OH.spectral_grad(out["mu"], h)
+        H = OH.full_from5(out["H"])
+        Q = OH.full_from5(st_["q5"])
+        dQ = np.array([[OH.spectral_grad(Q[i, j], h) for j in range(3)] for i in range(3)])  # [i,j,a]
+        rhs = -st_["psi"] * gmu - np.einsum("ij...,ija...->a...", H, dQ)
+        errs.append(np.abs(div - rhs).max() / np.abs(rhs).max())
+    assert errs[2] < 0.02, errs
+    assert errs[1] / errs[2] > 3.0, errs
+
+
+def test_onsager_reciprocity_reactive_stress():
+    """The flow-coupling of Eq. 2 and the reactive stress are Onsager partners:
+    H : S(W, Q) + sigma_R : W = 0 for every traceless velocity gradient W (W_ab = d_b u_a)."""
+    n = 8
+    st_ = OH.smooth_state((n, n, n), seed=2)
+    p = O.default_params((n, n, n), xi=0.7)
+    out = O.fields(np.ascontiguousarray(st_["q5"]), np.ascontiguousarray(st_["psi"]), p)
+    H = OH.full_from5(out["H"])
+    Q = OH.full_from5(st_["q5"])
+    sR = out["sR"].reshape(3, 3, n, n, n)
+    rng = np.random.default_rng(0)
+    for _ in range(40):
+        z, y, x = rng.integers(0, n, size=3)
+        W = rng.standard_normal((3, 3))
+        W -= np.eye(3) * np.trace(W) / 3
+        S = O.corotation(W, Q[:, :, z, y, x], 0.7)
+        lhs = np.sum(H[:, :, z, y, x] * S) + np.sum(sR[:, :, z, y, x] * W)
+        scale = np.abs(H[:, :, z, y, x]).max() * np.abs(W).max()
+        assert abs(lhs) < 1e-13 * max(scale, 1.0)
+        # symmetric part is traceless; antisymmetric part is Q H - H Q
+        assert abs(np.trace(sR[:, :, z, y, x])) < 1e-14
+        Hs, Qs = H[:, :, z, y, x], Q[:, :, z, y, x]
+        np.testing.assert_allclose(sR[:, :, z, y, x] - sR[:, :, z, y, x].T, 2 * (Qs @ Hs - Hs @ Qs), atol=1e-14)
+
+
+def test_active_stress_eq4():
+    """Eq. 4: sigma_act = -zeta Q inside the droplet (phi_c = 1), zero outside."""
+    n = 4
+    st_ = OH.smooth_state((n, n, n), seed=4)
+    for psi_v, phic in ((1.0, 1.0), (-1.0, 0.0), (0.0, 0.5)):
+        p = O.default_params((n, n, n), zeta=0.01)
+        out = O.fields(np.ascontiguousarray(st_["q5"]), np.full((n, n, n), psi_v), p)
+        Q = OH.full_from5(st_["q5"]).reshape(9, n, n, n)
+        np.testing.assert_allclose(out["sA"], -0.01 * phic * Q, atol=1e-16)
+
+
+def test_force_is_divergence_of_total_stress():
+    n = 6
+    st_ = OH.smooth_state((n, n, n), seed=8)
+    p = O.default_params((n, n, n))
+    out = O.fields(np.ascontiguousarray(st_["q5"]), np.ascontiguousarray(st_["psi"]), p)
+    np.testing.assert_allclose(out["sigma"], out["sE"] + out["sR"] + out["sA"], atol=1e-15)
+    F = O.force(out["sigma"])
+    s9 = out["sigma"].reshape(3, 3, n, n, n)
+    ref = np.zeros((3, n, n, n))
+    for a in range(3):
+        for b in range(3):
+            ref[a] += O.stencils(np.ascontiguousarray(s9[a, b]))[0][b]
+    np.testing.assert_allclose(F, ref, atol=1e-15)
+    # a telescoping divergence: total force vanishes
+    assert np.abs(F.sum(axis=(1, 2, 3))).max() < 1e-13
+
+
+# ---------------------------------------------------------------- the order-parameter update
+
+def test_upwind_exact_for_linear_profiles():
+    """First-order upwind advection is exact on linear profiles with uniform u; the
+    upwind flux form conserves psi."""
+    n = 8
+    p = O.default_params((n, n, n), gammaQ=0.0, M=0.0, xi=0.0)
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    q5 = np.zeros((5, n, n, n))
+    q5[1] = 0.01 * x + 0.02 * y - 0.01 * z
+    psi = 0.05 * y
+    for uu in ([0.01, -0.02, 0.005], [-0.01, 0.02, -0.005]):
+        u = np.array(uu).reshape(3, 1, 1, 1) * np.ones((3, n, n, n))
+        H = np.zeros((5, n, n, n))
+        mu = np.zeros((n, n, n))
+        rq, rp, W = O.op_rhs(q5, psi, u, H, mu, p)
+        sl = (slice(1, n - 1),) * 3
+        np.testing.assert_allclose(rq[1][sl], -(0.01 * uu[0] + 0.02 * uu[1] - 0.01 * uu[2]), atol=1e-15)
+        np.testing.assert_allclose(rp[sl], -0.05 * uu[1], atol=1e-15)
+        assert np.abs(W).max() < 1e-17
+        assert abs(rp.sum()) < 1e-14
+
+
+# ---------------------------------------------------------------- full step: conservation and symmetry
+
+def _droplet_state(n=16, R=5.0, **kw):
+    p = O.default_params((n, n, n), R=R, p0=8.0, **kw)
+    return O.State((n, n, n), p, seed=1)
+
+
+def _sums(s):
+    import math
+    c, _ = O.lattice()
+    mom = [math.fsum(np.tensordot(c[:, a].astype(float), s.f, axes=(0, 0)).ravel()) for a in range(3)]
+    return math.fsum(s.f.ravel()), math.fsum(s.psi.ravel()), np.array(mom)
+
+
+def test_full_step_conserves_mass_psi_momentum():
+    """Eqs. 6-8 with Guo forcing conserve mass; the total force is a telescoping sum, so
+    momentum is conserved too; the Cahn-Hilliard flux form conserves psi (Eq. 1)."""
+    s = _droplet_state(zeta=0.01)
+    m0, p0_, j0 = _sums(s)
+    s.step(20)
+    m1, p1, j1 = _sums(s)
+    N = 16 ** 3
+    assert abs(m1 - m0) < 1e-14 * N
+    assert abs(p1 - p0_) < 1e-14 * N
+    assert np.abs(j1 - j0).max() < 1e-15 * N
+    assert np.abs(s.u).max() > 1e-6  # the droplet does drive a flow
+
+
+def test_heun_and_sync_variants_conserve():
+    for kw in (dict(integrator=1), dict(coupling=1)):
+        s = _droplet_state(n=12, R=4.0, **kw)
+        m0, p0_, _ = _sums(s)
+        s.step(5)
+        m1, p1, _ = _sums(s)
+        assert abs(p1 - p0_) < 1e-14 * 12 ** 3
+        assert abs(m1 - m0) < 1e-14 * 12 ** 3
+
+
+def _random_state(n, seed):
+    c, w = O.lattice()
+    st_ = OH.smooth_state((n, n, n), seed=seed)
+    rng = np.random.default_rng(seed)
+    f = w.reshape(19, 1, 1, 1) * (1 + 0.01 * rng.standard_normal((19, n, n, n)))
+    u = 1e-3 * rng.standard_normal((3, n, n, n))
+    return f, np.ascontiguousarray(st_["q5"]), np.ascontiguousarray(np.clip(st_["psi"], -0.95, 0.95)), u
+
+
+def _run(f, q, psi, u, p, nsteps):
+    s = O.State.__new__(O.State)
+    nz = psi.shape[0]
+    s.shape, s.p, s.t = (nz, nz, nz), p, 0
+    s.f, s.q, s.psi, s.u = f.copy(), q.copy(), psi.copy(), u.copy()
+    s.step(nsteps)
+    return s
+
+
+@pytest.mark.parametrize("P,name", [
+    (np.array([[0, 1, 0], [0, 0, 1], [1, 0, 0]]), "cyclic"),
+    (np.array([[0, 1, 0], [1, 0, 0], [0, 0, 1]]), "swap-xy"),
+    (np.diag([1, 1, -1]), "mirror-z"),
+])
+def test_cubic_symmetry_equivariance(P, name):
+    """Rotations and reflections of the lattice commute with the step; improper ones flip
+    the handedness q0 -> -q0 (the chiral term is a pseudo-scalar)."""
+    c, w = O.lattice()
+    n = 6
+    f, q, psi, u = _random_state(n, seed=21)
+    p = O.default_params((n, n, n), zeta=0.01, W=0.05)
+    s1 = _run(f, q, psi, u, p, 3)
+    a = OH.transform_state(s1.f, s1.q, s1.psi, s1.u, P, c)
+    p2 = O.default_params((n, n, n), zeta=0.01, W=0.05)
+    p2.q0 = p.q0 * round(np.linalg.det(P))
+    t = OH.transform_state(f, q, psi, u, P, c)
+    s2 = _run(*t, p2, 3)
+    for x1, x2 in zip(a, (s2.f, s2.q, s2.psi, s2.u)):
+        np.testing.assert_allclose(x2, x1, atol=2e-13)
+
+
+def test_cholesteric_helix_is_stationary():
+    """A uniform helix (psi = 1, Q period pi/q0 commensurate with the box) drives no flow
+    with or without activity: rotation by pi about z maps it to itself, so sigma_xz =
+    sigma_yz = 0, and screw symmetry makes sigma_zz uniform.  Its phase does not drift."""
+    nz = 16
+    shp = (4, 4, nz)
+    for zeta in (0.0, 0.005):
+        p = O.default_params(shp, p0=16.0, zeta=zeta, R=1e9)
+        s = O.State(shp, p)
+        s.psi[:] = 1.0
+        z = np.arange(nz).reshape(nz, 1, 1)
+        th = p.q0 * (z - p.cz) * np.ones((nz, 4, 4))
+        nn = np.array([np.cos(th), np.sin(th), 0 * th])
+        Q = 0.5 * (np.einsum("a...,b...->ab...", nn, nn) - np.eye(3).reshape(3, 3, 1, 1, 1) / 3)
+        s.q = np.ascontiguousarray(np.array([Q[0, 0], Q[0, 1], Q[0, 2], Q[1, 1], Q[1, 2]]))
+        s.step(30)
+        assert np.abs(s.u).max() < 1e-13
+        assert np.abs(s.q[2]).max() < 1e-15 and np.abs(s.q[4]).max() < 1e-15
+        # screw symmetry: Q(z+1) = R(q0) Q(z) R(q0)^T
+        Qf = OH.full_from5(s.q)
+        c, sn = np.cos(p.q0), np.sin(p.q0)
+        Rm = np.array([[c, -sn, 0], [sn, c, 0], [0, 0, 1]])
+        for k in range(nz - 1):
+            np.testing.assert_allclose(Qf[:, :, k + 1, 0, 0], Rm @ Qf[:, :, k, 0, 0] @ Rm.T, atol=1e-13)
+        # phase: at z = cz the director stays along x (Q_xy = 0)
+        assert abs(s.q[1][int(p.cz), 0, 0]) < 1e-13
+        np.testing.assert_allclose(s.psi, 1.0, atol=1e-14)
+
+
+def test_flat_interface_is_equilibrium():
+    """psi = tanh(x/2) with Q = 0 is the flat-interface equilibrium for k_phi = 2a: mu
+    vanishes as the grid is refined (second order)."""
+    Lp = 64.0
+    errs = []
+    for n in (64, 128, 256):
+        h = Lp / n
+        x = np.arange(n) * h
+        psi1 = np.tanh((x - Lp / 4) / 2) - np.tanh((x - 3 * Lp / 4) / 2) - 1.0
+        psi = np.ascontiguousarray(np.broadcast_to(psi1, (4, 4, n)))
+        p = _scaled_params(BASE, h)
+        out = O.fields(np.zeros((5, 4, 4, n)), psi, p)
+        errs.append(np.abs(out["mu"]).max())
+    assert errs[2] < 1e-3 and errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5, errs
+
+
+# ---------------------------------------------------------------- initial state
+
+def test_noise_is_splitmix64():
+    vals = [int(l) for l in open(os.path.join(GOLDEN, "splitmix64_seed1234567.txt")) if l.strip()
+            and not l.startswith("#")]
+    for k, r in enumerate(vals):
+        # counter k+1 = 1 + 5*site + comp for instance 0
+        site, comp = divmod(k, 5)
+        expect = 2.0 * ((r >> 11) * 2.0 ** -53) - 1.0
+        assert O.noise(1234567, 0, site, comp) == expect
+
+
+def test_initial_droplet():
+    n = 32
+    p = O.default_params((n, n, n), R=8.0, p0=16.0)
+    s = O.State((n, n, n), p, seed=3)
+    assert np.all(np.abs(s.q) <= 0.5)
+    assert abs(s.psi[16, 16, 16] - np.tanh(4.0)) < 1e-15
+    inside = s.psi > np.tanh(0.0)
+    Q = OH.full_from5(s.q)
+    # away from the noise, the order inside is S0 = 0.5 along the helix
+    lam = np.linalg.eigvalsh(np.moveaxis(Q[:, :, 16, 16, 16], (0, 1), (0, 1)))
+    assert abs(1.5 * lam.max() - 0.5) < 5e-3
+    assert np.all(s.q[:, ~inside] == 0.0)
+    assert s.f.sum() == pytest.approx(n ** 3)
