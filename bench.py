@@ -1,0 +1,308 @@
+"""Benchmark of the hybrid LB step (MLUPS and fraction of the HBM roofline).
+
+Workload: one 3D active cholesteric droplet, 128^3 periodic box, R = 32, pitch 32,
+zeta = 0.005 (A0 = 1, chi_in = 3, K = 0.04, Gamma_Q = 0.3, xi = 0.7, a = b = 0.07,
+M = 0.1, tau = 1), FP32 with populations shifted by w_i rho0; synthetic seeded initial
+state (tanh droplet, cholesteric helix + 1e-3 noise).  The plain FP64 GPU path is timed
+on the same workload for the FP32/FP64 speedup.
+
+One JSON line on rank 0.  `value` is whole-job site updates per second (MLUPS) with the
+state resident in HBM; `e2e` is the same metric through the public API with host
+buffers (state uploaded and read back every step).  `--impl reference` times the FP64
+CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "hybrid-step MLUPS & % of HBM roofline, FP32 vs plain FP64 at stated error"
+BYTES_PER_SITE = {"fp32": 200, "fp64": 400}  # state read once + written once: (19 + 5 + 1) x 2 words
+
+
+def workload_params(L, n, prec):
+    return L.default_params((n, n, n), R=n / 4.0, p0=n / 4.0, precision=prec, zeta=0.005)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def committed_traffic():
+    """DRAM bytes per site-update of the step kernels from the committed ncu summary."""
+    p = os.path.join(ROOT, "profiles", "lbcad_step_fp32_128cube.md")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.startswith("traffic_bytes_per_site:"):
+            try:
+                return float(line.split(":", 1)[1].split()[0])
+            except ValueError:
+                return None
+    return None
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": smax, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def time_steps(sim, torch, K):
+    """Device time of K steps on the library's stream (CUDA events), ms per step."""
+    st = sim.torch_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sim.sync()
+    torch.cuda.synchronize()
+    e0.record(st)
+    sim.step(K)
+    e1.record(st)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / K
+
+
+def cpu_oracle_rate(n, budget_s=12.0, max_steps=None):
+    """Oracle site updates per second on a bounded sample of the workload (1 thread)."""
+    from oracle import oracle as O
+    O.build()
+    p = O.default_params((n, n, n), R=n / 4.0, p0=n / 4.0, zeta=0.005)
+    s = O.State((n, n, n), p, seed=1)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        s.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_steps and steps >= max_steps):
+            break
+    return n ** 3 * steps / el, steps, el
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle, as it stands, on this host's cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    from oracle import oracle as O
+    O.build()
+    K, W = args.steps, args.warmup
+    # each step is one oracle step on the largest droplet box (same workload family,
+    # R = n/4, pitch n/4) whose K + W steps fit in about two minutes
+    rate_probe, _, _ = cpu_oracle_rate(32, budget_s=1.0)
+    n = 32
+    for cand in (128, 96, 64, 48, 32):
+        if cand ** 3 * (K + W) / rate_probe <= 120.0:
+            n = cand
+            break
+    p = O.default_params((n, n, n), R=n / 4.0, p0=n / 4.0, zeta=0.005)
+    s = O.State((n, n, n), p, seed=1)
+    s.step(W)
+    t0 = time.perf_counter()
+    s.step(K)
+    el = time.perf_counter() - t0
+    mlups = n ** 3 * K / el / 1e6
+    sample = "oracle FP64 single-thread, %d^3 droplet (R=%d, pitch %d), %d timed steps after %d warm-up" % (
+        n, n // 4, n // 4, K, W)
+    line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": 1, "steps": K,
+            "warmup": W, "ms_per_step": el / K * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "active cholesteric droplet %d^3 (CPU sample of 128^3, R=32, pitch 32)" % n,
+                       "box": [n, n, n]},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="lbcad", choices=["lbcad", "reference"])
+    ap.add_argument("--size", type=int, default=128)
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2011_00287_gb300 as L
+    from paper_2011_00287_gb300 import build as B
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    B.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    n = args.size
+    N = n ** 3
+    K, W = args.steps, args.warmup
+    # replicas: each rank advances its own copy of the workload (weak scaling)
+    sim = L.Simulation([(n, n, n)], [workload_params(L, n, L.FP32)], seed=1 + rank, device=local)
+    sim.step(W)
+    sim.sync()
+    if dist:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        ms = time_steps(sim, torch, K)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    obs = sim.observables(0)
+    finite = all(math.isfinite(v) for v in obs)
+    value = world * N / (ms * 1e-3) / 1e6
+
+    # plain FP64 GPU path on the same workload
+    fp64 = None
+    if not args.no_fp64:
+        s64 = L.Simulation([(n, n, n)], [workload_params(L, n, L.FP64)], seed=1 + rank, device=local)
+        s64.step(3)
+        ms64 = time_steps(s64, torch, args.fp64_steps)
+        fp64 = {"mlups": N / (ms64 * 1e-3) / 1e6, "ms_per_step": ms64, "steps": args.fp64_steps}
+        s64.close()
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        mask = L.FIELD_G | L.FIELD_U | L.FIELD_Q | L.FIELD_PSI
+        host = torch.empty(28 * N, dtype=torch.float64).pin_memory()
+        got = sim.get_fields(0, mask, out=host)
+        state = {k: v for k, v in got.items()}
+        state_np = {k: v.numpy().copy() for k, v in state.items()}
+        pinned_in = torch.empty(28 * N, dtype=torch.float64).pin_memory()
+        o = 0
+        for k, c in (("g", 19), ("u", 3), ("q", 5), ("psi", 1)):
+            pinned_in[o * N:(o + c) * N] = torch.from_numpy(state_np[k].reshape(-1))
+            o += c
+        lib = L.library()
+        import ctypes
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            rc = lib.lbcad_set_fields(sim.ctx, 0, mask, ctypes.c_void_p(pinned_in.data_ptr()), 28 * N * 8, 0)
+            assert rc == 0
+            sim.step(1)
+            rc = lib.lbcad_get_fields(sim.ctx, 0, mask, ctypes.c_void_p(host.data_ptr()), 28 * N * 8, 0)
+            assert rc == 0
+        el = time.perf_counter() - t0
+        e2e = {"value": N * args.e2e_steps / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 28 * N * 8,
+               "d2h_bytes_per_step": 28 * N * 8,
+               "note": "per step: full state (g, u, Q, psi as FP64) set from pinned host memory, one step, "
+                       "full state read back to pinned host memory"}
+
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_SITE["fp32"] * N / (ms * 1e-3) / 1e9
+    traffic_site = committed_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (traffic_site * N) if traffic_site else None,
+                "kernel": "hybrid step (k_fields + k_update)", "algorithmic_bytes_per_site": 200,
+                "peak_kind": peak_kind}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        rate, steps, el = cpu_oracle_rate(n, budget_s=12.0)
+        cpu = {"value": rate / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": "FP64 oracle, single thread, %d step(s) of the same %d^3 droplet workload (%.1f s)" % (
+                   steps, n, el)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "active cholesteric droplet 128^3, R=32, pitch 32, zeta=0.005, FP32 "
+                                       "shifted populations" if n == 128 else "droplet %d^3" % n,
+                           "box": [n, n, n], "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "state %.0f MB per step > 129 MB L2, no flush" % (224 * N / 1e6)},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": 2 * K, "clocks": clk.summary(), "fp64_gpu": fp64,
+                "speedup_fp32_vs_fp64": (value / world / fp64["mlups"]) if fp64 else None,
+                "observables_finite": finite}
+        print(json.dumps(line))
+    sim.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

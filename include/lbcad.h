@@ -1,0 +1,181 @@
+/* lbcad.h -- C ABI of the GB300 hybrid lattice-Boltzmann library for 3D active
+ * cholesteric droplets (Carenza, Gonnella & Negro, arXiv:2011.00287).
+ *
+ * One timestep ("hybrid step") advances, on a periodic nx*ny*nz lattice:
+ *   - the D3Q19 populations f_i by BGK collision with a body force and streaming
+ *     (Sec. 3, Eqs. 6-8; Eq. 7 read as BGK with Guo forcing, Eq. 9-11 read as a
+ *     second-order equilibrium with the whole stress divergence entering as the force);
+ *   - the tensor order parameter Q (traceless symmetric) by the Beris-Edwards equation
+ *     with advection and co-rotation (Sec. 2, Eq. 2);
+ *   - the concentration psi = phi - 1 by the Cahn-Hilliard equation (Sec. 2, Eq. 1);
+ * with the molecular field H, chemical potential mu and stresses derived from the free
+ * energy of Eq. 5 (Landau-de Gennes bulk, one-constant elasticity with the chiral q0 term,
+ * binary mixture, interface and anchoring terms) plus the active stress of Eq. 4.
+ *
+ * All work runs in CUDA kernels on one GPU.  Every call returns LBCAD_OK (0) or a
+ * negative LBCAD_E_* code; no C++ exception crosses this boundary.  After an error,
+ * lbcad_last_error(ctx) returns a message (valid until the next call on ctx).
+ *
+ * Field layout.  Every field is row-major [component][z][y][x] (x fastest) with
+ * n = nx*ny*nz sites per component.  Field masks select, in this order:
+ *   LBCAD_FIELD_G   19 components: pre-collision populations f_i at the current time,
+ *                   unshifted, in the D3Q19 order returned by lbcad_lattice();
+ *   LBCAD_FIELD_RHO  1 component : rho = sum_i f_i;
+ *   LBCAD_FIELD_U    3 components: the fluid velocity u computed in the last step
+ *                   ((sum_i f_i c_i + F/2)/rho of the previous time level; 0 at t = 0);
+ *   LBCAD_FIELD_Q    5 components: Q_xx, Q_xy, Q_xz, Q_yy, Q_yz (Q_zz = -Q_xx - Q_yy);
+ *   LBCAD_FIELD_PSI  1 component : psi.
+ * The exchange type is always double, whatever the compute precision.
+ */
+#ifndef LBCAD_H
+#define LBCAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define LBCAD_OK 0
+#define LBCAD_E_INVALID_ARG (-1) /* bad pointer, size, parameter or instance index       */
+#define LBCAD_E_OOM (-2)         /* device allocation failed                             */
+#define LBCAD_E_CUDA (-3)        /* a CUDA runtime call failed (message has the reason)  */
+#define LBCAD_E_TIMEOUT (-4)     /* a bounded device wait gave up                        */
+#define LBCAD_E_NAN (-5)         /* a non-finite value was found in a reduction          */
+#define LBCAD_E_UNSUPPORTED (-6) /* option not available on this path                    */
+
+/* ---- options --------------------------------------------------------------------- */
+#define LBCAD_FP32 0 /* FP32 storage and arithmetic; populations stored as f_i - w_i rho0 */
+#define LBCAD_FP64 1 /* FP64 storage and arithmetic; populations stored unshifted         */
+#define LBCAD_EULER 0
+#define LBCAD_HEUN 1   /* predictor-corrector of Sec. 3 (oracle only for now)             */
+#define LBCAD_LAGGED 0 /* Q and psi advected with u of the previous step                  */
+#define LBCAD_SYNC 1   /* advected with u of this step (oracle only for now)              */
+
+#define LBCAD_FIELD_G 1u
+#define LBCAD_FIELD_RHO 2u
+#define LBCAD_FIELD_U 4u
+#define LBCAD_FIELD_Q 8u
+#define LBCAD_FIELD_PSI 16u
+
+typedef struct {
+  int32_t nx, ny, nz; /* each >= 4; periodic */
+} lbcad_grid;
+
+/* Device allocator callbacks: alloc returns a device pointer aligned to >= 256 bytes or
+ * NULL; free releases it.  Both are called only from lbcad_create* / lbcad_destroy. */
+typedef void* (*lbcad_alloc_fn)(size_t bytes, void* user);
+typedef void (*lbcad_free_fn)(void* ptr, void* user);
+
+/* Parameters of Eqs. 1-11 for one droplet instance (lattice units, dx = dt = 1). */
+typedef struct {
+  double tau;      /* BGK relaxation time (Eq. 7); viscosity (tau - 1/2)/3          */
+  double rho0;     /* reference density                                              */
+  double A0;       /* Landau-de Gennes scale (Eq. 5)                                 */
+  double chi0;     /* chi(phi) = chi0 + chis * phi, phi = 1 + psi (Eq. 5)            */
+  double chis;
+  double K;        /* one-constant elastic modulus K_Q (Eq. 5)                       */
+  double q0;       /* cholesteric wave number 2 pi / pitch (Eq. 5)                   */
+  double gammaQ;   /* rotational mobility multiplying H (Eq. 2)                      */
+  double xi;       /* flow-alignment parameter of the co-rotation term (Eq. 2)      */
+  double a, b;     /* binary bulk -a psi^2/2 + b psi^4/4 (Eq. 5 with phi0 = 2)       */
+  double kphi;     /* interface stiffness k_phi (Eq. 5)                              */
+  double M;        /* Cahn-Hilliard mobility (Eq. 1)                                 */
+  double W;        /* anchoring strength (Eq. 5), W > 0 tangential                  */
+  double zeta;     /* activity (Eq. 4), > 0 extensile                                */
+  double R;        /* droplet radius for the initial state                           */
+  double centre[3];/* droplet centre (x, y, z) for the initial state                 */
+  double S0;       /* scalar order of the initial helix inside the droplet           */
+  double noise;    /* amplitude of the seeded uniform noise on Q inside the droplet  */
+  int32_t precision;  /* LBCAD_FP32 or LBCAD_FP64                                     */
+  int32_t integrator; /* LBCAD_EULER (LBCAD_HEUN returns LBCAD_E_UNSUPPORTED)          */
+  int32_t coupling;   /* LBCAD_LAGGED (LBCAD_SYNC returns LBCAD_E_UNSUPPORTED)         */
+  int32_t device;     /* CUDA device ordinal; -1 = the current device                 */
+  void* stream;       /* cudaStream_t for all work; NULL = a private non-blocking stream */
+  lbcad_alloc_fn alloc; /* NULL = cudaMalloc                                          */
+  lbcad_free_fn free;   /* NULL = cudaFree                                            */
+  void* alloc_user;
+} lbcad_params;
+
+/* FP64 conserved sums and centroid moments of one instance at the current time. */
+typedef struct {
+  double mass;       /* sum over sites of rho                                        */
+  double sum_psi;    /* sum of psi                                                   */
+  double mom[3];     /* sum over sites of sum_i f_i c_i (pre-collision)               */
+  double cm_cos[3];  /* sum of phi_c cos(2 pi x_a / L_a), phi_c = (1 + psi)/2        */
+  double cm_sin[3];  /* sum of phi_c sin(2 pi x_a / L_a)                              */
+  double sum_phic;   /* sum of phi_c                                                 */
+} lbcad_obs;
+
+typedef struct lbcad_ctx lbcad_ctx;
+
+/* The D3Q19 velocity order used by LBCAD_FIELD_G: c[3*i + a], weights w[i]. */
+int lbcad_lattice(int32_t* c57, double* w19);
+
+/* Create one instance: validates params, allocates its device state (through
+ * params->alloc when given), builds the initial state on the host in FP64 and copies it
+ * to the device once (the only host->device transfer).  Initial state: rho = rho0,
+ * u = 0, psi = tanh((R - r)/2) with r the distance of the integer site to centre;
+ * where r < R, Q = S0 (n n - I/3) + noise * U[-1,1) per stored component, with the
+ * helix n = (cos q0 (z - cz), sin q0 (z - cz), 0); elsewhere Q = 0.  The uniform
+ * variate for (seed, instance, site s, component c) is SplitMix64: output number
+ * k = 1 + (instance << 40) + 5 s + c of the stream started from `seed`, mapped to
+ * [-1, 1) as 2 (r >> 11) 2^-53 - 1.  On success *out owns the state; free it with
+ * lbcad_destroy. */
+int lbcad_create(const lbcad_grid* grid, const lbcad_params* params, uint64_t seed, lbcad_ctx** out);
+
+/* Create n independent instances (uneven boxes and parameters allowed) advanced
+ * together: every lbcad_step launch covers all of them.  grids[i], params[i] describe
+ * instance i; precision, device, stream and allocator are taken from params[0] and must
+ * agree across instances. */
+int lbcad_create_batch(int32_t n, const lbcad_grid* grids, const lbcad_params* params, uint64_t seed,
+                       lbcad_ctx** out);
+
+/* Advance every instance by n >= 0 hybrid steps on the context's stream.  Asynchronous:
+ * returns after enqueueing (errors of enqueued kernels surface at the next synchronising
+ * call).  With graphs enabled (lbcad_set_graph), the steps replay a captured CUDA graph. */
+int lbcad_step(lbcad_ctx* c, int64_t n);
+
+/* Capture steps in a CUDA graph of `steps_per_graph` steps (0 disables; default 0). */
+int lbcad_set_graph(lbcad_ctx* c, int32_t steps_per_graph);
+
+/* Copy the selected fields of instance `inst` to dst (FP64, layout above).  bytes must
+ * be >= 8 * n * (number of selected components).  dst is a host pointer (pageable or
+ * pinned) unless dst_is_device.  Synchronises the context's stream. */
+int lbcad_get_fields(lbcad_ctx* c, int32_t inst, uint32_t mask, void* dst, size_t bytes, int32_t dst_is_device);
+
+/* Overwrite the selected fields (G, U, Q, PSI; RHO is derived and rejected) of instance
+ * `inst` from src (FP64, same layout).  G gives the pre-collision populations at the
+ * current time.  Synchronises the context's stream. */
+int lbcad_set_fields(lbcad_ctx* c, int32_t inst, uint32_t mask, const void* src, size_t bytes,
+                     int32_t src_is_device);
+
+/* FP64 reductions (deterministic order) of instance `inst`.  Returns LBCAD_E_NAN when a
+ * reduced value is not finite.  Synchronises the context's stream. */
+int lbcad_observables(lbcad_ctx* c, int32_t inst, lbcad_obs* out);
+
+/* Number of instances, lattice of one instance, steps taken so far. */
+int lbcad_num_instances(const lbcad_ctx* c);
+int lbcad_instance_grid(const lbcad_ctx* c, int32_t inst, lbcad_grid* out);
+int64_t lbcad_step_count(const lbcad_ctx* c);
+
+/* The cudaStream_t all work of the context is enqueued on (created by the library,
+ * non-blocking, when params->stream was NULL). */
+void* lbcad_stream(const lbcad_ctx* c);
+
+/* Block until all enqueued work of the context has finished; reports kernel errors. */
+int lbcad_sync(lbcad_ctx* c);
+
+/* Release the context and its device memory.  NULL is a no-op. */
+void lbcad_destroy(lbcad_ctx* c);
+
+/* Message of the last error on c (or of the last failed create when c is NULL). */
+const char* lbcad_last_error(const lbcad_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBCAD_H */

@@ -1,0 +1,3 @@
+// FP32 instantiation: populations stored shifted by their rest weights, f_i - w_i rho0.
+#include "lbcad_kernels.cuh"
+template struct lbcad::Launch<float, true>;

@@ -1,0 +1,69 @@
+// lbcad_internal.h -- types shared by the host runtime and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbcad {
+
+// D3Q19 velocities (rest, six faces, twelve edges), the order published by
+// lbcad_lattice().  constexpr so that fully unrolled loops fold them to immediates.
+__host__ __device__ constexpr int lat_c(int i, int a) {
+  return a == 0 ? (i == 1 ? 1 : i == 2 ? -1 : i == 7 ? 1 : i == 8 ? -1 : i == 9 ? 1 : i == 10 ? -1
+                   : i == 11 ? 1 : i == 12 ? -1 : i == 13 ? 1 : i == 14 ? -1 : 0)
+       : a == 1 ? (i == 3 ? 1 : i == 4 ? -1 : i == 7 ? 1 : i == 8 ? -1 : i == 9 ? -1 : i == 10 ? 1
+                   : i == 15 ? 1 : i == 16 ? -1 : i == 17 ? 1 : i == 18 ? -1 : 0)
+                : (i == 5 ? 1 : i == 6 ? -1 : i == 11 ? 1 : i == 12 ? -1 : i == 13 ? -1 : i == 14 ? 1
+                   : i == 15 ? 1 : i == 16 ? -1 : i == 17 ? -1 : i == 18 ? 1 : 0);
+}
+// |c_i|^2: 0 rest, 1 face, 2 edge.
+__host__ __device__ constexpr int lat_c2(int i) {
+  return lat_c(i, 0) * lat_c(i, 0) + lat_c(i, 1) * lat_c(i, 1) + lat_c(i, 2) * lat_c(i, 2);
+}
+__host__ __device__ constexpr double lat_w(int i) {
+  return lat_c2(i) == 0 ? 1.0 / 3.0 : lat_c2(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0;
+}
+
+// Per-instance coefficients in the compute type.
+template <typename T>
+struct Coef {
+  T tau_inv, guo, rho0;
+  T A0, chi0, chis, K, q0, gammaQ, xi, a, b, kphi, M, W, zeta;
+};
+
+// One instance of a launch: lattice, state buffers of this step parity, scratch.
+template <typename T>
+struct InstDesc {
+  int nx, ny, nz, pad;
+  long long N;
+  long long blk0;  // first block of this instance in per-site launches
+  long long nblk;  // number of blocks of this instance
+  const T* g_in;   // post-collision populations of the previous step [19][N]
+  T* g_out;
+  const T* q_in;   // [5][N]
+  T* q_out;
+  const T* psi_in; // [N]
+  T* psi_out;
+  const T* u_in;   // velocity of the previous step [3][N]
+  T* u_out;
+  T* sig;          // scratch: stress [9][N]
+  T* mu;           // scratch: chemical potential [N]
+  T* H;            // scratch: molecular field [5][N]
+  Coef<T> c;
+};
+
+// Launchers implemented per precision (lbcad_kernels_f32.cu / _f64.cu).
+template <typename T, bool SHIFT>
+struct Launch {
+  static cudaError_t step(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, cudaStream_t s);
+  static cudaError_t get_fields(const InstDesc<T>& I, uint32_t mask, double* dst, cudaStream_t s);
+  static cudaError_t set_fields(const InstDesc<T>& I, uint32_t mask, const double* src, T* g_target,
+                                T* q_target, T* psi_target, T* u_target, cudaStream_t s);
+  static cudaError_t observables(const InstDesc<T>& I, double* partial, int nblocks, double* out, cudaStream_t s);
+};
+
+constexpr int kStepBlock = 256;
+constexpr int kObsBlock = 256;
+constexpr int kObsMaxBlocks = 1024;
+
+}  // namespace lbcad

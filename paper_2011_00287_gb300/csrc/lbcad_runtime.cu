@@ -1,0 +1,535 @@
+// lbcad_runtime.cu -- host runtime behind the C ABI of include/lbcad.h: parameter
+// validation, device memory pool, the seeded initial state, the step loop (optionally
+// replayed from a captured CUDA graph), field exchange and FP64 observables.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbcad.h"
+#include "lbcad_internal.h"
+
+using namespace lbcad;
+
+namespace {
+
+thread_local std::string g_create_err;
+
+struct Inst {
+  lbcad_grid g;
+  lbcad_params p;
+  long long N = 0;
+  void* gb[2] = {nullptr, nullptr};  // populations, parity 0/1
+  void* qb[2] = {nullptr, nullptr};
+  void* pb[2] = {nullptr, nullptr};
+  void* ub[2] = {nullptr, nullptr};
+  void* sig = nullptr;
+  void* mu = nullptr;
+  void* H = nullptr;
+  long long blk0 = 0, nblk = 0;
+};
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (dev >= 0 && dev != prev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct lbcad_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int prec = LBCAD_FP32;
+  lbcad_alloc_fn alloc = nullptr;
+  lbcad_free_fn free = nullptr;
+  void* user = nullptr;
+  std::vector<Inst> inst;
+  std::vector<void*> allocs;
+  void* desc[2] = {nullptr, nullptr};
+  long long total_blocks = 0;
+  int64_t step = 0;
+  int graph_steps = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  double* obs_partial = nullptr;
+  double* obs_out = nullptr;
+  double* staging = nullptr;
+  size_t staging_bytes = 0;
+  std::string err;
+  size_t elem() const { return prec == LBCAD_FP64 ? sizeof(double) : sizeof(float); }
+};
+
+namespace {
+
+int fail(lbcad_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg; else g_create_err = msg;
+  return code;
+}
+
+#define CK(ctx, call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail((ctx), LBCAD_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+void* dev_alloc(lbcad_ctx* c, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = nullptr;
+  if (c->alloc) {
+    p = c->alloc(bytes, c->user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) c->allocs.push_back(p);
+  return p;
+}
+
+void release(lbcad_ctx* c) {
+  if (!c) return;
+  DeviceGuard dg(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  for (void* p : c->allocs) {
+    if (c->free) c->free(p, c->user); else cudaFree(p);
+  }
+  c->allocs.clear();
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+bool finite_params(const lbcad_params& p) {
+  const double v[] = {p.tau, p.rho0, p.A0, p.chi0, p.chis, p.K, p.q0, p.gammaQ, p.xi, p.a, p.b, p.kphi,
+                      p.M, p.W, p.zeta, p.R, p.centre[0], p.centre[1], p.centre[2], p.S0, p.noise};
+  for (double x : v)
+    if (!std::isfinite(x)) return false;
+  return true;
+}
+
+std::string validate(const lbcad_grid& g, const lbcad_params& p) {
+  if (g.nx < 4 || g.ny < 4 || g.nz < 4) return "grid: every edge must be >= 4";
+  if ((long long)g.nx * g.ny * g.nz > (1LL << 31)) return "grid: more than 2^31 sites";
+  if (!finite_params(p)) return "params: non-finite value";
+  if (!(p.tau > 0.5)) return "params: tau must be > 1/2";
+  if (!(p.rho0 > 0.0)) return "params: rho0 must be > 0";
+  if (p.precision != LBCAD_FP32 && p.precision != LBCAD_FP64) return "params: precision must be FP32 or FP64";
+  if (p.integrator != LBCAD_EULER && p.integrator != LBCAD_HEUN) return "params: unknown integrator";
+  if (p.coupling != LBCAD_LAGGED && p.coupling != LBCAD_SYNC) return "params: unknown coupling";
+  return "";
+}
+
+template <typename T>
+Coef<T> coefs(const lbcad_params& p) {
+  Coef<T> c;
+  c.tau_inv = (T)(1.0 / p.tau);
+  c.guo = (T)(1.0 - 0.5 / p.tau);
+  c.rho0 = (T)p.rho0;
+  c.A0 = (T)p.A0; c.chi0 = (T)p.chi0; c.chis = (T)p.chis; c.K = (T)p.K; c.q0 = (T)p.q0;
+  c.gammaQ = (T)p.gammaQ; c.xi = (T)p.xi; c.a = (T)p.a; c.b = (T)p.b; c.kphi = (T)p.kphi;
+  c.M = (T)p.M; c.W = (T)p.W; c.zeta = (T)p.zeta;
+  return c;
+}
+
+template <typename T>
+InstDesc<T> make_desc(const Inst& I, int parity) {
+  InstDesc<T> d;
+  std::memset(&d, 0, sizeof(d));
+  d.nx = I.g.nx; d.ny = I.g.ny; d.nz = I.g.nz;
+  d.N = I.N;
+  d.blk0 = I.blk0;
+  d.nblk = I.nblk;
+  const int a = parity, b = parity ^ 1;
+  d.g_in = (const T*)I.gb[a]; d.g_out = (T*)I.gb[b];
+  d.q_in = (const T*)I.qb[a]; d.q_out = (T*)I.qb[b];
+  d.psi_in = (const T*)I.pb[a]; d.psi_out = (T*)I.pb[b];
+  d.u_in = (const T*)I.ub[a]; d.u_out = (T*)I.ub[b];
+  d.sig = (T*)I.sig; d.mu = (T*)I.mu; d.H = (T*)I.H;
+  d.c = coefs<T>(I.p);
+  return d;
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): output number k of the stream started at seed.
+inline uint64_t splitmix64(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + k * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+inline double unit_noise(uint64_t seed, int inst, long long site, int comp) {
+  const uint64_t k = 1ULL + ((uint64_t)inst << 40) + 5ULL * (uint64_t)site + (uint64_t)comp;
+  return 2.0 * ((double)(splitmix64(seed, k) >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+
+// Seeded initial droplet in FP64 on the host: psi = tanh((R - r)/2); a cholesteric
+// helix about z of order S0 plus noise inside r < R; Q = 0 outside.
+void init_host(const lbcad_grid& g, const lbcad_params& p, uint64_t seed, int inst, std::vector<double>& q5,
+               std::vector<double>& psi) {
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  q5.assign(5 * N, 0.0);
+  psi.assign(N, 0.0);
+  for (int z = 0; z < g.nz; ++z)
+    for (int y = 0; y < g.ny; ++y)
+      for (int x = 0; x < g.nx; ++x) {
+        const long long s = x + (long long)g.nx * (y + (long long)g.ny * z);
+        const double dx = x - p.centre[0], dy = y - p.centre[1], dz = z - p.centre[2];
+        const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+        psi[s] = std::tanh((p.R - r) / 2.0);
+        if (r < p.R) {
+          const double n0 = std::cos(p.q0 * dz), n1 = std::sin(p.q0 * dz);
+          double Q[5] = {p.S0 * (n0 * n0 - 1.0 / 3.0), p.S0 * (n0 * n1), 0.0, p.S0 * (n1 * n1 - 1.0 / 3.0), 0.0};
+          for (int k = 0; k < 5; ++k) q5[k * N + s] = Q[k] + p.noise * unit_noise(seed, inst, s, k);
+        }
+      }
+}
+
+template <typename T>
+int upload_init(lbcad_ctx* c, Inst& I, uint64_t seed, int idx) {
+  std::vector<double> q5, psi;
+  init_host(I.g, I.p, seed, idx, q5, psi);
+  const long long N = I.N;
+  std::vector<T> tq(5 * N), tp(N);
+  for (long long k = 0; k < 5 * N; ++k) tq[k] = (T)q5[k];
+  for (long long k = 0; k < N; ++k) tp[k] = (T)psi[k];
+  const bool shifted = (c->prec == LBCAD_FP32);
+  std::vector<T> tg(19 * N);
+  for (int i = 0; i < 19; ++i) {
+    const T v = shifted ? T(0) : (T)(lat_w(i) * I.p.rho0);
+    for (long long s = 0; s < N; ++s) tg[i * N + s] = v;
+  }
+  CK(c, cudaMemcpyAsync(I.gb[0], tg.data(), 19 * N * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(I.qb[0], tq.data(), 5 * N * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(I.pb[0], tp.data(), N * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemsetAsync(I.ub[0], 0, 3 * N * sizeof(T), c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LBCAD_OK;
+}
+
+int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint64_t seed, lbcad_ctx** out) {
+  g_create_err.clear();
+  if (!out) return fail(nullptr, LBCAD_E_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !grids || !params) return fail(nullptr, LBCAD_E_INVALID_ARG, "need n >= 1 grids and params");
+  for (int i = 0; i < n; ++i) {
+    std::string v = validate(grids[i], params[i]);
+    if (!v.empty()) return fail(nullptr, LBCAD_E_INVALID_ARG, "instance " + std::to_string(i) + ": " + v);
+    if (params[i].precision != params[0].precision)
+      return fail(nullptr, LBCAD_E_INVALID_ARG, "all instances must share one precision");
+    if (params[i].integrator != LBCAD_EULER)
+      return fail(nullptr, LBCAD_E_UNSUPPORTED, "the GPU path implements the Euler integrator only");
+    if (params[i].coupling != LBCAD_LAGGED)
+      return fail(nullptr, LBCAD_E_UNSUPPORTED, "the GPU path implements lagged coupling only");
+  }
+  lbcad_ctx* c = new (std::nothrow) lbcad_ctx();
+  if (!c) return fail(nullptr, LBCAD_E_OOM, "host allocation failed");
+  const lbcad_params& p0 = params[0];
+  c->prec = p0.precision;
+  c->alloc = p0.alloc;
+  c->free = p0.free;
+  c->user = p0.alloc_user;
+  if ((c->alloc == nullptr) != (c->free == nullptr)) {
+    delete c;
+    return fail(nullptr, LBCAD_E_INVALID_ARG, "alloc and free callbacks must be given together");
+  }
+  if (p0.device >= 0) {
+    c->device = p0.device;
+  } else if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return fail(nullptr, LBCAD_E_CUDA, "no CUDA device");
+  }
+  DeviceGuard dg(c->device);
+  int code = LBCAD_OK;
+  auto bail = [&](int cd, const std::string& m) {
+    g_create_err = m.empty() ? c->err : m;
+    release(c);
+    delete c;
+    return cd;
+  };
+  if (p0.stream) {
+    c->stream = (cudaStream_t)p0.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(LBCAD_E_CUDA, "cudaStreamCreateWithFlags failed");
+    c->own_stream = true;
+  }
+  const size_t es = c->elem();
+  long long blk = 0;
+  long long maxN = 0;
+  c->inst.resize(n);
+  for (int i = 0; i < n; ++i) {
+    Inst& I = c->inst[i];
+    I.g = grids[i];
+    I.p = params[i];
+    I.N = (long long)I.g.nx * I.g.ny * I.g.nz;
+    maxN = I.N > maxN ? I.N : maxN;
+    I.blk0 = blk;
+    I.nblk = (I.N + kStepBlock - 1) / kStepBlock;
+    blk += I.nblk;
+    for (int par = 0; par < 2; ++par) {
+      I.gb[par] = dev_alloc(c, 19 * I.N * es);
+      I.qb[par] = dev_alloc(c, 5 * I.N * es);
+      I.pb[par] = dev_alloc(c, I.N * es);
+      I.ub[par] = dev_alloc(c, 3 * I.N * es);
+      if (!I.gb[par] || !I.qb[par] || !I.pb[par] || !I.ub[par]) return bail(LBCAD_E_OOM, "device allocation failed");
+    }
+    I.sig = dev_alloc(c, 9 * I.N * es);
+    I.mu = dev_alloc(c, I.N * es);
+    I.H = dev_alloc(c, 5 * I.N * es);
+    if (!I.sig || !I.mu || !I.H) return bail(LBCAD_E_OOM, "device allocation failed");
+  }
+  c->total_blocks = blk;
+  if (blk >= (1LL << 31)) return bail(LBCAD_E_INVALID_ARG, "too many blocks for one launch");
+  const size_t dsz = (c->prec == LBCAD_FP64 ? sizeof(InstDesc<double>) : sizeof(InstDesc<float>)) * n;
+  for (int par = 0; par < 2; ++par) {
+    c->desc[par] = dev_alloc(c, dsz);
+    if (!c->desc[par]) return bail(LBCAD_E_OOM, "device allocation failed");
+  }
+  c->obs_partial = (double*)dev_alloc(c, kObsMaxBlocks * 12 * sizeof(double));
+  c->obs_out = (double*)dev_alloc(c, 12 * sizeof(double));
+  if (!c->obs_partial || !c->obs_out) return bail(LBCAD_E_OOM, "device allocation failed");
+  for (int par = 0; par < 2; ++par) {
+    if (c->prec == LBCAD_FP64) {
+      std::vector<InstDesc<double>> h(n);
+      for (int i = 0; i < n; ++i) h[i] = make_desc<double>(c->inst[i], par);
+      if (cudaMemcpyAsync(c->desc[par], h.data(), dsz, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+          cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return bail(LBCAD_E_CUDA, "descriptor upload failed");
+    } else {
+      std::vector<InstDesc<float>> h(n);
+      for (int i = 0; i < n; ++i) h[i] = make_desc<float>(c->inst[i], par);
+      if (cudaMemcpyAsync(c->desc[par], h.data(), dsz, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+          cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return bail(LBCAD_E_CUDA, "descriptor upload failed");
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    code = (c->prec == LBCAD_FP64) ? upload_init<double>(c, c->inst[i], seed, i)
+                                   : upload_init<float>(c, c->inst[i], seed, i);
+    if (code != LBCAD_OK) return bail(code, "");
+  }
+  *out = c;
+  return LBCAD_OK;
+}
+
+int launch_steps(lbcad_ctx* c, int64_t n) {
+  for (int64_t k = 0; k < n; ++k) {
+    const int par = (int)(c->step & 1);
+    cudaError_t e;
+    if (c->prec == LBCAD_FP64)
+      e = Launch<double, false>::step((const InstDesc<double>*)c->desc[par], (int)c->inst.size(), c->total_blocks,
+                                      kStepBlock, c->stream);
+    else
+      e = Launch<float, true>::step((const InstDesc<float>*)c->desc[par], (int)c->inst.size(), c->total_blocks,
+                                    kStepBlock, c->stream);
+    if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
+    c->step++;
+  }
+  return LBCAD_OK;
+}
+
+template <typename T>
+InstDesc<T> desc_now(const lbcad_ctx* c, int inst) {
+  return make_desc<T>(c->inst[inst], (int)(c->step & 1));
+}
+
+int ensure_staging(lbcad_ctx* c, size_t bytes) {
+  if (c->staging_bytes >= bytes) return LBCAD_OK;
+  // the old buffer stays in the pool until destroy; staging only grows
+  void* p = dev_alloc(c, bytes);
+  if (!p) return fail(c, LBCAD_E_OOM, "staging allocation failed");
+  c->staging = (double*)p;
+  c->staging_bytes = bytes;
+  return LBCAD_OK;
+}
+
+int ncomp_of(uint32_t mask) {
+  return ((mask & LBCAD_FIELD_G) ? 19 : 0) + ((mask & LBCAD_FIELD_RHO) ? 1 : 0) + ((mask & LBCAD_FIELD_U) ? 3 : 0) +
+         ((mask & LBCAD_FIELD_Q) ? 5 : 0) + ((mask & LBCAD_FIELD_PSI) ? 1 : 0);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbcad_lattice(int32_t* c57, double* w19) {
+  if (!c57 || !w19) return LBCAD_E_INVALID_ARG;
+  for (int i = 0; i < 19; ++i) {
+    for (int a = 0; a < 3; ++a) c57[3 * i + a] = lat_c(i, a);
+    w19[i] = lat_w(i);
+  }
+  return LBCAD_OK;
+}
+
+int lbcad_create(const lbcad_grid* grid, const lbcad_params* params, uint64_t seed, lbcad_ctx** out) {
+  return create_impl(1, grid, params, seed, out);
+}
+
+int lbcad_create_batch(int32_t n, const lbcad_grid* grids, const lbcad_params* params, uint64_t seed,
+                       lbcad_ctx** out) {
+  return create_impl(n, grids, params, seed, out);
+}
+
+int lbcad_set_graph(lbcad_ctx* c, int32_t steps_per_graph) {
+  if (!c || steps_per_graph < 0) return LBCAD_E_INVALID_ARG;
+  DeviceGuard dg(c->device);
+  if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+  if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  c->graph_steps = steps_per_graph + (steps_per_graph & 1);  // even: parity is unchanged by a replay
+  return LBCAD_OK;
+}
+
+int lbcad_step(lbcad_ctx* c, int64_t n) {
+  if (!c || n < 0) return LBCAD_E_INVALID_ARG;
+  DeviceGuard dg(c->device);
+  int64_t left = n;
+  if (c->graph_steps > 0) {
+    if ((c->step & 1) && left > 0) {
+      int r = launch_steps(c, 1);
+      if (r) return r;
+      left--;
+    }
+    while (left >= c->graph_steps) {
+      if (!c->gexec) {
+        const int64_t step0 = c->step;
+        CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        int r = launch_steps(c, c->graph_steps);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        c->step = step0;
+        if (r) { if (g) cudaGraphDestroy(g); return r; }
+        if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        c->graph = g;
+        CK(c, cudaGraphInstantiate(&c->gexec, c->graph, 0));
+      }
+      CK(c, cudaGraphLaunch(c->gexec, c->stream));
+      c->step += c->graph_steps;
+      left -= c->graph_steps;
+    }
+  }
+  return launch_steps(c, left);
+}
+
+int lbcad_get_fields(lbcad_ctx* c, int32_t inst, uint32_t mask, void* dst, size_t bytes, int32_t dst_is_device) {
+  if (!c) return LBCAD_E_INVALID_ARG;
+  if (inst < 0 || inst >= (int)c->inst.size()) return fail(c, LBCAD_E_INVALID_ARG, "instance out of range");
+  if (!dst || mask == 0 || (mask & ~31u)) return fail(c, LBCAD_E_INVALID_ARG, "bad dst or mask");
+  const long long N = c->inst[inst].N;
+  const size_t need = (size_t)ncomp_of(mask) * N * sizeof(double);
+  if (bytes < need) return fail(c, LBCAD_E_INVALID_ARG, "dst too small");
+  DeviceGuard dg(c->device);
+  double* target = (double*)dst;
+  if (!dst_is_device) {
+    int r = ensure_staging(c, need);
+    if (r) return r;
+    target = c->staging;
+  }
+  cudaError_t e = (c->prec == LBCAD_FP64)
+                      ? Launch<double, false>::get_fields(desc_now<double>(c, inst), mask, target, c->stream)
+                      : Launch<float, true>::get_fields(desc_now<float>(c, inst), mask, target, c->stream);
+  if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("get_fields: ") + cudaGetErrorString(e));
+  if (!dst_is_device) CK(c, cudaMemcpyAsync(dst, target, need, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LBCAD_OK;
+}
+
+int lbcad_set_fields(lbcad_ctx* c, int32_t inst, uint32_t mask, const void* src, size_t bytes,
+                     int32_t src_is_device) {
+  if (!c) return LBCAD_E_INVALID_ARG;
+  if (inst < 0 || inst >= (int)c->inst.size()) return fail(c, LBCAD_E_INVALID_ARG, "instance out of range");
+  if (!src || mask == 0 || (mask & ~31u) || (mask & LBCAD_FIELD_RHO))
+    return fail(c, LBCAD_E_INVALID_ARG, "bad src or mask (RHO cannot be set)");
+  const long long N = c->inst[inst].N;
+  const size_t need = (size_t)ncomp_of(mask) * N * sizeof(double);
+  if (bytes < need) return fail(c, LBCAD_E_INVALID_ARG, "src too small");
+  DeviceGuard dg(c->device);
+  const double* from = (const double*)src;
+  if (!src_is_device) {
+    int r = ensure_staging(c, need);
+    if (r) return r;
+    CK(c, cudaMemcpyAsync(c->staging, src, need, cudaMemcpyHostToDevice, c->stream));
+    from = c->staging;
+  }
+  Inst& I = c->inst[inst];
+  const int par = (int)(c->step & 1);
+  cudaError_t e;
+  if (c->prec == LBCAD_FP64)
+    e = Launch<double, false>::set_fields(desc_now<double>(c, inst), mask, from, (double*)I.gb[par],
+                                          (double*)I.qb[par], (double*)I.pb[par], (double*)I.ub[par], c->stream);
+  else
+    e = Launch<float, true>::set_fields(desc_now<float>(c, inst), mask, from, (float*)I.gb[par], (float*)I.qb[par],
+                                        (float*)I.pb[par], (float*)I.ub[par], c->stream);
+  if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("set_fields: ") + cudaGetErrorString(e));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LBCAD_OK;
+}
+
+int lbcad_observables(lbcad_ctx* c, int32_t inst, lbcad_obs* out) {
+  if (!c || !out) return LBCAD_E_INVALID_ARG;
+  if (inst < 0 || inst >= (int)c->inst.size()) return fail(c, LBCAD_E_INVALID_ARG, "instance out of range");
+  DeviceGuard dg(c->device);
+  const long long N = c->inst[inst].N;
+  long long nb = (N + kObsBlock - 1) / kObsBlock;
+  if (nb > kObsMaxBlocks) nb = kObsMaxBlocks;
+  cudaError_t e = (c->prec == LBCAD_FP64)
+                      ? Launch<double, false>::observables(desc_now<double>(c, inst), c->obs_partial, (int)nb,
+                                                           c->obs_out, c->stream)
+                      : Launch<float, true>::observables(desc_now<float>(c, inst), c->obs_partial, (int)nb,
+                                                         c->obs_out, c->stream);
+  if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("observables: ") + cudaGetErrorString(e));
+  double h[12];
+  CK(c, cudaMemcpyAsync(h, c->obs_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  out->mass = h[0];
+  out->sum_psi = h[1];
+  for (int a = 0; a < 3; ++a) {
+    out->mom[a] = h[2 + a];
+    out->cm_cos[a] = h[5 + a];
+    out->cm_sin[a] = h[8 + a];
+  }
+  out->sum_phic = h[11];
+  for (double v : h)
+    if (!std::isfinite(v)) return fail(c, LBCAD_E_NAN, "non-finite value in observables");
+  return LBCAD_OK;
+}
+
+int lbcad_num_instances(const lbcad_ctx* c) { return c ? (int)c->inst.size() : 0; }
+
+int lbcad_instance_grid(const lbcad_ctx* c, int32_t inst, lbcad_grid* out) {
+  if (!c || !out || inst < 0 || inst >= (int)c->inst.size()) return LBCAD_E_INVALID_ARG;
+  *out = c->inst[inst].g;
+  return LBCAD_OK;
+}
+
+int64_t lbcad_step_count(const lbcad_ctx* c) { return c ? c->step : -1; }
+
+void* lbcad_stream(const lbcad_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+int lbcad_sync(lbcad_ctx* c) {
+  if (!c) return LBCAD_E_INVALID_ARG;
+  DeviceGuard dg(c->device);
+  CK(c, cudaStreamSynchronize(c->stream));
+  CK(c, cudaGetLastError());
+  return LBCAD_OK;
+}
+
+void lbcad_destroy(lbcad_ctx* c) {
+  if (!c) return;
+  release(c);
+  delete c;
+}
+
+const char* lbcad_last_error(const lbcad_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+"""Host-side checks of the C ABI (no GPU): the library builds, loads, exports every
+symbol include/lbcad.h declares, and rejects bad arguments before touching a device."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+from paper_2011_00287_gb300 import build as B
+from paper_2011_00287_gb300 import lbcad as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.library()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "lbcad.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbcad_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_signatures():
+    assert set(declared_symbols()) == set(L._SIGS), (declared_symbols(), sorted(L._SIGS))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_lattice_table(lib):
+    c, w = L.lattice()
+    assert c.shape == (19, 3) and abs(w.sum() - 1.0) < 1e-15
+    # isotropy: sum w c c = I/3, and the table holds each D3Q19 velocity once
+    import numpy as np
+    assert np.allclose((w[:, None, None] * c[:, :, None] * c[:, None, :]).sum(0), np.eye(3) / 3)
+    assert len({tuple(v) for v in c}) == 19
+
+
+def _create(lib, grid, **kw):
+    p = L._fill_params(L.default_params(grid, **kw), None, 0, None)
+    g = L.lbcad_grid(*grid)
+    ctx = ctypes.c_void_p()
+    code = lib.lbcad_create(ctypes.byref(g), ctypes.byref(p), 1, ctypes.byref(ctx))
+    return code, lib.lbcad_last_error(None).decode()
+
+
+@pytest.mark.parametrize("grid,kw,code", [
+    ((3, 8, 8), {}, L.LBCAD_E_INVALID_ARG),
+    ((8, 8, 8), dict(tau=0.5), L.LBCAD_E_INVALID_ARG),
+    ((8, 8, 8), dict(rho0=-1.0), L.LBCAD_E_INVALID_ARG),
+    ((8, 8, 8), dict(zeta=math.nan), L.LBCAD_E_INVALID_ARG),
+    ((8, 8, 8), dict(precision=7), L.LBCAD_E_INVALID_ARG),
+    ((8, 8, 8), dict(integrator=L.HEUN), L.LBCAD_E_UNSUPPORTED),
+    ((8, 8, 8), dict(coupling=L.SYNC), L.LBCAD_E_UNSUPPORTED),
+])
+def test_create_rejects_bad_arguments_on_the_host(lib, grid, kw, code):
+    got, msg = _create(lib, grid, **kw)
+    assert got == code and msg
+
+
+def test_null_arguments(lib):
+    assert lib.lbcad_step(None, 1) == L.LBCAD_E_INVALID_ARG
+    assert lib.lbcad_sync(None) == L.LBCAD_E_INVALID_ARG
+    assert lib.lbcad_num_instances(None) == 0
+    assert lib.lbcad_step_count(None) == -1
+    lib.lbcad_destroy(None)
+    assert lib.lbcad_lattice(None, None) == L.LBCAD_E_INVALID_ARG

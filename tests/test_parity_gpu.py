@@ -1,0 +1,218 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances: the FP64 GPU path within 1e-12 max abs per field after 10 steps; the FP32
+path (populations shifted by w_i rho0) within 1e-5 relative L2 per field after 100
+steps.  Populations are compared shifted (f_i - w_i rho0), which is the stricter test.
+"""
+import numpy as np
+import pytest
+
+import paper_2011_00287_gb300 as L
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2011_00287_gb300 import build as B
+    B.build()
+    O.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _perm():
+    """Index map from the library's D3Q19 order to the oracle's."""
+    cl, _ = L.lattice()
+    co, _ = O.lattice()
+    return np.array([int(np.where((co == v).all(1))[0][0]) for v in cl])
+
+
+def _oracle(shape, seed=1, inst=0, **kw):
+    return O.State(shape, O.default_params(shape, **kw), seed=seed, inst=inst)
+
+
+def _lib_params(shape, prec, **kw):
+    return L.default_params(shape, precision=prec, **kw)
+
+
+def _shifted(f):
+    _, w = O.lattice()
+    return f - w.reshape(19, 1, 1, 1)
+
+
+def _compare_fp64(got, ref, tol=1e-12):
+    perm = _perm()
+    errs = {
+        "g": np.abs(got["g"] - ref.f[perm]).max(),
+        "q": np.abs(got["q"] - ref.q).max(),
+        "psi": np.abs(got["psi"] - ref.psi).max(),
+        "u": np.abs(got["u"] - ref.u).max(),
+    }
+    for k, e in errs.items():
+        assert e <= tol, errs
+    return errs
+
+
+def _rel_l2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _compare_fp32(got, ref, tol=1e-5):
+    perm = _perm()
+    errs = {
+        "g": _rel_l2(_shifted(got["g"]), _shifted(ref.f)[perm]),
+        "q": _rel_l2(got["q"], ref.q),
+        "psi": _rel_l2(got["psi"], ref.psi),
+        "u": _rel_l2(got["u"], ref.u),
+    }
+    for k, e in errs.items():
+        assert e <= tol, errs
+    return errs
+
+
+KW0 = dict(R=8.0, p0=16.0)  # droplet R = 8, pitch 16 in a 32^3 box
+
+
+@pytest.mark.parametrize("prec", [L.FP64, L.FP32])
+def test_initial_state_matches_oracle(prec):
+    shape = (32, 32, 32)
+    sim = L.Simulation([shape], [_lib_params(shape, prec, **KW0)], seed=3)
+    got = sim.get_fields(0, L.FIELD_G | L.FIELD_RHO | L.FIELD_U | L.FIELD_Q | L.FIELD_PSI)
+    ref = _oracle(shape, seed=3, **KW0)
+    if prec == L.FP64:
+        assert np.array_equal(got["q"], ref.q) and np.array_equal(got["psi"], ref.psi)
+        assert np.array_equal(got["g"], ref.f[_perm()])
+    else:
+        assert np.array_equal(got["q"], ref.q.astype(np.float32).astype(np.float64))
+        assert np.array_equal(got["psi"], ref.psi.astype(np.float32).astype(np.float64))
+        assert np.abs(got["g"] - ref.f[_perm()]).max() < 1e-16 + 1e-7
+    assert np.all(got["u"] == 0.0)
+    np.testing.assert_allclose(got["rho"], 1.0, atol=1e-15)
+
+
+@pytest.mark.parametrize("shape,kw", [
+    ((32, 32, 32), KW0),
+    ((21, 13, 10), dict(R=4.0, p0=8.0, zeta=0.01, W=0.05)),   # ragged, non-cubic, odd edges
+    ((4, 5, 6), dict(R=2.0, p0=6.0)),                           # minimum edges: everything wraps
+])
+def test_fp64_parity_10_steps(shape, kw):
+    sim = L.Simulation([shape], [_lib_params(shape, L.FP64, **kw)], seed=2)
+    sim.step(10)
+    ref = _oracle(shape, seed=2, **kw).step(10)
+    _compare_fp64(sim.get_fields(0), ref)
+
+
+def test_fp32_parity_100_steps():
+    shape = (32, 32, 32)
+    sim = L.Simulation([shape], [_lib_params(shape, L.FP32, **KW0)], seed=1)
+    sim.step(100)
+    ref = _oracle(shape, seed=1, **KW0).step(100)
+    errs = _compare_fp32(sim.get_fields(0), ref)
+    print("fp32 rel L2 after 100 steps:", errs)
+
+
+def test_observables_match_oracle():
+    shape = (24, 20, 16)
+    kw = dict(R=5.0, p0=8.0)
+    sim = L.Simulation([shape], [_lib_params(shape, L.FP64, **kw)], seed=4)
+    sim.step(7)
+    ref = _oracle(shape, seed=4, **kw).step(7)
+    got = sim.observables(0)
+    exp = ref.observables()
+    np.testing.assert_allclose(got, exp, rtol=1e-12, atol=1e-10)
+
+
+def test_batch_uneven_instances_match_separate_oracle_runs():
+    shapes = [(16, 12, 10), (12, 12, 12), (20, 8, 9)]
+    kws = [dict(R=3.0, p0=8.0, zeta=0.002), dict(R=3.0, p0=12.0, zeta=0.008), dict(R=2.5, p0=6.0, zeta=0.005)]
+    sim = L.Simulation(shapes, [_lib_params(s, L.FP64, **k) for s, k in zip(shapes, kws)], seed=9)
+    sim.step(6)
+    for i, (s, k) in enumerate(zip(shapes, kws)):
+        ref = _oracle(s, seed=9, inst=i, **k).step(6)
+        _compare_fp64(sim.get_fields(i), ref)
+
+
+def test_set_get_roundtrip_and_resume():
+    """set_fields of the oracle state, then stepping, reproduces the oracle (checkpoint
+    resume through the ABI)."""
+    shape = (16, 12, 10)
+    kw = dict(R=4.0, p0=8.0)
+    ref = _oracle(shape, seed=5, **kw).step(3)
+    sim = L.Simulation([shape], [_lib_params(shape, L.FP64, **kw)], seed=99)
+    perm = _perm()
+    inv = np.argsort(perm)
+    sim.set_fields(0, {"g": ref.f[perm], "u": ref.u, "q": ref.q, "psi": ref.psi})
+    got = sim.get_fields(0)
+    assert np.array_equal(got["g"], ref.f[perm]) and np.array_equal(got["q"], ref.q)
+    sim.step(4)
+    ref.step(4)
+    _compare_fp64(sim.get_fields(0), ref)
+    assert inv.shape == (19,)
+
+
+def test_graph_replay_is_bitwise_identical():
+    shape = (20, 16, 12)
+    kw = dict(R=4.0, p0=8.0)
+    a = L.Simulation([shape], [_lib_params(shape, L.FP32, **kw)], seed=6)
+    b = L.Simulation([shape], [_lib_params(shape, L.FP32, **kw)], seed=6)
+    b.set_graph(4)
+    a.step(11)
+    b.step(11)
+    fa, fb = a.get_fields(0), b.get_fields(0)
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    assert b.step_count == 11
+
+
+def test_fp32_conservation_at_bench_size():
+    """128^3, R = 32, p0 = 32 (the benchmarked workload): FP64 sums of mass, psi and
+    momentum are conserved by the FP32 step to float roundoff."""
+    shape = (128, 128, 128)
+    sim = L.Simulation([shape], [_lib_params(shape, L.FP32, R=32.0, p0=32.0)], seed=1)
+    o0 = sim.observables(0)
+    sim.step(20)
+    o1 = sim.observables(0)
+    N = 128 ** 3
+    assert abs(o1[0] - o0[0]) < 1e-6 * N * 1e-3
+    assert abs(o1[1] - o0[1]) < 1e-6 * N
+    assert np.abs(o1[2:5]).max() < 1e-6 * N * 1e-3
+
+
+def test_fp32_parity_at_bench_size_2_steps():
+    """Full-size parity: the 128^3 workload in the benchmarked launch configuration,
+    two steps, every field against the oracle."""
+    shape = (128, 128, 128)
+    kw = dict(R=32.0, p0=32.0)
+    sim = L.Simulation([shape], [_lib_params(shape, L.FP32, **kw)], seed=1)
+    sim.step(2)
+    ref = _oracle(shape, seed=1, **kw).step(2)
+    _compare_fp32(sim.get_fields(0), ref, tol=1e-5)
+
+
+def test_deterministic():
+    shape = (16, 16, 16)
+    kw = dict(R=4.0, p0=8.0)
+    outs = []
+    for _ in range(2):
+        s = L.Simulation([shape], [_lib_params(shape, L.FP32, **kw)], seed=8)
+        s.step(5)
+        outs.append((s.get_fields(0), s.observables(0)))
+    for k in outs[0][0]:
+        assert np.array_equal(outs[0][0][k], outs[1][0][k])
+    assert np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_invalid_instance_and_sizes_raise():
+    shape = (8, 8, 8)
+    sim = L.Simulation([shape], [_lib_params(shape, L.FP32)], seed=1)
+    with pytest.raises(L.LbcadError):
+        sim.get_fields(1)
+    with pytest.raises(L.LbcadError):
+        sim.observables(3)
+    lib = L.library()
+    import ctypes
+    buf = np.zeros(10)
+    assert lib.lbcad_get_fields(sim.ctx, 0, L.FIELD_Q, ctypes.c_void_p(buf.ctypes.data), buf.nbytes, 0) == \
+        L.lbcad.LBCAD_E_INVALID_ARG
