@@ -168,6 +168,39 @@ void* lbcad_stream(const lbcad_ctx* c);
 /* Block until all enqueued work of the context has finished; reports kernel errors. */
 int lbcad_sync(lbcad_ctx* c);
 
+/* ---- one step without any device allocation ------------------------------------- *
+ * The paper has no counterpart of this call; it serves callers that must not have a
+ * library allocate device memory (a host framework that owns all device memory through
+ * its own pool, or a loop that cannot take the synchronisation cudaMalloc/cudaFree may
+ * cause).  It advances ONE instance by ONE hybrid step with the two-kernel step and
+ * keeps that step's scratch (H, mu and sigma: 15 values per site) in a fixed static
+ * device array of LBCAD_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library
+ * holds until the process exits.  It calls no cudaMalloc or cudaFree and creates no
+ * stream.
+ *
+ * Buffers (device pointers, owned by the caller, in the library's storage layout,
+ * element type float for LBCAD_FP32 and double for LBCAD_FP64, each [component][z][y][x]):
+ *   g_in  [19][n]  post-collision populations of the previous step (FP32: f_i - w_i rho0;
+ *                  FP64: f_i), so the initial state at rest is 0 (FP32) or w_i rho0 (FP64);
+ *   q_in  [5][n], psi_in [n], u_in [3][n]: Q, psi and the velocity of the previous step;
+ *   g_out, q_out, psi_out, u_out: the same fields after the step (must not alias inputs).
+ * params supplies the physics, precision, device (-1 = current) and stream (NULL = the
+ * legacy default stream); integrator/coupling must be Euler/lagged; alloc callbacks are
+ * ignored.  Returns after enqueueing the work on that stream.
+ *
+ * Limits: 15 * round_up_256(n * element size) bytes must fit in the scratch array, i.e.
+ * up to 279,616 sites in FP32 (64^3 fits) and 139,808 in FP64; larger grids return
+ * LBCAD_E_INVALID_ARG with a message in lbcad_last_error(NULL).
+ * Sharing: every call on a device uses the same scratch and descriptor, so calls whose
+ * work overlaps on the GPU (different streams, or host threads) race and corrupt each
+ * other; serialise them.  The array keeps the last call's contents; nothing needs to
+ * start at zero because each call writes every scratch value before reading it.
+ * Set-up: the first call on a device looks up the device addresses of the static arrays
+ * with cudaGetSymbolAddress; make that first call before any stream capture. */
+#define LBCAD_NOALLOC_SCRATCH_BYTES (16u << 20)
+int lbcad_step_noalloc(const lbcad_grid* grid, const lbcad_params* params, const void* g_in, const void* q_in,
+                       const void* psi_in, const void* u_in, void* g_out, void* q_out, void* psi_out, void* u_out);
+
 /* Release the context and its device memory.  NULL is a no-op. */
 void lbcad_destroy(lbcad_ctx* c);
 

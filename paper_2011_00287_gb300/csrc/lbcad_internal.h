@@ -62,6 +62,9 @@ struct Launch {
   static cudaError_t observables(const InstDesc<T>& I, double* partial, int nblocks, double* out, cudaStream_t s);
 };
 
+// Sets the message that lbcad_last_error(NULL) returns on this thread.
+void set_thread_error(const char* msg);
+
 constexpr int kStepBlock = 256;
 constexpr int kObsBlock = 256;
 constexpr int kObsMaxBlocks = 1024;

@@ -46,6 +46,8 @@ struct DeviceGuard {
 
 }  // namespace
 
+void lbcad::set_thread_error(const char* msg) { g_create_err = msg ? msg : ""; }
+
 struct lbcad_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;

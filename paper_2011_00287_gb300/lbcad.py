@@ -82,6 +82,7 @@ _SIGS = {
     "lbcad_step_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "lbcad_stream": (ctypes.c_void_p, [ctypes.c_void_p]),
     "lbcad_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "lbcad_step_noalloc": (ctypes.c_int, [_P(lbcad_grid), _P(lbcad_params)] + [ctypes.c_void_p] * 8),
     "lbcad_destroy": (None, [ctypes.c_void_p]),
     "lbcad_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
 }
