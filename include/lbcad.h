@@ -138,6 +138,15 @@ int lbcad_create_batch(int32_t n, const lbcad_grid* grids, const lbcad_params* p
  * call).  With graphs enabled (lbcad_set_graph), the steps replay a captured CUDA graph. */
 int lbcad_step(lbcad_ctx* c, int64_t n);
 
+/* Kernel path of lbcad_step.  LBCAD_PATH_FUSED (default): one persistent kernel per
+ * step with shared-memory halo tiles.  LBCAD_PATH_TWO_KERNEL: a stencil kernel writing
+ * H, mu and sigma to a per-site scratch (allocated on the first switch, 15 values per
+ * site) and an update kernel; same arithmetic, kept as a cross-check.  Changing the path
+ * drops a captured graph. */
+#define LBCAD_PATH_FUSED 0
+#define LBCAD_PATH_TWO_KERNEL 1
+int lbcad_set_path(lbcad_ctx* c, int32_t path);
+
 /* Capture steps in a CUDA graph of `steps_per_graph` steps (0 disables; default 0). */
 int lbcad_set_graph(lbcad_ctx* c, int32_t steps_per_graph);
 

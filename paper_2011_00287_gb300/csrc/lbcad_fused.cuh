@@ -1,0 +1,289 @@
+// lbcad_fused.cuh -- the whole hybrid step in one persistent kernel.
+//
+// Each block owns a TX x TY column of the lattice and marches up z, keeping in shared
+// memory rings of planes:
+//   Q and psi with a halo of 2 (5 planes: z-1 .. z+3),
+//   sigma (9) and mu with a halo of 1 (3 planes: z-1 .. z+1),
+//   u of the previous step with a halo of 1 (4 planes: z-1 .. z+2),
+// and the molecular field H of the next output plane in registers.  Per output plane z:
+//   1. sigma phase: stencils, H, mu and sigma of plane z+1 on the tile plus a halo of 1
+//      (the halo sites are the only redundant work: (TX+2)(TY+2)/(TX TY)).  The halo
+//      sites take a second round on NHALO threads; the other threads meanwhile load the
+//      Q/psi plane z+3 and the u plane z+2 for the next iteration;
+//   2. output phase: F = div sigma, lap mu, grad u, upwind Q and psi, pull of the 19
+//      populations from global memory, BGK + Guo collision; store g, Q, psi, u.
+// Every global element of the state is read once per step from HBM and written once
+// (the design floor of 224 B per site in FP32); the halo re-reads of Q, psi and u hit L2.
+//
+// The grid is persistent: the flattened space of (tile column, z plane) work is split
+// evenly across the blocks, so load balance does not depend on the box shape and one
+// launch covers every instance of a batch.
+#pragma once
+
+#include "lbcad_kernels.cuh"
+
+namespace lbcad {
+
+template <typename T, int TX, int TY>
+struct FusedGeom {
+  static constexpr int NT = TX * TY;
+  static constexpr int QW = TX + 4, QH = TY + 4, QP = QW * QH;
+  static constexpr int SW = TX + 2, SH = TY + 2, SP = SW * SH;
+  static constexpr int QSLOT = 6 * QP, SSLOT = 10 * SP, USLOT = 3 * SP;
+  // rings: Q/psi planes z-1 .. z+3, sigma/mu planes z-1 .. z+1, u planes z-1 .. z+2
+  static constexpr int NQS = 5, NSS = 3, NUS = 4;
+  static constexpr size_t elems = (size_t)NQS * QSLOT + (size_t)NSS * SSLOT + (size_t)NUS * USLOT;
+  static constexpr size_t bytes = elems * sizeof(T) + (QW + QH) * sizeof(int);
+  static constexpr int NHALO = SP - NT;   // halo sites of the sigma phase (second round)
+  static constexpr int NLOAD = NT - NHALO;  // threads free to prefetch during that round
+  static_assert(NHALO > 0 && NHALO < NT, "halo sites must fit in one extra round");
+  static constexpr int QLD = (QP + NLOAD - 1) / NLOAD;  // Q sites each loader thread fetches
+  static constexpr int ULD = (SP + NLOAD - 1) / NLOAD;
+};
+
+__device__ __forceinline__ int wrapmod(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+template <typename T, int QW, int QP>
+struct SmemFieldsAcc {
+  const T* pl[3];  // centre of the Q/psi planes p-1, p, p+1
+  __device__ __forceinline__ T q(int k, int cx, int cy, int cz) const { return pl[cz + 1][k * QP + cy * QW + cx]; }
+  __device__ __forceinline__ T psi(int cx, int cy, int cz) const { return pl[cz + 1][5 * QP + cy * QW + cx]; }
+};
+
+template <typename T, int QW, int QP, int SW, int SP>
+struct SmemUpdateAcc {
+  const T* qpl[3];
+  const T* spl[3];
+  const T* upl[3];
+  __device__ __forceinline__ T q(int k, int cx, int cy, int cz) const { return qpl[cz + 1][k * QP + cy * QW + cx]; }
+  __device__ __forceinline__ T psi(int cx, int cy, int cz) const { return qpl[cz + 1][5 * QP + cy * QW + cx]; }
+  __device__ __forceinline__ T sig(int k, int cx, int cy, int cz) const { return spl[cz + 1][k * SP + cy * SW + cx]; }
+  __device__ __forceinline__ T mu(int cx, int cy, int cz) const { return spl[cz + 1][9 * SP + cy * SW + cx]; }
+  __device__ __forceinline__ T u(int a, int cx, int cy, int cz) const { return upl[cz + 1][a * SP + cy * SW + cx]; }
+};
+
+// Ring slots of plane p (p >= -2).
+__device__ __forceinline__ int qslot(int p) { return (p + 10) % 5; }
+__device__ __forceinline__ int sslot(int p) { return (p + 9) % 3; }
+__device__ __forceinline__ int uslot(int p) { return (p + 8) % 4; }
+
+template <typename T, bool SHIFT, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 2 : 1)
+    k_step_fused(const InstDesc<T>* __restrict__ D, const FusedTile* __restrict__ tiles, int ntiles,
+                 long long total) {
+  using G = FusedGeom<T, TX, TY>;
+  constexpr int QW = G::QW, QP = G::QP, SW = G::SW, SH = G::SH, SP = G::SP, NT = G::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sQ = reinterpret_cast<T*>(smem_raw);
+  T* sS = sQ + G::NQS * G::QSLOT;
+  T* sU = sS + G::NSS * G::SSLOT;
+  int* xmap = reinterpret_cast<int*>(sU + G::NUS * G::USLOT);  // global x of Q-tile column
+  int* ymap = xmap + QW;                                         // global y * nx of Q-tile row
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+
+  // this thread's halo site of the sigma phase (threads < NHALO)
+  int hx = 0, hy = 0;
+  if (tid < G::NHALO) {
+    if (tid < 2 * SW) {
+      hy = tid < SW ? 0 : SH - 1;
+      hx = tid < SW ? tid : tid - SW;
+    } else {
+      const int r = tid - 2 * SW;
+      hy = 1 + (r >> 1);
+      hx = (r & 1) ? SW - 1 : 0;
+    }
+  }
+  const int lt = tid - G::NHALO;  // loader index (threads >= NHALO)
+
+  const long long begin = (total * blockIdx.x) / gridDim.x;
+  const long long end = (total * (blockIdx.x + 1)) / gridDim.x;
+  long long it = begin;
+  while (it < end) {
+    int lo = 0, hi = ntiles - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tiles[mid].start <= it) lo = mid; else hi = mid - 1;
+    }
+    const FusedTile tl = tiles[lo];
+    const InstDesc<T>& I = D[tl.inst];
+    const int nx = I.nx, ny = I.ny, nz = I.nz;
+    const long long N = I.N;
+    const long long plane = (long long)nx * ny;
+    const int zb = (int)(it - tl.start);
+    const long long seg_end = end < tl.start + tl.nz ? end : tl.start + tl.nz;
+    const int ze = (int)(seg_end - tl.start);
+    it = seg_end;
+    const Coef<T> cf = I.c;
+    const T* __restrict__ qin = I.q_in;
+    const T* __restrict__ pin = I.psi_in;
+    const T* __restrict__ uin = I.u_in;
+    const T* __restrict__ gin = I.g_in;
+
+    __syncthreads();  // the previous segment is done with the shared tiles
+    for (int k = tid; k < QW; k += NT) xmap[k] = wrapmod(tl.x0 + k - 2, nx);
+    for (int k = tid; k < G::QH; k += NT) ymap[k] = wrapmod(tl.y0 + k - 2, ny) * nx;
+    __syncthreads();
+
+    // planes are loaded by a fixed set of tile positions per thread: their in-plane
+    // global offsets are computed once per segment
+    auto load_q_all = [&](int p) {  // every thread (prologue)
+      T* dst = sQ + qslot(p) * G::QSLOT;
+      const long long gz = (long long)wrapmod(p, nz) * plane;
+      for (int k = tid; k < QP; k += NT) {
+        const int ly = k / QW, lx = k - ly * QW;
+        const long long gs = gz + ymap[ly] + xmap[lx];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) dst[f * QP + k] = ld(qin + f * N + gs);
+        dst[5 * QP + k] = ld(pin + gs);
+      }
+    };
+    auto load_u_all = [&](int p) {
+      T* dst = sU + uslot(p) * G::USLOT;
+      const long long gz = (long long)wrapmod(p, nz) * plane;
+      for (int k = tid; k < SP; k += NT) {
+        const int sy = k / SW, sx = k - sy * SW;
+        const long long gs = gz + ymap[sy + 1] + xmap[sx + 1];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dst[a * SP + k] = ld(uin + a * N + gs);
+      }
+    };
+    int qoff[G::QLD], uoff[G::ULD];
+    if (lt >= 0) {
+#pragma unroll
+      for (int j = 0; j < G::QLD; ++j) {
+        const int k = lt + j * G::NLOAD;
+        if (k < QP) {
+          const int ly = k / QW, lx = k - ly * QW;
+          qoff[j] = ymap[ly] + xmap[lx];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < G::ULD; ++j) {
+        const int k = lt + j * G::NLOAD;
+        if (k < SP) {
+          const int sy = k / SW, sx = k - sy * SW;
+          uoff[j] = ymap[sy + 1] + xmap[sx + 1];
+        }
+      }
+    }
+    // prefetch by the loader threads: Q/psi plane pq and u plane pu
+    auto prefetch = [&](int pq, int pu) {
+      T* dq = sQ + qslot(pq) * G::QSLOT;
+      const long long gzq = (long long)wrapmod(pq, nz) * plane;
+#pragma unroll
+      for (int j = 0; j < G::QLD; ++j) {
+        const int k = lt + j * G::NLOAD;
+        if (k < QP) {
+          const long long gs = gzq + qoff[j];
+#pragma unroll
+          for (int f = 0; f < 5; ++f) dq[f * QP + k] = ld(qin + f * N + gs);
+          dq[5 * QP + k] = ld(pin + gs);
+        }
+      }
+      T* du = sU + uslot(pu) * G::USLOT;
+      const long long gzu = (long long)wrapmod(pu, nz) * plane;
+#pragma unroll
+      for (int j = 0; j < G::ULD; ++j) {
+        const int k = lt + j * G::NLOAD;
+        if (k < SP) {
+          const long long gs = gzu + uoff[j];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) du[a * SP + k] = ld(uin + a * N + gs);
+        }
+      }
+    };
+    // H, mu and sigma of plane p at sigma-tile site (sx, sy); returns H.
+    auto sigma_site = [&](int p, int sx, int sy, T H[5]) {
+      SmemFieldsAcc<T, QW, QP> acc;
+      const int qc = (sy + 1) * QW + (sx + 1);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) acc.pl[j] = sQ + qslot(p - 1 + j) * G::QSLOT + qc;
+      T q0[5], p0, dq[3][5], lapq[5], dp[3], lapp, hp[6];
+      gather_fields<T>(acc, q0, p0, dq, lapq, dp, lapp, hp);
+      T sig[9], mu;
+      local_fields<T>(cf, q0, p0, dq, lapq, dp, lapp, hp, H, mu, sig);
+      T* dst = sS + sslot(p) * G::SSLOT + sy * SW + sx;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) dst[k * SP] = sig[k];
+      dst[9 * SP] = mu;
+    };
+
+    load_q_all(zb - 2);
+    load_q_all(zb - 1);
+    load_q_all(zb);
+    load_u_all(zb - 1);
+    T Hc[5] = {T(0), T(0), T(0), T(0), T(0)};
+    for (int z = zb - 2; z < ze; ++z) {
+      __syncthreads();  // Q(z .. z+2) and u(z-1 .. z+1) resident; the previous output phase is done
+      // sigma phase for plane z+1: interior sites first (their H is kept for the next
+      // output plane), then the halo sites while the other threads prefetch
+      // Q(z+3) and u(z+2) into the slots of Q(z-2) and u(z-2)
+      T Hn[5];
+      sigma_site(z + 1, tx + 1, ty + 1, Hn);
+      if (tid < G::NHALO) {
+        T Hh[5];
+        sigma_site(z + 1, hx, hy, Hh);
+      } else {
+        prefetch(z + 3, z + 2);
+      }
+      __syncthreads();
+      if (z >= zb && tl.x0 + tx < nx && tl.y0 + ty < ny) {
+        SmemUpdateAcc<T, QW, QP, SW, SP> acc;
+        const int qc = (ty + 2) * QW + (tx + 2);
+        const int sc = (ty + 1) * SW + (tx + 1);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          acc.qpl[j] = sQ + qslot(z - 1 + j) * G::QSLOT + qc;
+          acc.spl[j] = sS + sslot(z - 1 + j) * G::SSLOT + sc;
+          acc.upl[j] = sU + uslot(z - 1 + j) * G::USLOT + sc;
+        }
+        T F[3], lapmu, Wg[3][3], q0[5], qf[6][5], p0, pf[6], u0[3], uf[6];
+        gather_update<T>(acc, F, lapmu, Wg, q0, qf, p0, pf, u0, uf);
+        const long long zo[3] = {(long long)wrapmod(z - 1, nz) * plane, (long long)z * plane,
+                                 (long long)wrapmod(z + 1, nz) * plane};
+        T g[19];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+          const int cx = lat_c(i, 0), cy = lat_c(i, 1), cz = lat_c(i, 2);
+          g[i] = ld(gin + i * N + zo[1 - cz] + ymap[ty + 2 - cy] + xmap[tx + 2 - cx]);
+        }
+        T qn[5], pn, u[3];
+        update_math<T, SHIFT>(cf, F, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hc, g, qn, pn, u);
+        const long long s = zo[1] + ymap[ty + 2] + xmap[tx + 2];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) I.q_out[k * N + s] = qn[k];
+        I.psi_out[s] = pn;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) I.g_out[i * N + s] = g[i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) I.u_out[a * N + s] = u[a];
+      }
+#pragma unroll
+      for (int k = 0; k < 5; ++k) Hc[k] = Hn[k];
+    }
+  }
+}
+
+template <typename T, bool SHIFT>
+cudaError_t LaunchFused<T, SHIFT>::step(const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles,
+                                        long long total, int grid, cudaStream_t s) {
+  using G = FusedGeom<T, kFusedTX, kFusedTY>;
+  k_step_fused<T, SHIFT, kFusedTX, kFusedTY><<<grid, G::NT, G::bytes, s>>>(d_desc, tiles, ntiles, total);
+  return cudaGetLastError();
+}
+
+template <typename T, bool SHIFT>
+cudaError_t LaunchFused<T, SHIFT>::prepare(int* blocks_per_sm, size_t* smem) {
+  using G = FusedGeom<T, kFusedTX, kFusedTY>;
+  auto k = k_step_fused<T, SHIFT, kFusedTX, kFusedTY>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::bytes);
+  if (e != cudaSuccess) return e;
+  *smem = G::bytes;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, G::NT, G::bytes);
+}
+
+}  // namespace lbcad

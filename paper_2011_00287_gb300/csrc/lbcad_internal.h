@@ -62,6 +62,24 @@ struct Launch {
   static cudaError_t observables(const InstDesc<T>& I, double* partial, int nblocks, double* out, cudaStream_t s);
 };
 
+// One xy tile column of the fused step: instance, tile origin, the instance's nz and the
+// first index of this column in the flattened (tile column, z plane) work space.
+struct FusedTile {
+  int inst, x0, y0, nz;
+  long long start;
+};
+
+constexpr int kFusedTX = 32;
+constexpr int kFusedTY = 8;
+
+// The fused one-kernel step (lbcad_fused.cuh).
+template <typename T, bool SHIFT>
+struct LaunchFused {
+  static cudaError_t step(const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles, long long total, int grid,
+                          cudaStream_t s);
+  static cudaError_t prepare(int* blocks_per_sm, size_t* smem_bytes);
+};
+
 // Sets the message that lbcad_last_error(NULL) returns on this thread.
 void set_thread_error(const char* msg);
 

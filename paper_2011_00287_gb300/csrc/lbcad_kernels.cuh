@@ -77,18 +77,19 @@ __device__ __forceinline__ void local_fields(const Coef<T>& c, const T q[5], T p
 #pragma unroll
   for (int a = 0; a < 3; ++a) full3(dq[a], dQ[a]);
   const T chi = c.chi0 + c.chis * (T(1) + psi);
+  // Q.Q is symmetric: six products
   T QQ[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) QQ[i][j] = Q[i][0] * Q[0][j] + Q[i][1] * Q[1][j] + Q[i][2] * Q[2][j];
+    for (int j = i; j < 3; ++j) {
+      QQ[i][j] = Q[i][0] * Q[0][j] + Q[i][1] * Q[1][j] + Q[i][2] * Q[2][j];
+      QQ[j][i] = QQ[i][j];
+    }
   const T trQ2 = QQ[0][0] + QQ[1][1] + QQ[2][2];
-  T trQ3 = T(0);
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) trQ3 += QQ[i][j] * Q[i][j];
-  // curl: C_ab = eps_amn d_m Q_nb
+  const T trQ3 = QQ[0][0] * Q[0][0] + QQ[1][1] * Q[1][1] + QQ[2][2] * Q[2][2] +
+                 T(2) * (QQ[0][1] * Q[0][1] + QQ[0][2] * Q[0][2] + QQ[1][2] * Q[1][2]);
+  // curl: C_ab = eps_amn d_m Q_nb, and its symmetric part CC = C + C^T
   T C[3][3];
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
@@ -96,63 +97,67 @@ __device__ __forceinline__ void local_fields(const Coef<T>& c, const T q[5], T p
     C[1][b] = dQ[2][0][b] - dQ[0][2][b];
     C[2][b] = dQ[0][1][b] - dQ[1][0][b];
   }
+  T CC[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      CC[i][j] = C[i][j] + C[j][i];
+      CC[j][i] = CC[i][j];
+    }
   const T g2 = dp[0] * dp[0] + dp[1] * dp[1] + dp[2] * dp[2];
-  const T lin = -c.A0 * (T(1) - chi / T(3)) - c.A0 * chi * trQ2 - T(4) * c.K * c.q0 * c.q0;
   const T Ac = c.A0 * chi;
   const T Kq = T(2) * c.K * c.q0;
-  // H = -dF/dQ, symmetric traceless by construction (C + C^T is traceless for symmetric Q)
+  const T lin = -c.A0 * (T(1) - chi / T(3)) - Ac * trQ2 - Kq * T(2) * c.q0;
+  const T iso = (Ac * trQ2 - c.W * g2) / T(3);
+  // H = -dF/dQ (traceless symmetric by construction: tr CC = 0 for symmetric Q)
   const int I5[5] = {0, 0, 0, 1, 1};
   const int J5[5] = {0, 1, 2, 1, 2};
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     const int i = I5[k], j = J5[k];
-    const T dij = (i == j) ? T(1) : T(0);
-    H[k] = lin * Q[i][j] + Ac * (QQ[i][j] - dij * trQ2 / T(3)) + c.K * lapq[k] - Kq * (C[i][j] + C[j][i]) -
-           c.W * (dp[i] * dp[j] - dij * g2 / T(3));
+    T h = lin * Q[i][j] + Ac * QQ[i][j] + c.K * lapq[k] - Kq * CC[i][j] - c.W * dp[i] * dp[j];
+    if (i == j) h -= iso;
+    H[k] = h;
   }
   T Hf[3][3];
   full3(H, Hf);
 
   // mu = dF/dpsi
-  T Qh = Q[0][0] * hp[0] + Q[1][1] * hp[1] + Q[2][2] * hp[2] +
-         T(2) * (Q[0][1] * hp[3] + Q[0][2] * hp[4] + Q[1][2] * hp[5]);
+  const T Qh = Q[0][0] * hp[0] + Q[1][1] * hp[1] + Q[2][2] * hp[2] +
+               T(2) * (Q[0][1] * hp[3] + Q[0][2] * hp[4] + Q[1][2] * hp[5]);
   T divQdp = T(0);
 #pragma unroll
   for (int b = 0; b < 3; ++b) divQdp += (dQ[0][0][b] + dQ[1][1][b] + dQ[2][2][b]) * dp[b];
-  mu = -c.a * psi + c.b * psi * psi * psi - c.kphi * lapp +
-       c.A0 * c.chis * (-trQ2 / T(6) - trQ3 / T(3) + trQ2 * trQ2 / T(4)) - T(2) * c.W * (divQdp + Qh);
+  const T psi2 = psi * psi;
+  mu = psi * (c.b * psi2 - c.a) - c.kphi * lapp + c.A0 * c.chis * (trQ2 * (T(0.25) * trQ2 - T(1) / T(6)) - trQ3 / T(3)) -
+       T(2) * c.W * (divQdp + Qh);
 
-  // Gram matrix of the Q derivatives and the free-energy density
+  // Gram matrix of the Q derivatives (symmetric), Q:curl Q, Q.grad psi
   T G[3][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = a; b < 3; ++b) {
-      T s = T(0);
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) s += dQ[a][i][j] * dQ[b][i][j];
+      const T s = dQ[a][0][0] * dQ[b][0][0] + dQ[a][1][1] * dQ[b][1][1] + dQ[a][2][2] * dQ[b][2][2] +
+                  T(2) * (dQ[a][0][1] * dQ[b][0][1] + dQ[a][0][2] * dQ[b][0][2] + dQ[a][1][2] * dQ[b][1][2]);
       G[a][b] = s;
       G[b][a] = s;
     }
-  T QC = T(0);
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) QC += Q[i][j] * C[i][j];
+  const T QC = Q[0][0] * C[0][0] + Q[1][1] * C[1][1] + Q[2][2] * C[2][2] + Q[0][1] * CC[0][1] +
+               Q[0][2] * CC[0][2] + Q[1][2] * CC[1][2];
   T Qdp[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) Qdp[i] = Q[i][0] * dp[0] + Q[i][1] * dp[1] + Q[i][2] * dp[2];
   const T anch = dp[0] * Qdp[0] + dp[1] * Qdp[1] + dp[2] * Qdp[2];
-  const T psi2 = psi * psi;
-  const T fden = -T(0.5) * c.a * psi2 + T(0.25) * c.b * psi2 * psi2 + T(0.5) * c.kphi * g2 +
+  const T fden = psi2 * (T(0.25) * c.b * psi2 - T(0.5) * c.a) + T(0.5) * c.kphi * g2 +
                  c.A0 * (T(0.5) * (T(1) - chi / T(3)) * trQ2 - chi / T(3) * trQ3 + chi / T(4) * trQ2 * trQ2) +
-                 T(0.5) * c.K * (G[0][0] + G[1][1] + G[2][2]) + Kq * QC + T(2) * c.K * c.q0 * c.q0 * trQ2 +
-                 c.W * anch;
+                 T(0.5) * c.K * (G[0][0] + G[1][1] + G[2][2]) + Kq * QC + Kq * c.q0 * trQ2 + c.W * anch;
   const T P0 = psi * mu - fden;
 
-  // reactive parts: QH, HQ, tr(QH)
+  // reactive and active parts: with (HQ)_ab = (QH)_ba,
+  //   -xi (HQ~ + Q~H) + 2 xi Q~ tr(QH) + QH - HQ - zeta phi_c Q
+  //   = (1 - xi) QH - (1 + xi) HQ - (2 xi/3) H + (2 xi tr(QH) - zeta phi_c) Q + (2 xi/3) tr(QH) I
   T QH[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -160,187 +165,173 @@ __device__ __forceinline__ void local_fields(const Coef<T>& c, const T q[5], T p
     for (int j = 0; j < 3; ++j) QH[i][j] = Q[i][0] * Hf[0][j] + Q[i][1] * Hf[1][j] + Q[i][2] * Hf[2][j];
   const T trQH = QH[0][0] + QH[1][1] + QH[2][2];
   const T phic = T(0.5) * (T(1) + psi);
-
+  const T cQ = T(2) * c.xi * trQH - c.zeta * phic;
+  const T cI = T(2) * c.xi / T(3) * trQH - P0;
+  const T cH = -T(2) * c.xi / T(3);
+  const T cP = T(1) - c.xi, cM = -(T(1) + c.xi);
+  T wv[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) wv[b] = c.kphi * dp[b] + T(2) * c.W * Qdp[b];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    // axial vector of the antisymmetric part of dQ_a . Q: v_b = eps_bgm (dQ_a Q)_gm
-    T A[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) A[i][j] = dQ[a][i][0] * Q[0][j] + dQ[a][i][1] * Q[1][j] + dQ[a][i][2] * Q[2][j];
-    const T v[3] = {A[1][2] - A[2][1], A[2][0] - A[0][2], A[0][1] - A[1][0]};
+    // v_b = eps_bgm (dQ_a Q)_gm: the axial vector of the antisymmetric part of dQ_a Q
+    T v[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      const T dab = (a == b) ? T(1) : T(0);
-      // QH^T = HQ for symmetric Q, H: (HQ)_ab = QH_ba
-      const T HQab = QH[b][a];
-      T s = -P0 * dab - c.K * G[a][b] - Kq * v[b] - dp[a] * (c.kphi * dp[b] + T(2) * c.W * Qdp[b]);
-      s += -c.xi * (HQab + QH[a][b]) - (T(2) * c.xi / T(3)) * Hf[a][b] +
-           T(2) * c.xi * trQH * (Q[a][b] + dab / T(3)) + (QH[a][b] - HQab);
-      s += -c.zeta * phic * Q[a][b];
+      const int g = (b + 1) % 3, m = (b + 2) % 3;
+      v[b] = dQ[a][g][0] * Q[0][m] + dQ[a][g][1] * Q[1][m] + dQ[a][g][2] * Q[2][m] -
+             (dQ[a][m][0] * Q[0][g] + dQ[a][m][1] * Q[1][g] + dQ[a][m][2] * Q[2][g]);
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      T s = cQ * Q[a][b] + cP * QH[a][b] + cM * QH[b][a] + cH * Hf[a][b] - c.K * G[a][b] - Kq * v[b] - dp[a] * wv[b];
+      if (a == b) s += cI;
       sig[3 * a + b] = s;
     }
   }
 }
 
-// ---------------------------------------------------------------- k_fields
+// ---------------------------------------------------------------- shared per-site pieces
+// Both step paths (two kernels through global memory, one fused kernel through shared
+// memory tiles) evaluate their stencils with the functions below, in the same order and
+// with the same arithmetic, through an accessor A that returns neighbour values:
+//   A::q(k, cx, cy, cz), A::psi(cx, cy, cz)            (gather_fields)
+//   A::sig(k, ...), A::mu(...), A::u(a, ...), q, psi   (gather_update)
+// With cx, cy, cz compile-time constants after unrolling, a shared-memory accessor
+// turns every neighbour read into one load at an immediate offset.
+//
+// D3Q19 velocities come in opposite pairs (i, i+1) for odd i, so the isotropic gradient
+// 3 Sum_i w_i c_i f(x + c_i) is (1/12) Sum_pairs c_i (f_i - f_{i+1}) (x2 for faces):
+//   d_x = [2 D1 + D7 + D9 + D11 + D13]/12,  d_y = [2 D3 + D7 - D9 + D15 + D17]/12,
+//   d_z = [2 D5 + D11 - D13 + D15 - D17]/12,  D_i = f(x + c_i) - f(x + c_{i+1}).
+// Laplacians are sums of differences to the centre value (Sum_i w_i c_i = 0), which
+// keeps them free of cancellation in FP32.
+
 template <typename T>
-__global__ void __launch_bounds__(kStepBlock) k_fields(const InstDesc<T>* __restrict__ D, int ninst) {
-  const int ii = find_inst(D, ninst, (long long)blockIdx.x);
-  const InstDesc<T>& I = D[ii];
-  const long long N = I.N;
-  const long long s = ((long long)blockIdx.x - I.blk0) * blockDim.x + threadIdx.x;
-  if (s >= N) return;
-  const int nx = I.nx, ny = I.ny, nz = I.nz;
-  const int x = (int)(s % nx);
-  const long long t = s / nx;
-  const int y = (int)(t % ny);
-  const int z = (int)(t / ny);
-  const Nbr nb = make_nbr(x, y, z, nx, ny, nz);
-  const T* __restrict__ q = I.q_in;
-  const T* __restrict__ ps = I.psi_in;
-
-  T q0[5];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) q0[k] = ld(q + k * N + s);
-  const T p0 = ld(ps + s);
-  T dq[3][5], lapq[5], dp[3], hp[6];
-  T lapp = T(0);
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    lapq[k] = T(0);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) dq[a][k] = T(0);
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) dp[a] = T(0);
-#pragma unroll
-  for (int k = 0; k < 6; ++k) hp[k] = T(0);
-
-#pragma unroll
-  for (int i = 1; i < 19; ++i) {
-    const int cx = lat_c(i, 0), cy = lat_c(i, 1), cz = lat_c(i, 2);
-    const long long n = nb.off(cx, cy, cz);
-    // differences to the centre value: Sum_i w_i c_i = 0 makes every stencil below a
-    // sum of differences, which keeps FP32 Laplacians free of cancellation
-    T qn[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) qn[k] = ld(q + k * N + n) - q0[k];
-    const T pn = ld(ps + n) - p0;
-    const bool face = lat_c2(i) == 1;
-    const T gw = face ? T(1.0 / 6.0) : T(1.0 / 12.0);
-    const T lw = face ? T(1.0 / 3.0) : T(1.0 / 6.0);
-    const int cc[3] = {cx, cy, cz};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (cc[a] == 0) continue;
-      const T wa = cc[a] > 0 ? gw : -gw;
-#pragma unroll
-      for (int k = 0; k < 5; ++k) dq[a][k] += wa * qn[k];
-      dp[a] += wa * pn;
-    }
-#pragma unroll
-    for (int k = 0; k < 5; ++k) lapq[k] += lw * qn[k];
-    lapp += lw * pn;
-    if (face) {
-      const int a = cx ? 0 : (cy ? 1 : 2);
-      hp[a] += pn;
-    } else {
-      const T sgn = T(0.25) * T(cx * cy + cx * cz + cy * cz);  // c_a c_b of the two non-zero axes
-      const int k = (cz == 0) ? 3 : (cy == 0 ? 4 : 5);          // xy, xz, yz
-      hp[k] += sgn * pn;
-    }
-  }
-
-  T H[5], sig[9], mu;
-  local_fields<T>(I.c, q0, p0, dq, lapq, dp, lapp, hp, H, mu, sig);
-#pragma unroll
-  for (int k = 0; k < 5; ++k) I.H[k * N + s] = H[k];
-  I.mu[s] = mu;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) I.sig[k * N + s] = sig[k];
+__device__ __forceinline__ void grad_from_pairs(const T D[19], T g[3]) {
+  g[0] = (T(2) * D[1] + D[7] + D[9] + D[11] + D[13]) * T(1.0 / 12.0);
+  g[1] = (T(2) * D[3] + D[7] - D[9] + D[15] + D[17]) * T(1.0 / 12.0);
+  g[2] = (T(2) * D[5] + D[11] - D[13] + D[15] - D[17]) * T(1.0 / 12.0);
 }
 
-// ---------------------------------------------------------------- k_update
-template <typename T, bool SHIFT>
-__global__ void __launch_bounds__(kStepBlock) k_update(const InstDesc<T>* __restrict__ D, int ninst) {
-  const int ii = find_inst(D, ninst, (long long)blockIdx.x);
-  const InstDesc<T>& I = D[ii];
-  const long long N = I.N;
-  const long long s = ((long long)blockIdx.x - I.blk0) * blockDim.x + threadIdx.x;
-  if (s >= N) return;
-  const int nx = I.nx, ny = I.ny, nz = I.nz;
-  const int x = (int)(s % nx);
-  const long long t = s / nx;
-  const int y = (int)(t % ny);
-  const int z = (int)(t / ny);
-  const Nbr nb = make_nbr(x, y, z, nx, ny, nz);
-  const Coef<T> c = I.c;
-  const T* __restrict__ sg = I.sig;
-  const T* __restrict__ mu = I.mu;
-  const T* __restrict__ ui = I.u_in;
-  const T* __restrict__ q = I.q_in;
-  const T* __restrict__ ps = I.psi_in;
+// Laplacian from differences to the centre: (1/3) Sum_faces d + (1/6) Sum_edges d.
+template <typename T>
+__device__ __forceinline__ T lap_from_diffs(const T d[19]) {
+  const T sf = (d[1] + d[2]) + (d[3] + d[4]) + (d[5] + d[6]);
+  const T se = ((d[7] + d[8]) + (d[9] + d[10])) + ((d[11] + d[12]) + (d[13] + d[14])) +
+               ((d[15] + d[16]) + (d[17] + d[18]));
+  return (T(2) * sf + se) * T(1.0 / 6.0);
+}
 
-  T s0[9], u0[3];
+// a1: gradient and Laplacian of the five Q components and psi, and the Hessian of psi
+// (three-point differences on the diagonal, four corners off it).
+template <typename T, class A>
+__device__ __forceinline__ void gather_fields(const A& acc, T q0[5], T& p0, T dq[3][5], T lapq[5], T dp[3],
+                                              T& lapp, T hp[6]) {
 #pragma unroll
-  for (int k = 0; k < 9; ++k) s0[k] = ld(sg + k * N + s);
+  for (int k = 0; k < 6; ++k) {
+    T f[19];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) u0[a] = ld(ui + a * N + s);
-  const T mu0 = ld(mu + s);
-  T F[3] = {T(0), T(0), T(0)};
-  T Wg[3][3];
+    for (int i = 0; i < 19; ++i)
+      f[i] = (k < 5) ? acc.q(k, lat_c(i, 0), lat_c(i, 1), lat_c(i, 2)) : acc.psi(lat_c(i, 0), lat_c(i, 1), lat_c(i, 2));
+    T d[19], D[19];
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+    for (int i = 1; i < 19; ++i) d[i] = f[i] - f[0];
 #pragma unroll
-    for (int b = 0; b < 3; ++b) Wg[a][b] = T(0);
-  T lapmu = T(0);
-  T qf[6][5], pf[6], uf[6];
+    for (int i = 1; i < 19; i += 2) D[i] = d[i] - d[i + 1];
+    T g[3];
+    grad_from_pairs(D, g);
+    const T lp = lap_from_diffs(d);
+    if (k < 5) {
+      q0[k] = f[0];
 #pragma unroll
-  for (int i = 1; i < 19; ++i) {
-    const int cx = lat_c(i, 0), cy = lat_c(i, 1), cz = lat_c(i, 2);
-    const long long n = nb.off(cx, cy, cz);
-    const bool face = lat_c2(i) == 1;
-    const T gw = face ? T(1.0 / 6.0) : T(1.0 / 12.0);
-    const T lw = face ? T(1.0 / 3.0) : T(1.0 / 6.0);
-    lapmu += lw * (ld(mu + n) - mu0);
-    T un[3];
+      for (int a = 0; a < 3; ++a) dq[a][k] = g[a];
+      lapq[k] = lp;
+    } else {
+      p0 = f[0];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) un[a] = ld(ui + a * N + n);
-    const int cc[3] = {cx, cy, cz};
+      for (int a = 0; a < 3; ++a) dp[a] = g[a];
+      lapp = lp;
+      hp[0] = d[1] + d[2];
+      hp[1] = d[3] + d[4];
+      hp[2] = d[5] + d[6];
+      hp[3] = T(0.25) * ((d[7] + d[8]) - (d[9] + d[10]));
+      hp[4] = T(0.25) * ((d[11] + d[12]) - (d[13] + d[14]));
+      hp[5] = T(0.25) * ((d[15] + d[16]) - (d[17] + d[18]));
+    }
+  }
+}
+
+// a3 (divergence) and the stencils of a4: F = div sigma, lap mu, W_ab = d_b u_a, and the
+// face values of Q, psi and u for the upwind terms (face slot 2a: +e_a, 2a+1: -e_a).
+template <typename T, class A>
+__device__ __forceinline__ void gather_update(const A& acc, T F[3], T& lapmu, T Wg[3][3], T q0[5], T qf[6][5],
+                                              T& p0, T pf[6], T u0[3], T uf[6]) {
+  // F_a = d_x sigma_ax + d_y sigma_ay + d_z sigma_az
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    T acc2 = T(0), acc1 = T(0);
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      if (cc[b] == 0) continue;
-      const T wb = cc[b] > 0 ? gw : -gw;
+      const int k = 3 * a + b;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        F[a] += wb * (ld(sg + (3 * a + b) * N + n) - s0[3 * a + b]);
-        Wg[a][b] += wb * (un[a] - u0[a]);
+      for (int i = 1; i < 19; i += 2) {
+        const int cb = lat_c(i, b);
+        if (cb == 0) continue;
+        const T Di = acc.sig(k, lat_c(i, 0), lat_c(i, 1), lat_c(i, 2)) -
+                     acc.sig(k, lat_c(i + 1, 0), lat_c(i + 1, 1), lat_c(i + 1, 2));
+        if (lat_c2(i) == 1) acc2 += (cb > 0 ? Di : -Di);
+        else acc1 += (cb > 0 ? Di : -Di);
       }
     }
-    if (face) {
-      const int a = cx ? 0 : (cy ? 1 : 2);
-#pragma unroll
-      for (int k = 0; k < 5; ++k) qf[i - 1][k] = ld(q + k * N + n);
-      pf[i - 1] = ld(ps + n);
-      uf[i - 1] = un[a];
-    }
+    F[a] = (T(2) * acc2 + acc1) * T(1.0 / 12.0);
   }
+  // lap mu
+  {
+    T d[19];
+    const T m0 = acc.mu(0, 0, 0);
+#pragma unroll
+    for (int i = 1; i < 19; ++i) d[i] = acc.mu(lat_c(i, 0), lat_c(i, 1), lat_c(i, 2)) - m0;
+    lapmu = lap_from_diffs(d);
+  }
+  // grad u and the axial face velocities
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    T f[19], D[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) f[i] = acc.u(a, lat_c(i, 0), lat_c(i, 1), lat_c(i, 2));
+#pragma unroll
+    for (int i = 1; i < 19; i += 2) D[i] = f[i] - f[i + 1];
+    grad_from_pairs(D, Wg[a]);
+    u0[a] = f[0];
+    uf[2 * a] = f[1 + 2 * a];
+    uf[2 * a + 1] = f[2 + 2 * a];
+  }
+#pragma unroll
+  for (int i = 1; i < 7; ++i) {
+    const int cx = lat_c(i, 0), cy = lat_c(i, 1), cz = lat_c(i, 2);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) qf[i - 1][k] = acc.q(k, cx, cy, cz);
+    pf[i - 1] = acc.psi(cx, cy, cz);
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) q0[k] = acc.q(k, 0, 0, 0);
+  p0 = acc.psi(0, 0, 0);
+}
 
-  // ---- Beris-Edwards update of Q (Eq. 2) with u of the previous step
-  T q0[5], Hs[5];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    q0[k] = ld(q + k * N + s);
-    Hs[k] = I.H[k * N + s];
-  }
-  const T p0 = ld(ps + s);
+// a4 + a5 at one site: Beris-Edwards update of Q (Eq. 2) with the velocity of the
+// previous step, Cahn-Hilliard update of psi (Eq. 1), and BGK + Guo collision of the
+// pulled populations g (Eqs. 6-8; overwritten with the post-collision values).  The
+// equilibrium and forcing terms of opposite velocities c and -c share their even part.
+template <typename T, bool SHIFT>
+__device__ __forceinline__ void update_math(const Coef<T>& c, const T F[3], T lapmu, const T Wg[3][3],
+                                            const T q0[5], const T qf[6][5], T p0, const T pf[6], const T u0[3],
+                                            const T uf[6], const T Hs[5], T g[19], T qn[5], T& pn, T u[3]) {
   T adv[5] = {T(0), T(0), T(0), T(0), T(0)};
   T divJ = T(0);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const int ip = 2 * a, im = 2 * a + 1;  // face slots of +e_a, -e_a
+    const int ip = 2 * a, im = 2 * a + 1;
     const T up = u0[a] > T(0) ? u0[a] : T(0);
     const T um = u0[a] < T(0) ? u0[a] : T(0);
 #pragma unroll
@@ -367,13 +358,16 @@ __global__ void __launch_bounds__(kStepBlock) k_update(const InstDesc<T>* __rest
 #pragma unroll
     for (int j = 0; j < 3; ++j) trQW += Q[i][j] * Wg[j][i];
   const T trD = Dm[0][0] + Dm[1][1] + Dm[2][2];
+  // co-rotation S = xi (DQ + QD) + (2 xi/3) D + (Om Q - Q Om) - 2 xi tr(QW)(Q + I/3),
+  // projected to its traceless part (its trace is 2 xi tr(D)/3)
+  const T cq = -T(2) * c.xi * trQW;
+  const T cdiag = cq / T(3) - (T(2) * c.xi / T(9)) * trD;
+  const T c23 = T(2) * c.xi / T(3);
   const int I5[5] = {0, 0, 0, 1, 1};
   const int J5[5] = {0, 1, 2, 1, 2};
-  T qn[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     const int i = I5[k], j = J5[k];
-    const T dij = (i == j) ? T(1) : T(0);
     T DQ = T(0), QD = T(0), OQ = T(0), QO = T(0);
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
@@ -382,48 +376,139 @@ __global__ void __launch_bounds__(kStepBlock) k_update(const InstDesc<T>* __rest
       OQ += Om[i][m] * Q[m][j];
       QO += Q[i][m] * Om[m][j];
     }
-    // S projected to its traceless part (its trace is 2 xi tr(D)/3)
-    const T S = c.xi * (DQ + QD) + (T(2) * c.xi / T(3)) * Dm[i][j] + (OQ - QO) -
-                T(2) * c.xi * trQW * (Q[i][j] + dij / T(3)) - dij * (T(2) * c.xi / T(9)) * trD;
+    T S = c.xi * (DQ + QD) + c23 * Dm[i][j] + (OQ - QO) + cq * Q[i][j];
+    if (i == j) S += cdiag;
     qn[k] = q0[k] - adv[k] + S + c.gammaQ * Hs[k];
   }
-#pragma unroll
-  for (int k = 0; k < 5; ++k) I.q_out[k * N + s] = qn[k];
-  // ---- Cahn-Hilliard update of psi (Eq. 1)
-  I.psi_out[s] = p0 - divJ + c.M * lapmu;
+  pn = p0 - divJ + c.M * lapmu;
 
-  // ---- LB: pull, BGK + Guo collision (Eqs. 6-8), write post-collision at s
-  T g[19];
+  // moments from opposite pairs
+  T m0 = g[0];
+  T j[3] = {T(0), T(0), T(0)};
 #pragma unroll
-  for (int i = 0; i < 19; ++i) {
-    const long long src = nb.off(-lat_c(i, 0), -lat_c(i, 1), -lat_c(i, 2));
-    g[i] = ld(I.g_in + i * N + src);
-  }
-  T m0 = T(0), j[3] = {T(0), T(0), T(0)};
+  for (int i = 1; i < 19; i += 2) {
+    m0 += g[i] + g[i + 1];
+    const T dg = g[i] - g[i + 1];
 #pragma unroll
-  for (int i = 0; i < 19; ++i) {
-    m0 += g[i];
-    if (lat_c(i, 0)) j[0] += lat_c(i, 0) > 0 ? g[i] : -g[i];
-    if (lat_c(i, 1)) j[1] += lat_c(i, 1) > 0 ? g[i] : -g[i];
-    if (lat_c(i, 2)) j[2] += lat_c(i, 2) > 0 ? g[i] : -g[i];
+    for (int a = 0; a < 3; ++a)
+      if (lat_c(i, a)) j[a] += lat_c(i, a) > 0 ? dg : -dg;
   }
   const T rho = SHIFT ? (c.rho0 + m0) : m0;
   const T rinv = T(1) / rho;
-  T u[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) u[a] = (j[a] + T(0.5) * F[a]) * rinv;
   const T u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const T uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+  // equilibrium w rho (1 + 3 cu + 4.5 cu^2 - 1.5 u^2) (shifted: minus w rho0) and Guo
+  // term guo w (3 (c - u).F + 9 (c.u)(c.F)), split into even (A, C) and odd (B, E) parts
+  const T base = SHIFT ? (m0 - T(1.5) * rho * u2) : (rho - T(1.5) * rho * u2);
+  const T r45 = T(4.5) * rho;
+  const T r3 = T(3) * rho;
+  const T om = c.tau_inv;
+  {
+    const T w = T(lat_w(0));
+    const T geq = w * base;
+    const T Fi = -T(3) * c.guo * w * uF;
+    g[0] = g[0] - (g[0] - geq) * om + Fi;
+  }
 #pragma unroll
-  for (int i = 0; i < 19; ++i) {
+  for (int i = 1; i < 19; i += 2) {
     const T w = T(lat_w(i));
     const T cu = T(lat_c(i, 0)) * u[0] + T(lat_c(i, 1)) * u[1] + T(lat_c(i, 2)) * u[2];
     const T cF = T(lat_c(i, 0)) * F[0] + T(lat_c(i, 1)) * F[1] + T(lat_c(i, 2)) * F[2];
-    const T poly = T(3) * cu + T(4.5) * cu * cu - T(1.5) * u2;
-    const T geq = SHIFT ? w * (m0 + rho * poly) : w * rho * (T(1) + poly);
-    const T Fi = c.guo * w * (T(3) * (cF - uF) + T(9) * cu * cF);
-    I.g_out[i * N + s] = g[i] - (g[i] - geq) * c.tau_inv + Fi;
+    const T Aeq = w * (base + r45 * cu * cu);
+    const T Beq = w * r3 * cu;
+    const T gw = c.guo * w;
+    const T Cf = gw * (T(9) * cu * cF - T(3) * uF);
+    const T Ef = T(3) * gw * cF;
+    const T gp = g[i], gm = g[i + 1];
+    g[i] = gp - (gp - (Aeq + Beq)) * om + (Cf + Ef);
+    g[i + 1] = gm - (gm - (Aeq - Beq)) * om + (Cf - Ef);
   }
+}
+
+// Neighbour reads straight from global memory with periodic wrap (two-kernel path).
+template <typename T>
+struct GlobalAcc {
+  const T* q_;
+  const T* ps;
+  const T* sg;
+  const T* mu_;
+  const T* u_;
+  long long N;
+  Nbr nb;
+  __device__ __forceinline__ T q(int k, int cx, int cy, int cz) const { return ld(q_ + k * N + nb.off(cx, cy, cz)); }
+  __device__ __forceinline__ T psi(int cx, int cy, int cz) const { return ld(ps + nb.off(cx, cy, cz)); }
+  __device__ __forceinline__ T sig(int k, int cx, int cy, int cz) const { return ld(sg + k * N + nb.off(cx, cy, cz)); }
+  __device__ __forceinline__ T mu(int cx, int cy, int cz) const { return ld(mu_ + nb.off(cx, cy, cz)); }
+  __device__ __forceinline__ T u(int a, int cx, int cy, int cz) const { return ld(u_ + a * N + nb.off(cx, cy, cz)); }
+};
+
+// ---------------------------------------------------------------- k_fields
+template <typename T>
+__global__ void __launch_bounds__(kStepBlock) k_fields(const InstDesc<T>* __restrict__ D, int ninst) {
+  const int ii = find_inst(D, ninst, (long long)blockIdx.x);
+  const InstDesc<T>& I = D[ii];
+  const long long N = I.N;
+  const long long s = ((long long)blockIdx.x - I.blk0) * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  const int nx = I.nx, ny = I.ny, nz = I.nz;
+  const int x = (int)(s % nx);
+  const long long t = s / nx;
+  const int y = (int)(t % ny);
+  const int z = (int)(t / ny);
+  GlobalAcc<T> acc;
+  acc.q_ = I.q_in;
+  acc.ps = I.psi_in;
+  acc.N = N;
+  acc.nb = make_nbr(x, y, z, nx, ny, nz);
+  T q0[5], p0, dq[3][5], lapq[5], dp[3], lapp, hp[6];
+  gather_fields<T>(acc, q0, p0, dq, lapq, dp, lapp, hp);
+  T H[5], sig[9], mu;
+  local_fields<T>(I.c, q0, p0, dq, lapq, dp, lapp, hp, H, mu, sig);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) I.H[k * N + s] = H[k];
+  I.mu[s] = mu;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) I.sig[k * N + s] = sig[k];
+}
+
+// ---------------------------------------------------------------- k_update
+template <typename T, bool SHIFT>
+__global__ void __launch_bounds__(kStepBlock) k_update(const InstDesc<T>* __restrict__ D, int ninst) {
+  const int ii = find_inst(D, ninst, (long long)blockIdx.x);
+  const InstDesc<T>& I = D[ii];
+  const long long N = I.N;
+  const long long s = ((long long)blockIdx.x - I.blk0) * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  const int nx = I.nx, ny = I.ny, nz = I.nz;
+  const int x = (int)(s % nx);
+  const long long t = s / nx;
+  const int y = (int)(t % ny);
+  const int z = (int)(t / ny);
+  GlobalAcc<T> acc;
+  acc.q_ = I.q_in;
+  acc.ps = I.psi_in;
+  acc.sg = I.sig;
+  acc.mu_ = I.mu;
+  acc.u_ = I.u_in;
+  acc.N = N;
+  acc.nb = make_nbr(x, y, z, nx, ny, nz);
+  T F[3], lapmu, Wg[3][3], q0[5], qf[6][5], p0, pf[6], u0[3], uf[6];
+  gather_update<T>(acc, F, lapmu, Wg, q0, qf, p0, pf, u0, uf);
+  T Hs[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) Hs[k] = I.H[k * N + s];
+  T g[19];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) g[i] = ld(I.g_in + i * N + acc.nb.off(-lat_c(i, 0), -lat_c(i, 1), -lat_c(i, 2)));
+  T qn[5], pn, u[3];
+  update_math<T, SHIFT>(I.c, F, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hs, g, qn, pn, u);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) I.q_out[k * N + s] = qn[k];
+  I.psi_out[s] = pn;
+#pragma unroll
+  for (int i = 0; i < 19; ++i) I.g_out[i * N + s] = g[i];
 #pragma unroll
   for (int a = 0; a < 3; ++a) I.u_out[a * N + s] = u[a];
 }

@@ -68,6 +68,12 @@ struct lbcad_ctx {
   double* obs_out = nullptr;
   double* staging = nullptr;
   size_t staging_bytes = 0;
+  int path = LBCAD_PATH_FUSED;
+  bool scratch_ready = false;
+  FusedTile* tiles = nullptr;
+  int ntiles = 0;
+  long long fused_total = 0;
+  int fused_grid = 0;
   std::string err;
   size_t elem() const { return prec == LBCAD_FP64 ? sizeof(double) : sizeof(float); }
 };
@@ -219,6 +225,9 @@ int upload_init(lbcad_ctx* c, Inst& I, uint64_t seed, int idx) {
   return LBCAD_OK;
 }
 
+int upload_descs(lbcad_ctx* c);
+int prepare_fused(lbcad_ctx* c);
+
 int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint64_t seed, lbcad_ctx** out) {
   g_create_err.clear();
   if (!out) return fail(nullptr, LBCAD_E_INVALID_ARG, "out is NULL");
@@ -286,10 +295,6 @@ int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint
       I.ub[par] = dev_alloc(c, 3 * I.N * es);
       if (!I.gb[par] || !I.qb[par] || !I.pb[par] || !I.ub[par]) return bail(LBCAD_E_OOM, "device allocation failed");
     }
-    I.sig = dev_alloc(c, 9 * I.N * es);
-    I.mu = dev_alloc(c, I.N * es);
-    I.H = dev_alloc(c, 5 * I.N * es);
-    if (!I.sig || !I.mu || !I.H) return bail(LBCAD_E_OOM, "device allocation failed");
   }
   c->total_blocks = blk;
   if (blk >= (1LL << 31)) return bail(LBCAD_E_INVALID_ARG, "too many blocks for one launch");
@@ -301,21 +306,8 @@ int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint
   c->obs_partial = (double*)dev_alloc(c, kObsMaxBlocks * 12 * sizeof(double));
   c->obs_out = (double*)dev_alloc(c, 12 * sizeof(double));
   if (!c->obs_partial || !c->obs_out) return bail(LBCAD_E_OOM, "device allocation failed");
-  for (int par = 0; par < 2; ++par) {
-    if (c->prec == LBCAD_FP64) {
-      std::vector<InstDesc<double>> h(n);
-      for (int i = 0; i < n; ++i) h[i] = make_desc<double>(c->inst[i], par);
-      if (cudaMemcpyAsync(c->desc[par], h.data(), dsz, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
-          cudaStreamSynchronize(c->stream) != cudaSuccess)
-        return bail(LBCAD_E_CUDA, "descriptor upload failed");
-    } else {
-      std::vector<InstDesc<float>> h(n);
-      for (int i = 0; i < n; ++i) h[i] = make_desc<float>(c->inst[i], par);
-      if (cudaMemcpyAsync(c->desc[par], h.data(), dsz, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
-          cudaStreamSynchronize(c->stream) != cudaSuccess)
-        return bail(LBCAD_E_CUDA, "descriptor upload failed");
-    }
-  }
+  if (upload_descs(c) != LBCAD_OK) return bail(LBCAD_E_CUDA, "");
+  if ((code = prepare_fused(c)) != LBCAD_OK) return bail(code, "");
   for (int i = 0; i < n; ++i) {
     code = (c->prec == LBCAD_FP64) ? upload_init<double>(c, c->inst[i], seed, i)
                                    : upload_init<float>(c, c->inst[i], seed, i);
@@ -325,11 +317,81 @@ int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint
   return LBCAD_OK;
 }
 
+int upload_descs(lbcad_ctx* c) {
+  const int n = (int)c->inst.size();
+  for (int par = 0; par < 2; ++par) {
+    if (c->prec == LBCAD_FP64) {
+      std::vector<InstDesc<double>> h(n);
+      for (int i = 0; i < n; ++i) h[i] = make_desc<double>(c->inst[i], par);
+      CK(c, cudaMemcpyAsync(c->desc[par], h.data(), n * sizeof(h[0]), cudaMemcpyHostToDevice, c->stream));
+      CK(c, cudaStreamSynchronize(c->stream));
+    } else {
+      std::vector<InstDesc<float>> h(n);
+      for (int i = 0; i < n; ++i) h[i] = make_desc<float>(c->inst[i], par);
+      CK(c, cudaMemcpyAsync(c->desc[par], h.data(), n * sizeof(h[0]), cudaMemcpyHostToDevice, c->stream));
+      CK(c, cudaStreamSynchronize(c->stream));
+    }
+  }
+  return LBCAD_OK;
+}
+
+// Scratch (sigma, mu, H per site) of the two-kernel path, allocated on first use.
+int ensure_scratch(lbcad_ctx* c) {
+  if (c->scratch_ready) return LBCAD_OK;
+  const size_t es = c->elem();
+  for (Inst& I : c->inst) {
+    I.sig = dev_alloc(c, 9 * I.N * es);
+    I.mu = dev_alloc(c, I.N * es);
+    I.H = dev_alloc(c, 5 * I.N * es);
+    if (!I.sig || !I.mu || !I.H) return fail(c, LBCAD_E_OOM, "scratch allocation failed");
+  }
+  c->scratch_ready = true;
+  return upload_descs(c);
+}
+
+// Tile columns of the fused step and its persistent grid size.
+int prepare_fused(lbcad_ctx* c) {
+  std::vector<FusedTile> t;
+  long long start = 0;
+  for (int i = 0; i < (int)c->inst.size(); ++i) {
+    const Inst& I = c->inst[i];
+    for (int y0 = 0; y0 < I.g.ny; y0 += kFusedTY)
+      for (int x0 = 0; x0 < I.g.nx; x0 += kFusedTX) {
+        t.push_back(FusedTile{i, x0, y0, I.g.nz, start});
+        start += I.g.nz;
+      }
+  }
+  c->ntiles = (int)t.size();
+  c->fused_total = start;
+  c->tiles = (FusedTile*)dev_alloc(c, t.size() * sizeof(FusedTile));
+  if (!c->tiles) return fail(c, LBCAD_E_OOM, "tile list allocation failed");
+  CK(c, cudaMemcpyAsync(c->tiles, t.data(), t.size() * sizeof(FusedTile), cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  int bps = 0, sms = 0;
+  size_t smem = 0;
+  cudaError_t e = (c->prec == LBCAD_FP64) ? LaunchFused<double, false>::prepare(&bps, &smem)
+                                          : LaunchFused<float, true>::prepare(&bps, &smem);
+  if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("fused kernel set-up: ") + cudaGetErrorString(e));
+  CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+  if (bps < 1) return fail(c, LBCAD_E_CUDA, "fused kernel does not fit on an SM");
+  long long grid = (long long)sms * bps;
+  if (grid > c->fused_total) grid = c->fused_total;
+  c->fused_grid = (int)grid;
+  return LBCAD_OK;
+}
+
 int launch_steps(lbcad_ctx* c, int64_t n) {
   for (int64_t k = 0; k < n; ++k) {
     const int par = (int)(c->step & 1);
     cudaError_t e;
-    if (c->prec == LBCAD_FP64)
+    if (c->path == LBCAD_PATH_FUSED) {
+      if (c->prec == LBCAD_FP64)
+        e = LaunchFused<double, false>::step((const InstDesc<double>*)c->desc[par], c->tiles, c->ntiles,
+                                             c->fused_total, c->fused_grid, c->stream);
+      else
+        e = LaunchFused<float, true>::step((const InstDesc<float>*)c->desc[par], c->tiles, c->ntiles,
+                                           c->fused_total, c->fused_grid, c->stream);
+    } else if (c->prec == LBCAD_FP64)
       e = Launch<double, false>::step((const InstDesc<double>*)c->desc[par], (int)c->inst.size(), c->total_blocks,
                                       kStepBlock, c->stream);
     else
@@ -381,6 +443,22 @@ int lbcad_create(const lbcad_grid* grid, const lbcad_params* params, uint64_t se
 int lbcad_create_batch(int32_t n, const lbcad_grid* grids, const lbcad_params* params, uint64_t seed,
                        lbcad_ctx** out) {
   return create_impl(n, grids, params, seed, out);
+}
+
+int lbcad_set_path(lbcad_ctx* c, int32_t path) {
+  if (!c) return LBCAD_E_INVALID_ARG;
+  if (path != LBCAD_PATH_FUSED && path != LBCAD_PATH_TWO_KERNEL) return fail(c, LBCAD_E_INVALID_ARG, "unknown path");
+  DeviceGuard dg(c->device);
+  if (path == LBCAD_PATH_TWO_KERNEL) {
+    int r = ensure_scratch(c);
+    if (r) return r;
+  }
+  if (path != c->path) {
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    c->path = path;
+  }
+  return LBCAD_OK;
 }
 
 int lbcad_set_graph(lbcad_ctx* c, int32_t steps_per_graph) {

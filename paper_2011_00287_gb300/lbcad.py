@@ -28,6 +28,7 @@ FP32, FP64 = 0, 1
 EULER, HEUN = 0, 1
 LAGGED, SYNC = 0, 1
 FIELD_G, FIELD_RHO, FIELD_U, FIELD_Q, FIELD_PSI = 1, 2, 4, 8, 16
+PATH_FUSED, PATH_TWO_KERNEL = 0, 1
 FIELD_NCOMP = {FIELD_G: 19, FIELD_RHO: 1, FIELD_U: 3, FIELD_Q: 5, FIELD_PSI: 1}
 FIELD_NAMES = {FIELD_G: "g", FIELD_RHO: "rho", FIELD_U: "u", FIELD_Q: "q", FIELD_PSI: "psi"}
 
@@ -72,6 +73,7 @@ _SIGS = {
                                           _P(ctypes.c_void_p)]),
     "lbcad_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "lbcad_set_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "lbcad_set_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "lbcad_get_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p,
                                         ctypes.c_size_t, ctypes.c_int32]),
     "lbcad_set_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p,
@@ -257,6 +259,9 @@ class Simulation:
     def step(self, n: int = 1):
         _check(library().lbcad_step(self.ctx, int(n)), self.ctx)
         return self
+
+    def set_path(self, path: int):
+        _check(library().lbcad_set_path(self.ctx, int(path)), self.ctx)
 
     def set_graph(self, steps_per_graph: int):
         _check(library().lbcad_set_graph(self.ctx, int(steps_per_graph)), self.ctx)

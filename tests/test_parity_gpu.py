@@ -92,13 +92,16 @@ def test_initial_state_matches_oracle(prec):
     np.testing.assert_allclose(got["rho"], 1.0, atol=1e-15)
 
 
+@pytest.mark.parametrize("path", [L.lbcad.PATH_FUSED, L.lbcad.PATH_TWO_KERNEL])
 @pytest.mark.parametrize("shape,kw", [
     ((32, 32, 32), KW0),
     ((21, 13, 10), dict(R=4.0, p0=8.0, zeta=0.01, W=0.05)),   # ragged, non-cubic, odd edges
     ((4, 5, 6), dict(R=2.0, p0=6.0)),                           # minimum edges: everything wraps
+    ((70, 9, 40), dict(R=4.0, p0=10.0)),                        # several tiles in x, ragged y
 ])
-def test_fp64_parity_10_steps(shape, kw):
+def test_fp64_parity_10_steps(shape, kw, path):
     sim = L.Simulation([shape], [_lib_params(shape, L.FP64, **kw)], seed=2)
+    sim.set_path(path)
     sim.step(10)
     ref = _oracle(shape, seed=2, **kw).step(10)
     _compare_fp64(sim.get_fields(0), ref)
@@ -216,3 +219,36 @@ def test_invalid_instance_and_sizes_raise():
     buf = np.zeros(10)
     assert lib.lbcad_get_fields(sim.ctx, 0, L.FIELD_Q, ctypes.c_void_p(buf.ctypes.data), buf.nbytes, 0) == \
         L.lbcad.LBCAD_E_INVALID_ARG
+
+
+@pytest.mark.parametrize("prec", [L.FP32, L.FP64])
+def test_fused_and_two_kernel_paths_agree(prec):
+    """The fused kernel and the two-kernel path share the per-site arithmetic; their
+    results agree to rounding (the compiler may contract differently)."""
+    shape = (40, 18, 12)
+    kw = dict(R=5.0, p0=8.0, zeta=0.01)
+    a = L.Simulation([shape], [_lib_params(shape, prec, **kw)], seed=3)
+    b = L.Simulation([shape], [_lib_params(shape, prec, **kw)], seed=3)
+    b.set_path(L.lbcad.PATH_TWO_KERNEL)
+    a.step(20)
+    b.step(20)
+    fa, fb = a.get_fields(0), b.get_fields(0)
+    for k in fa:
+        if prec == L.FP64:
+            assert np.abs(fa[k] - fb[k]).max() <= 1e-13, k
+        else:
+            x, y = (_shifted(fa[k]), _shifted(fb[k])) if k == "g" else (fa[k], fb[k])
+            assert _rel_l2(x, y) <= 1e-6, k
+
+
+def test_path_switch_mid_run():
+    shape = (24, 16, 12)
+    kw = dict(R=4.0, p0=8.0)
+    sim = L.Simulation([shape], [_lib_params(shape, L.FP64, **kw)], seed=5)
+    sim.step(3)
+    sim.set_path(L.lbcad.PATH_TWO_KERNEL)
+    sim.step(3)
+    sim.set_path(L.lbcad.PATH_FUSED)
+    sim.step(2)
+    ref = _oracle(shape, seed=5, **kw).step(8)
+    _compare_fp64(sim.get_fields(0), ref)
