@@ -218,6 +218,7 @@ def main():
     K, W = args.steps, args.warmup
     # replicas: each rank advances its own copy of the workload (weak scaling)
     sim = L.Simulation([(n, n, n)], [workload_params(L, n, L.FP32)], seed=1 + rank, device=local)
+    tile_cfg, tile_ms = sim.autotune(5)
     sim.step(W)
     sim.sync()
     if dist:
@@ -293,6 +294,7 @@ def main():
                            "box": [n, n, n], "parallelism": "replicas" if world > 1 else "single",
                            "l2": "state %.0f MB per step > 129 MB L2, no flush" % (224 * N / 1e6)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "tiles": {"chosen": ["32x8", "32x16", "64x8"][tile_cfg], "ms_per_cfg": tile_ms},
                 "gpu_launches": K, "clocks": clk.summary(), "fp64_gpu": fp64,
                 "speedup_fp32_vs_fp64": (value / world / fp64["mlups"]) if fp64 else None,
                 "observables_finite": finite}

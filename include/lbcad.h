@@ -147,6 +147,18 @@ int lbcad_step(lbcad_ctx* c, int64_t n);
 #define LBCAD_PATH_TWO_KERNEL 1
 int lbcad_set_path(lbcad_ctx* c, int32_t path);
 
+/* Picks the fastest tile shape of the fused step for this context by timing each
+ * candidate over `reps` launches that recompute the step from the current state into
+ * the next-state buffers (the simulation does not advance; results are unchanged, only
+ * speed).  Writes the chosen index to *chosen and, if ms_per_cfg is given, the measured
+ * milliseconds per launch of up to ncfg candidates (-1 for a shape that does not fit).
+ * Candidates: 0 = 32x8 tiles (default), 1 = 32x16, 2 = 64x8 (FP32 only). */
+int lbcad_autotune(lbcad_ctx* c, int32_t reps, int32_t* chosen, float* ms_per_cfg, int32_t ncfg);
+
+/* Selects tile shape `cfg` of the fused step explicitly (same candidates as above).
+ * The arithmetic per site does not depend on the tile shape: results are identical. */
+int lbcad_set_tiles(lbcad_ctx* c, int32_t cfg);
+
 /* Capture steps in a CUDA graph of `steps_per_graph` steps (0 disables; default 0). */
 int lbcad_set_graph(lbcad_ctx* c, int32_t steps_per_graph);
 

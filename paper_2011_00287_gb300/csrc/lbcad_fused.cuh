@@ -71,7 +71,7 @@ __device__ __forceinline__ int sslot(int p) { return (p + 9) % 3; }
 __device__ __forceinline__ int uslot(int p) { return (p + 8) % 4; }
 
 template <typename T, bool SHIFT, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 2 : 1)
     k_step_fused(const InstDesc<T>* __restrict__ D, const FusedTile* __restrict__ tiles, int ntiles,
                  long long total) {
   using G = FusedGeom<T, TX, TY>;
@@ -223,13 +223,18 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 2 : 1)
       // output plane), then the halo sites while the other threads prefetch
       // Q(z+3) and u(z+2) into the slots of Q(z-2) and u(z-2)
       T Hn[5];
-      sigma_site(z + 1, tx + 1, ty + 1, Hn);
-      if (tid < G::NHALO) {
-        T Hh[5];
-        sigma_site(z + 1, hx, hy, Hh);
-      } else {
-        prefetch(z + 3, z + 2);
+#pragma unroll 1
+      for (int r = 0; r < 2; ++r) {  // one copy of the sigma code for both rounds
+        if (r == 1 && tid >= G::NHALO) break;
+        const int sx = r ? hx : tx + 1, sy = r ? hy : ty + 1;
+        T H[5];
+        sigma_site(z + 1, sx, sy, H);
+        if (r == 0) {
+#pragma unroll
+          for (int k = 0; k < 5; ++k) Hn[k] = H[k];
+        }
       }
+      if (tid >= G::NHALO) prefetch(z + 3, z + 2);
       __syncthreads();
       if (z >= zb && tl.x0 + tx < nx && tl.y0 + ty < ny) {
         SmemUpdateAcc<T, QW, QP, SW, SP> acc;
@@ -245,15 +250,18 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 2 : 1)
         gather_update<T>(acc, F, lapmu, Wg, q0, qf, p0, pf, u0, uf);
         const long long zo[3] = {(long long)wrapmod(z - 1, nz) * plane, (long long)z * plane,
                                  (long long)wrapmod(z + 1, nz) * plane};
+        // in-plane offsets of this thread's output site and its x, y neighbours (pull)
+        const int pxo[3] = {xmap[tx + 1], xmap[tx + 2], xmap[tx + 3]};
+        const int pyo[3] = {ymap[ty + 1], ymap[ty + 2], ymap[ty + 3]};
         T g[19];
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
           const int cx = lat_c(i, 0), cy = lat_c(i, 1), cz = lat_c(i, 2);
-          g[i] = ld(gin + i * N + zo[1 - cz] + ymap[ty + 2 - cy] + xmap[tx + 2 - cx]);
+          g[i] = ld(gin + i * N + zo[1 - cz] + pyo[1 - cy] + pxo[1 - cx]);
         }
         T qn[5], pn, u[3];
         update_math<T, SHIFT>(cf, F, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hc, g, qn, pn, u);
-        const long long s = zo[1] + ymap[ty + 2] + xmap[tx + 2];
+        const long long s = zo[1] + pyo[1] + pxo[1];
 #pragma unroll
         for (int k = 0; k < 5; ++k) I.q_out[k * N + s] = qn[k];
         I.psi_out[s] = pn;
@@ -268,22 +276,53 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 2 : 1)
   }
 }
 
-template <typename T, bool SHIFT>
-cudaError_t LaunchFused<T, SHIFT>::step(const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles,
-                                        long long total, int grid, cudaStream_t s) {
-  using G = FusedGeom<T, kFusedTX, kFusedTY>;
-  k_step_fused<T, SHIFT, kFusedTX, kFusedTY><<<grid, G::NT, G::bytes, s>>>(d_desc, tiles, ntiles, total);
+template <typename T, bool SHIFT, int TX, int TY>
+cudaError_t launch_cfg(const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles, long long total, int grid,
+                       cudaStream_t s) {
+  using G = FusedGeom<T, TX, TY>;
+  k_step_fused<T, SHIFT, TX, TY><<<grid, G::NT, G::bytes, s>>>(d_desc, tiles, ntiles, total);
   return cudaGetLastError();
 }
 
-template <typename T, bool SHIFT>
-cudaError_t LaunchFused<T, SHIFT>::prepare(int* blocks_per_sm, size_t* smem) {
-  using G = FusedGeom<T, kFusedTX, kFusedTY>;
-  auto k = k_step_fused<T, SHIFT, kFusedTX, kFusedTY>;
+template <typename T, bool SHIFT, int TX, int TY>
+cudaError_t prepare_cfg(FusedCfg* cfg) {
+  using G = FusedGeom<T, TX, TY>;
+  auto k = k_step_fused<T, SHIFT, TX, TY>;
+  cfg->tx = TX;
+  cfg->ty = TY;
+  cfg->threads = G::NT;
+  cfg->smem = G::bytes;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::bytes);
   if (e != cudaSuccess) return e;
-  *smem = G::bytes;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, G::NT, G::bytes);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cfg->blocks_per_sm, k, G::NT, G::bytes);
+}
+
+// Tile shapes offered to the autotuner: 32x8 (two blocks per SM in FP32), 32x16 and
+// 64x8 (one block per SM, fewer redundant halo sites).  FP64 only fits 32x8.
+template <typename T, bool SHIFT>
+int LaunchFused<T, SHIFT>::num_configs() {
+  return sizeof(T) == 4 ? 3 : 1;
+}
+
+template <typename T, bool SHIFT>
+cudaError_t LaunchFused<T, SHIFT>::prepare(int cfg_index, FusedCfg* cfg) {
+  if constexpr (sizeof(T) == 4) {
+    if (cfg_index == 1) return prepare_cfg<T, SHIFT, 32, 16>(cfg);
+    if (cfg_index == 2) return prepare_cfg<T, SHIFT, 64, 8>(cfg);
+  }
+  if (cfg_index == 0) return prepare_cfg<T, SHIFT, 32, 8>(cfg);
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, bool SHIFT>
+cudaError_t LaunchFused<T, SHIFT>::step(int cfg_index, const InstDesc<T>* d_desc, const FusedTile* tiles,
+                                        int ntiles, long long total, int grid, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (cfg_index == 1) return launch_cfg<T, SHIFT, 32, 16>(d_desc, tiles, ntiles, total, grid, s);
+    if (cfg_index == 2) return launch_cfg<T, SHIFT, 64, 8>(d_desc, tiles, ntiles, total, grid, s);
+  }
+  if (cfg_index == 0) return launch_cfg<T, SHIFT, 32, 8>(d_desc, tiles, ntiles, total, grid, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace lbcad

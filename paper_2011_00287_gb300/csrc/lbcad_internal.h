@@ -69,15 +69,19 @@ struct FusedTile {
   long long start;
 };
 
-constexpr int kFusedTX = 32;
-constexpr int kFusedTY = 8;
+// A tile shape of the fused step and its launch resources.
+struct FusedCfg {
+  int tx = 0, ty = 0, threads = 0, blocks_per_sm = 0;
+  size_t smem = 0;
+};
 
-// The fused one-kernel step (lbcad_fused.cuh).
+// The fused one-kernel step (lbcad_fused.cuh), in several tile shapes.
 template <typename T, bool SHIFT>
 struct LaunchFused {
-  static cudaError_t step(const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles, long long total, int grid,
-                          cudaStream_t s);
-  static cudaError_t prepare(int* blocks_per_sm, size_t* smem_bytes);
+  static int num_configs();
+  static cudaError_t prepare(int cfg_index, FusedCfg* cfg);
+  static cudaError_t step(int cfg_index, const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles,
+                          long long total, int grid, cudaStream_t s);
 };
 
 // Sets the message that lbcad_last_error(NULL) returns on this thread.

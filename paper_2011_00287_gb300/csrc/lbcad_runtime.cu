@@ -71,9 +71,12 @@ struct lbcad_ctx {
   int path = LBCAD_PATH_FUSED;
   bool scratch_ready = false;
   FusedTile* tiles = nullptr;
+  size_t tiles_cap = 0;
   int ntiles = 0;
   long long fused_total = 0;
   int fused_grid = 0;
+  int cfg_index = 0;
+  FusedCfg cfg;
   std::string err;
   size_t elem() const { return prec == LBCAD_FP64 ? sizeof(double) : sizeof(float); }
 };
@@ -226,7 +229,7 @@ int upload_init(lbcad_ctx* c, Inst& I, uint64_t seed, int idx) {
 }
 
 int upload_descs(lbcad_ctx* c);
-int prepare_fused(lbcad_ctx* c);
+int prepare_fused(lbcad_ctx* c, int cfg_index);
 
 int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint64_t seed, lbcad_ctx** out) {
   g_create_err.clear();
@@ -307,7 +310,7 @@ int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint
   c->obs_out = (double*)dev_alloc(c, 12 * sizeof(double));
   if (!c->obs_partial || !c->obs_out) return bail(LBCAD_E_OOM, "device allocation failed");
   if (upload_descs(c) != LBCAD_OK) return bail(LBCAD_E_CUDA, "");
-  if ((code = prepare_fused(c)) != LBCAD_OK) return bail(code, "");
+  if ((code = prepare_fused(c, 0)) != LBCAD_OK) return bail(code, "");
   for (int i = 0; i < n; ++i) {
     code = (c->prec == LBCAD_FP64) ? upload_init<double>(c, c->inst[i], seed, i)
                                    : upload_init<float>(c, c->inst[i], seed, i);
@@ -349,35 +352,53 @@ int ensure_scratch(lbcad_ctx* c) {
   return upload_descs(c);
 }
 
-// Tile columns of the fused step and its persistent grid size.
-int prepare_fused(lbcad_ctx* c) {
+// Tile columns of the fused step for tile shape `cfg_index` and its persistent grid size.
+int prepare_fused(lbcad_ctx* c, int cfg_index) {
+  FusedCfg cfg;
+  cudaError_t e = (c->prec == LBCAD_FP64) ? LaunchFused<double, false>::prepare(cfg_index, &cfg)
+                                          : LaunchFused<float, true>::prepare(cfg_index, &cfg);
+  if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("fused kernel set-up: ") + cudaGetErrorString(e));
+  if (cfg.blocks_per_sm < 1) return fail(c, LBCAD_E_UNSUPPORTED, "fused tile shape does not fit on an SM");
   std::vector<FusedTile> t;
   long long start = 0;
   for (int i = 0; i < (int)c->inst.size(); ++i) {
     const Inst& I = c->inst[i];
-    for (int y0 = 0; y0 < I.g.ny; y0 += kFusedTY)
-      for (int x0 = 0; x0 < I.g.nx; x0 += kFusedTX) {
+    for (int y0 = 0; y0 < I.g.ny; y0 += cfg.ty)
+      for (int x0 = 0; x0 < I.g.nx; x0 += cfg.tx) {
         t.push_back(FusedTile{i, x0, y0, I.g.nz, start});
         start += I.g.nz;
       }
   }
-  c->ntiles = (int)t.size();
-  c->fused_total = start;
-  c->tiles = (FusedTile*)dev_alloc(c, t.size() * sizeof(FusedTile));
-  if (!c->tiles) return fail(c, LBCAD_E_OOM, "tile list allocation failed");
+  if (t.size() > c->tiles_cap) {
+    c->tiles = (FusedTile*)dev_alloc(c, t.size() * sizeof(FusedTile));
+    if (!c->tiles) return fail(c, LBCAD_E_OOM, "tile list allocation failed");
+    c->tiles_cap = t.size();
+  }
   CK(c, cudaMemcpyAsync(c->tiles, t.data(), t.size() * sizeof(FusedTile), cudaMemcpyHostToDevice, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
-  int bps = 0, sms = 0;
-  size_t smem = 0;
-  cudaError_t e = (c->prec == LBCAD_FP64) ? LaunchFused<double, false>::prepare(&bps, &smem)
-                                          : LaunchFused<float, true>::prepare(&bps, &smem);
-  if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("fused kernel set-up: ") + cudaGetErrorString(e));
+  int sms = 0;
   CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-  if (bps < 1) return fail(c, LBCAD_E_CUDA, "fused kernel does not fit on an SM");
-  long long grid = (long long)sms * bps;
-  if (grid > c->fused_total) grid = c->fused_total;
+  long long grid = (long long)sms * cfg.blocks_per_sm;
+  if (grid > start) grid = start;
+  c->ntiles = (int)t.size();
+  c->fused_total = start;
   c->fused_grid = (int)grid;
+  c->cfg_index = cfg_index;
+  c->cfg = cfg;
   return LBCAD_OK;
+}
+
+cudaError_t launch_fused(lbcad_ctx* c, int par) {
+  if (c->prec == LBCAD_FP64)
+    return LaunchFused<double, false>::step(c->cfg_index, (const InstDesc<double>*)c->desc[par], c->tiles, c->ntiles,
+                                            c->fused_total, c->fused_grid, c->stream);
+  return LaunchFused<float, true>::step(c->cfg_index, (const InstDesc<float>*)c->desc[par], c->tiles, c->ntiles,
+                                        c->fused_total, c->fused_grid, c->stream);
+}
+
+void drop_graph(lbcad_ctx* c) {
+  if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+  if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
 }
 
 int launch_steps(lbcad_ctx* c, int64_t n) {
@@ -385,12 +406,7 @@ int launch_steps(lbcad_ctx* c, int64_t n) {
     const int par = (int)(c->step & 1);
     cudaError_t e;
     if (c->path == LBCAD_PATH_FUSED) {
-      if (c->prec == LBCAD_FP64)
-        e = LaunchFused<double, false>::step((const InstDesc<double>*)c->desc[par], c->tiles, c->ntiles,
-                                             c->fused_total, c->fused_grid, c->stream);
-      else
-        e = LaunchFused<float, true>::step((const InstDesc<float>*)c->desc[par], c->tiles, c->ntiles,
-                                           c->fused_total, c->fused_grid, c->stream);
+      e = launch_fused(c, par);
     } else if (c->prec == LBCAD_FP64)
       e = Launch<double, false>::step((const InstDesc<double>*)c->desc[par], (int)c->inst.size(), c->total_blocks,
                                       kStepBlock, c->stream);
@@ -458,6 +474,59 @@ int lbcad_set_path(lbcad_ctx* c, int32_t path) {
     if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
     c->path = path;
   }
+  return LBCAD_OK;
+}
+
+int lbcad_autotune(lbcad_ctx* c, int32_t reps, int32_t* chosen, float* ms_per_cfg, int32_t ncfg) {
+  if (!c || reps < 1) return LBCAD_E_INVALID_ARG;
+  DeviceGuard dg(c->device);
+  const int n = (c->prec == LBCAD_FP64) ? LaunchFused<double, false>::num_configs()
+                                        : LaunchFused<float, true>::num_configs();
+  const int par = (int)(c->step & 1);
+  cudaEvent_t e0, e1;
+  CK(c, cudaEventCreate(&e0));
+  CK(c, cudaEventCreate(&e1));
+  int best = -1;
+  float best_ms = 0.f;
+  for (int k = 0; k < n; ++k) {
+    float ms = -1.f;
+    if (prepare_fused(c, k) == LBCAD_OK) {
+      // each launch recomputes step t -> t+1 into the output buffers; the state at t is
+      // read only, so the simulation does not advance
+      cudaError_t e = launch_fused(c, par);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_fused(c, par);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ms /= reps;
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return fail(c, LBCAD_E_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+      }
+      if (best < 0 || ms < best_ms) { best = k; best_ms = ms; }
+    }
+    if (ms_per_cfg && k < ncfg) ms_per_cfg[k] = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0) return fail(c, LBCAD_E_UNSUPPORTED, "no fused tile shape fits");
+  int r = prepare_fused(c, best);
+  if (r) return r;
+  drop_graph(c);
+  if (chosen) *chosen = best;
+  return LBCAD_OK;
+}
+
+int lbcad_set_tiles(lbcad_ctx* c, int32_t cfg) {
+  if (!c) return LBCAD_E_INVALID_ARG;
+  DeviceGuard dg(c->device);
+  const int n = (c->prec == LBCAD_FP64) ? LaunchFused<double, false>::num_configs()
+                                        : LaunchFused<float, true>::num_configs();
+  if (cfg < 0 || cfg >= n) return fail(c, LBCAD_E_INVALID_ARG, "tile shape index out of range");
+  int r = prepare_fused(c, cfg);
+  if (r) return r;
+  drop_graph(c);
   return LBCAD_OK;
 }
 

@@ -74,6 +74,9 @@ _SIGS = {
     "lbcad_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "lbcad_set_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "lbcad_set_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "lbcad_set_tiles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "lbcad_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _P(ctypes.c_int32), _P(ctypes.c_float),
+                                      ctypes.c_int32]),
     "lbcad_get_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p,
                                         ctypes.c_size_t, ctypes.c_int32]),
     "lbcad_set_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p,
@@ -262,6 +265,17 @@ class Simulation:
 
     def set_path(self, path: int):
         _check(library().lbcad_set_path(self.ctx, int(path)), self.ctx)
+
+    def autotune(self, reps: int = 5):
+        """Time each fused tile shape without advancing the state; keep the fastest.
+        Returns (chosen index, ms per launch of each candidate)."""
+        chosen = ctypes.c_int32(-1)
+        ms = (ctypes.c_float * 8)()
+        _check(library().lbcad_autotune(self.ctx, int(reps), ctypes.byref(chosen), ms, 8), self.ctx)
+        return chosen.value, [v for v in ms][:3]
+
+    def set_tiles(self, cfg: int):
+        _check(library().lbcad_set_tiles(self.ctx, int(cfg)), self.ctx)
 
     def set_graph(self, steps_per_graph: int):
         _check(library().lbcad_set_graph(self.ctx, int(steps_per_graph)), self.ctx)

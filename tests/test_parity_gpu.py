@@ -252,3 +252,28 @@ def test_path_switch_mid_run():
     sim.step(2)
     ref = _oracle(shape, seed=5, **kw).step(8)
     _compare_fp64(sim.get_fields(0), ref)
+
+
+def test_tile_shapes_and_autotune_give_identical_results():
+    """The per-site arithmetic does not depend on the tile shape; autotuning times the
+    shapes without advancing the state."""
+    shape = (70, 36, 20)
+    kw = dict(R=6.0, p0=10.0, zeta=0.01)
+    ref = L.Simulation([shape], [_lib_params(shape, L.FP32, **kw)], seed=4)
+    ref.step(5)
+    fr = ref.get_fields(0)
+    for cfg in range(3):
+        s = L.Simulation([shape], [_lib_params(shape, L.FP32, **kw)], seed=4)
+        s.set_tiles(cfg)
+        s.step(5)
+        f = s.get_fields(0)
+        for k in fr:
+            assert np.array_equal(f[k], fr[k]), (cfg, k)
+    s = L.Simulation([shape], [_lib_params(shape, L.FP32, **kw)], seed=4)
+    s.step(2)
+    chosen, ms = s.autotune(3)
+    assert 0 <= chosen < 3 and s.step_count == 2
+    s.step(3)
+    f = s.get_fields(0)
+    for k in fr:
+        assert np.array_equal(f[k], fr[k]), k
