@@ -28,7 +28,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "hybrid-step MLUPS & % of HBM roofline, FP32 vs plain FP64 at stated error"
-BYTES_PER_SITE = {"fp32": 200, "fp64": 400}  # state read once + written once: (19 + 5 + 1) x 2 words
+BYTES_PER_SITE = {"fp32": 200, "fp64": 400}
+TILE_NAMES = ["32x8", "32x16", "64x8", "32x8-pipelined-8+8", "32x8-pipelined-6+10"]  # state read once + written once: (19 + 5 + 1) x 2 words
 
 
 def workload_params(L, n, prec):
@@ -221,7 +222,7 @@ def run_batch(args):
     sites = sim.sites()
     print(json.dumps({"metric": METRIC + " (batched 64 uneven droplets)", "value": sites / (ms * 1e-3) / 1e6,
                       "unit": "MLUPS", "n_gpus": 1, "steps": K, "ms_per_step": ms, "sites": sites,
-                      "dtype": "f32", "data": "synthetic", "tiles": {"chosen": cfg, "ms_per_cfg": tms},
+                      "dtype": "f32", "data": "synthetic", "tiles": {"chosen": TILE_NAMES[cfg], "ms_per_cfg": dict(zip(TILE_NAMES, tms))},
                       "config": {"workload": "64 droplets, edges from {48,64,80,96}, seed 7"},
                       "clocks": clk.summary()}))
     sim.close()
@@ -343,7 +344,7 @@ def main():
                            "box": [n, n, n], "parallelism": "replicas" if world > 1 else "single",
                            "l2": "state %.0f MB per step > 129 MB L2, no flush" % (224 * N / 1e6)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "tiles": {"chosen": ["32x8", "32x16", "64x8"][tile_cfg], "ms_per_cfg": tile_ms},
+                "tiles": {"chosen": TILE_NAMES[tile_cfg], "ms_per_cfg": dict(zip(TILE_NAMES, tile_ms))},
                 "gpu_launches": K, "clocks": clk.summary(), "fp64_gpu": fp64,
                 "speedup_fp32_vs_fp64": (value / world / fp64["mlups"]) if fp64 else None,
                 "observables_finite": finite}

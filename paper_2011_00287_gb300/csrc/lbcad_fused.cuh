@@ -276,6 +276,199 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
   }
 }
 
+// ---------------------------------------------------------------- pipelined variant
+// Same per-site arithmetic, different schedule: 32x8 tiles, 16 warps.  The first NS
+// threads compute sigma, mu and H of plane k+1 (the 340 sigma-tile sites in rounds)
+// while the other 512 - NS threads compute the output of plane k-1 (one site each), in
+// the same phase; one barrier per plane.  The output half carries the population pulls
+// and the stores, so memory traffic overlaps the sigma arithmetic.  Planes for the next
+// phase arrive by cp.async during the phase.
+// Rings: Q/psi 6 planes (k-2 .. k+3), sigma/mu 4 (k-2 .. k+1), H 3 (k-1 .. k+1),
+// u 4 (k-2 .. k+1).
+template <int NS_>
+struct PipeGeom {
+  static constexpr int TX = 32, TY = 8, NT = 512, NS = NS_, NO = NT - NS;
+  static constexpr int QW = TX + 4, QH = TY + 4, QP = QW * QH;
+  static constexpr int SW = TX + 2, SH = TY + 2, SP = SW * SH;
+  static constexpr int IP = TX * TY;
+  static constexpr int NQS = 6, NSS = 4, NHS = 3, NUS = 4;
+  static_assert(QP <= NT && SP <= NT && SP <= 2 * NS && NO >= IP, "site counts per thread");
+  template <typename T>
+  static constexpr size_t bytes() {
+    return ((size_t)NQS * 6 * QP + (size_t)NSS * 10 * SP + (size_t)NHS * 5 * IP + (size_t)NUS * 3 * SP) * sizeof(T) +
+           (QW + QH) * sizeof(int);
+  }
+};
+
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  if constexpr (sizeof(T) == 4) cp_async4(dst, src); else cp_async8(dst, src);
+}
+
+template <typename T, bool SHIFT, int NS>
+__global__ void __launch_bounds__(512, 1)
+    k_step_pipe(const InstDesc<T>* __restrict__ D, const FusedTile* __restrict__ tiles, int ntiles, long long total) {
+  using G = PipeGeom<NS>;
+  constexpr int QW = G::QW, QP = G::QP, SW = G::SW, SP = G::SP, TX = G::TX;
+  constexpr int QSLOT = 6 * QP, SSLOT = 10 * SP, HSLOT = 5 * G::IP, USLOT = 3 * SP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sQ = reinterpret_cast<T*>(smem_raw);
+  T* sS = sQ + G::NQS * QSLOT;
+  T* sH = sS + G::NSS * SSLOT;
+  T* sU = sH + G::NHS * HSLOT;
+  int* xmap = reinterpret_cast<int*>(sU + G::NUS * USLOT);
+  int* ymap = xmap + QW;
+  const int tid = threadIdx.x;
+  auto q6 = [](int p) { return (p + 12) % 6; };
+  auto s4 = [](int p) { return (p + 12) % 4; };
+  auto h3 = [](int p) { return (p + 12) % 3; };
+
+  const long long begin = (total * blockIdx.x) / gridDim.x;
+  const long long end = (total * (blockIdx.x + 1)) / gridDim.x;
+  long long it = begin;
+  while (it < end) {
+    int lo = 0, hi = ntiles - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tiles[mid].start <= it) lo = mid; else hi = mid - 1;
+    }
+    const FusedTile tl = tiles[lo];
+    const InstDesc<T>& I = D[tl.inst];
+    const int nx = I.nx, ny = I.ny, nz = I.nz;
+    const long long N = I.N;
+    const long long plane = (long long)nx * ny;
+    const int zb = (int)(it - tl.start);
+    const long long seg_end = end < tl.start + tl.nz ? end : tl.start + tl.nz;
+    const int ze = (int)(seg_end - tl.start);
+    it = seg_end;
+    const Coef<T> cf = I.c;
+    const T* __restrict__ qin = I.q_in;
+    const T* __restrict__ pin = I.psi_in;
+    const T* __restrict__ uin = I.u_in;
+    const T* __restrict__ gin = I.g_in;
+
+    __syncthreads();
+    for (int k = tid; k < QW; k += G::NT) xmap[k] = wrapmod(tl.x0 + k - 2, nx);
+    for (int k = tid; k < G::QH; k += G::NT) ymap[k] = wrapmod(tl.y0 + k - 2, ny) * nx;
+    __syncthreads();
+    // this thread's load sites (at most one Q/psi site and one u site per plane)
+    int qoff = 0, uoff = 0;
+    if (tid < QP) {
+      const int ly = tid / QW, lx = tid - ly * QW;
+      qoff = ymap[ly] + xmap[lx];
+    }
+    if (tid < SP) {
+      const int sy = tid / SW, sx = tid - sy * SW;
+      uoff = ymap[sy + 1] + xmap[sx + 1];
+    }
+    auto issue_q = [&](int p) {
+      if (tid < QP) {
+        T* dst = sQ + q6(p) * QSLOT + tid;
+        const long long gs = (long long)wrapmod(p, nz) * plane + qoff;
+#pragma unroll
+        for (int f = 0; f < 5; ++f) cp_async_elem(dst + f * QP, qin + f * N + gs);
+        cp_async_elem(dst + 5 * QP, pin + gs);
+      }
+    };
+    auto issue_u = [&](int p) {
+      if (tid < SP) {
+        T* dst = sU + s4(p) * USLOT + tid;
+        const long long gs = (long long)wrapmod(p, nz) * plane + uoff;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) cp_async_elem(dst + a * SP, uin + a * N + gs);
+      }
+    };
+    issue_q(zb - 2);
+    issue_q(zb - 1);
+    issue_q(zb);
+    cp_async_commit_wait_all();
+    __syncthreads();
+
+    for (int k = zb - 2; k <= ze; ++k) {
+      issue_q(k + 3);
+      issue_u(k + 1);
+      if (tid < G::NS) {
+        // sigma, mu (and H on interior sites) of plane k+1
+#pragma unroll 1
+        for (int ss = tid; k + 1 <= ze && ss < SP; ss += G::NS) {
+          const int sy = ss / SW, sx = ss - sy * SW;
+          SmemFieldsAcc<T, QW, QP> acc;
+          const int qc = (sy + 1) * QW + (sx + 1);
+#pragma unroll
+          for (int j = 0; j < 3; ++j) acc.pl[j] = sQ + q6(k + j) * QSLOT + qc;
+          T q0[5], p0, dq[3][5], lapq[5], dp[3], lapp, hp[6];
+          gather_fields<T>(acc, q0, p0, dq, lapq, dp, lapp, hp);
+          T H[5], sig[9], mu;
+          local_fields<T>(cf, q0, p0, dq, lapq, dp, lapp, hp, H, mu, sig);
+          T* dst = sS + s4(k + 1) * SSLOT + sy * SW + sx;
+#pragma unroll
+          for (int c = 0; c < 9; ++c) dst[c * SP] = sig[c];
+          dst[9 * SP] = mu;
+          if (sx >= 1 && sx <= TX && sy >= 1 && sy <= G::TY) {
+            T* hd = sH + h3(k + 1) * HSLOT + (sy - 1) * TX + (sx - 1);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) hd[c * G::IP] = H[c];
+          }
+        }
+      } else if (k - 1 >= zb) {
+        // output of plane z = k-1
+        const int z = k - 1;
+        const long long zo[3] = {(long long)wrapmod(z - 1, nz) * plane, (long long)z * plane,
+                                 (long long)wrapmod(z + 1, nz) * plane};
+        const int site = tid - G::NS;
+        const int tx = site % TX, ty = site / TX;
+        if (site < G::IP && tl.x0 + tx < nx && tl.y0 + ty < ny) {
+          SmemUpdateAcc<T, QW, QP, SW, SP> acc;
+          const int qc = (ty + 2) * QW + (tx + 2);
+          const int sc = (ty + 1) * SW + (tx + 1);
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            acc.qpl[j] = sQ + q6(z - 1 + j) * QSLOT + qc;
+            acc.spl[j] = sS + s4(z - 1 + j) * SSLOT + sc;
+            acc.upl[j] = sU + s4(z - 1 + j) * USLOT + sc;
+          }
+          T F[3], lapmu, Wg[3][3], q0[5], qf[6][5], p0, pf[6], u0[3], uf[6];
+          gather_update<T>(acc, F, lapmu, Wg, q0, qf, p0, pf, u0, uf);
+          const int pxo[3] = {xmap[tx + 1], xmap[tx + 2], xmap[tx + 3]};
+          const int pyo[3] = {ymap[ty + 1], ymap[ty + 2], ymap[ty + 3]};
+          T g[19];
+#pragma unroll
+          for (int i = 0; i < 19; ++i) {
+            const int cx = lat_c(i, 0), cy = lat_c(i, 1), cz = lat_c(i, 2);
+            g[i] = ld(gin + i * N + zo[1 - cz] + pyo[1 - cy] + pxo[1 - cx]);
+          }
+          T Hs[5];
+#pragma unroll
+          for (int c = 0; c < 5; ++c) Hs[c] = sH[h3(z) * HSLOT + c * G::IP + site];
+          T qn[5], pn, u[3];
+          update_math<T, SHIFT>(cf, F, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hs, g, qn, pn, u);
+          const long long s = zo[1] + pyo[1] + pxo[1];
+#pragma unroll
+          for (int c = 0; c < 5; ++c) I.q_out[c * N + s] = qn[c];
+          I.psi_out[s] = pn;
+#pragma unroll
+          for (int i = 0; i < 19; ++i) I.g_out[i * N + s] = g[i];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) I.u_out[a * N + s] = u[a];
+        }
+      }
+      cp_async_commit_wait_all();
+      __syncthreads();
+    }
+  }
+}
+
 template <typename T, bool SHIFT, int TX, int TY>
 cudaError_t launch_cfg(const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles, long long total, int grid,
                        cudaStream_t s) {
@@ -301,7 +494,28 @@ cudaError_t prepare_cfg(FusedCfg* cfg) {
 // 64x8 (one block per SM, fewer redundant halo sites).  FP64 only fits 32x8.
 template <typename T, bool SHIFT>
 int LaunchFused<T, SHIFT>::num_configs() {
-  return sizeof(T) == 4 ? 3 : 1;
+  return sizeof(T) == 4 ? 5 : 1;
+}
+
+template <typename T, bool SHIFT, int NS>
+cudaError_t prepare_pipe(FusedCfg* cfg) {
+  using G = PipeGeom<NS>;
+  auto k = k_step_pipe<T, SHIFT, NS>;
+  cfg->tx = G::TX;
+  cfg->ty = G::TY;
+  cfg->threads = G::NT;
+  cfg->smem = G::template bytes<T>();
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg->smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cfg->blocks_per_sm, k, G::NT, cfg->smem);
+}
+
+template <typename T, bool SHIFT, int NS>
+cudaError_t launch_pipe(const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles, long long total, int grid,
+                        cudaStream_t s) {
+  using G = PipeGeom<NS>;
+  k_step_pipe<T, SHIFT, NS><<<grid, G::NT, G::template bytes<T>(), s>>>(d_desc, tiles, ntiles, total);
+  return cudaGetLastError();
 }
 
 template <typename T, bool SHIFT>
@@ -309,6 +523,8 @@ cudaError_t LaunchFused<T, SHIFT>::prepare(int cfg_index, FusedCfg* cfg) {
   if constexpr (sizeof(T) == 4) {
     if (cfg_index == 1) return prepare_cfg<T, SHIFT, 32, 16>(cfg);
     if (cfg_index == 2) return prepare_cfg<T, SHIFT, 64, 8>(cfg);
+    if (cfg_index == 3) return prepare_pipe<T, SHIFT, 256>(cfg);
+    if (cfg_index == 4) return prepare_pipe<T, SHIFT, 192>(cfg);
   }
   if (cfg_index == 0) return prepare_cfg<T, SHIFT, 32, 8>(cfg);
   return cudaErrorInvalidValue;
@@ -320,6 +536,8 @@ cudaError_t LaunchFused<T, SHIFT>::step(int cfg_index, const InstDesc<T>* d_desc
   if constexpr (sizeof(T) == 4) {
     if (cfg_index == 1) return launch_cfg<T, SHIFT, 32, 16>(d_desc, tiles, ntiles, total, grid, s);
     if (cfg_index == 2) return launch_cfg<T, SHIFT, 64, 8>(d_desc, tiles, ntiles, total, grid, s);
+    if (cfg_index == 3) return launch_pipe<T, SHIFT, 256>(d_desc, tiles, ntiles, total, grid, s);
+    if (cfg_index == 4) return launch_pipe<T, SHIFT, 192>(d_desc, tiles, ntiles, total, grid, s);
   }
   if (cfg_index == 0) return launch_cfg<T, SHIFT, 32, 8>(d_desc, tiles, ntiles, total, grid, s);
   return cudaErrorInvalidValue;

@@ -272,7 +272,7 @@ class Simulation:
         chosen = ctypes.c_int32(-1)
         ms = (ctypes.c_float * 8)()
         _check(library().lbcad_autotune(self.ctx, int(reps), ctypes.byref(chosen), ms, 8), self.ctx)
-        return chosen.value, [v for v in ms][:3]
+        return chosen.value, [v for v in ms][:5]
 
     def set_tiles(self, cfg: int):
         _check(library().lbcad_set_tiles(self.ctx, int(cfg)), self.ctx)
