@@ -179,6 +179,29 @@ int lbcad_set_fields(lbcad_ctx* c, int32_t inst, uint32_t mask, const void* src,
  * reduced value is not finite.  Synchronises the context's stream. */
 int lbcad_observables(lbcad_ctx* c, int32_t inst, lbcad_obs* out);
 
+/* Adjoint (reverse mode) of nsteps hybrid steps of a single-instance context.
+ * Objective: J = |X(t0 + nsteps) - X(t0)|^2 / 2, X the droplet centroid (per-axis circular
+ * mean of phi_c = (1 + psi)/2, minimum-image displacement), t0 the current step.
+ * Runs the forward from the current state (the context advances by nsteps, as with
+ * lbcad_step), storing a checkpoint every ckpt_every steps; then, segment by segment in
+ * reverse, replays the segment's states and applies the vector-Jacobian product of each
+ * step (per-site Jacobians by forward-mode dual numbers through the step's own
+ * arithmetic).  Writes dJ/dzeta and dJ/dq0 (accumulated in FP64; q0 enters through H and
+ * sigma, the initial Q held fixed), dJ/dQ(t0) for the five stored Q components
+ * ([5][z][y][x], host FP64, may be NULL) and J itself.  Device memory grows by
+ * (ceil(nsteps/ckpt_every) + ckpt_every + 2) states plus 154 values per site, owned by the
+ * context until lbcad_destroy.  The paper has no adjoint; this is the differentiation form
+ * of the step (gradient of the droplet's drift with respect to activity, chirality and
+ * the initial order). */
+int lbcad_adjoint(lbcad_ctx* c, int64_t nsteps, int32_t ckpt_every, double* dJ_dzeta, double* dJ_dq0,
+                  double* dJ_dQ0, double* J);
+
+/* Gradient of the last lbcad_adjoint's J with respect to the whole state at its start,
+ * in the lbcad_get_fields layout and convention (G = pre-collision populations f_i, U =
+ * velocity of the previous step, Q, PSI; RHO is not a state and is rejected).  FP64 host
+ * buffer of >= 8 n (components) bytes. */
+int lbcad_adjoint_fields(lbcad_ctx* c, uint32_t mask, void* dst, size_t bytes);
+
 /* Number of instances, lattice of one instance, steps taken so far. */
 int lbcad_num_instances(const lbcad_ctx* c);
 int lbcad_instance_grid(const lbcad_ctx* c, int32_t inst, lbcad_grid* out);

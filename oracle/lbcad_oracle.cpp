@@ -80,7 +80,54 @@ struct Box {
   }
 };
 
-typedef double M3[3][3];
+// Everything below is templated on the scalar type R: R = double is the oracle; R = Dual
+// (a value and one tangent, defined further down) carries forward-mode derivatives through
+// the same arithmetic.
+template <typename R>
+using M3 = R[3][3];
+
+// Parameters promoted to R (so that zeta and q0 can carry tangents).
+template <typename R>
+struct PR {
+  R tau, rho0, A0, chi0, chis, K, q0, gammaQ, xi, a, b, kphi, M, W, zeta;
+  int integrator, coupling;
+};
+
+template <typename R>
+PR<R> promote(const orc_params& p) {
+  PR<R> r;
+  r.tau = p.tau; r.rho0 = p.rho0; r.A0 = p.A0; r.chi0 = p.chi0; r.chis = p.chis; r.K = p.K; r.q0 = p.q0;
+  r.gammaQ = p.gammaQ; r.xi = p.xi; r.a = p.a; r.b = p.b; r.kphi = p.kphi; r.M = p.M; r.W = p.W; r.zeta = p.zeta;
+  r.integrator = p.integrator;
+  r.coupling = p.coupling;
+  return r;
+}
+
+inline double max0(double v) { return std::fmax(v, 0.0); }
+inline double min0(double v) { return std::fmin(v, 0.0); }
+
+// Forward-mode dual number: a value and one directional derivative.  Every operation of
+// the step is +, -, *, / or a comparison, so these rules differentiate it exactly; at the
+// switching points of max(u, 0) and of the upwind face choice the derivative of the
+// branch taken is used.
+struct Dual {
+  double v, d;
+  Dual() : v(0.0), d(0.0) {}
+  Dual(double x) : v(x), d(0.0) {}
+  Dual(double x, double dx) : v(x), d(dx) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) { return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)); }
+inline Dual& operator+=(Dual& a, Dual b) { return a = a + b; }
+inline Dual& operator-=(Dual& a, Dual b) { return a = a - b; }
+inline Dual& operator*=(Dual& a, Dual b) { return a = a * b; }
+inline bool operator>(Dual a, Dual b) { return a.v > b.v; }
+inline bool operator<(Dual a, Dual b) { return a.v < b.v; }
+inline Dual max0(Dual a) { return a.v > 0.0 ? a : Dual(0.0); }
+inline Dual min0(Dual a) { return a.v < 0.0 ? a : Dual(0.0); }
 
 int eps(int a, int b, int c) {
   if (a == b || b == c || a == c) return 0;
@@ -90,65 +137,72 @@ int eps(int a, int b, int c) {
 }
 
 // The five stored components are xx, xy, xz, yy, yz; zz = -xx - yy.
-void q_full(const double* q5, long N, long s, M3 Q) {
-  double xx = q5[0 * N + s], xy = q5[1 * N + s], xz = q5[2 * N + s];
-  double yy = q5[3 * N + s], yz = q5[4 * N + s];
+template <typename R>
+void q_full(const R* q5, long N, long s, M3<R> Q) {
+  R xx = q5[0 * N + s], xy = q5[1 * N + s], xz = q5[2 * N + s];
+  R yy = q5[3 * N + s], yz = q5[4 * N + s];
   Q[0][0] = xx; Q[0][1] = xy; Q[0][2] = xz;
   Q[1][0] = xy; Q[1][1] = yy; Q[1][2] = yz;
   Q[2][0] = xz; Q[2][1] = yz; Q[2][2] = -xx - yy;
 }
 
-void q_store(const M3 Q, double* q5, long N, long s) {
+template <typename R>
+void q_store(const M3<R> Q, R* q5, long N, long s) {
   q5[0 * N + s] = Q[0][0]; q5[1 * N + s] = Q[0][1]; q5[2 * N + s] = Q[0][2];
   q5[3 * N + s] = Q[1][1]; q5[4 * N + s] = Q[1][2];
 }
 
 // Symmetric traceless projection.
-void sym_traceless(const M3 A, M3 out) {
-  double tr = (A[0][0] + A[1][1] + A[2][2]) / 3.0;
+template <typename R>
+void sym_traceless(const M3<R> A, M3<R> out) {
+  R tr = (A[0][0] + A[1][1] + A[2][2]) / 3.0;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) out[i][j] = 0.5 * (A[i][j] + A[j][i]) - (i == j ? tr : 0.0);
 }
 
-void matmul(const M3 A, const M3 B, M3 C) {
+template <typename R>
+void matmul(const M3<R> A, const M3<R> B, M3<R> C) {
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      double s = 0.0;
+      R s = 0.0;
       for (int k = 0; k < 3; ++k) s += A[i][k] * B[k][j];
       C[i][j] = s;
     }
 }
 
-double trace_prod(const M3 A, const M3 B) {  // tr(A B) = A_ij B_ji
-  double s = 0.0;
+template <typename R>
+R trace_prod(const M3<R> A, const M3<R> B) {  // tr(A B) = A_ij B_ji
+  R s = 0.0;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) s += A[i][j] * B[j][i];
   return s;
 }
 
 // Per-site stencil results (Sec. 3: finite differences on Q and psi).
+template <typename R>
 struct Derivs {
-  double dQ[3][3][3];  // dQ[a][i][j] = d_a Q_ij
-  double lapQ[3][3];
-  double dpsi[3];
-  double lappsi;
-  double hpsi[3][3];
+  R dQ[3][3][3];  // dQ[a][i][j] = d_a Q_ij
+  R lapQ[3][3];
+  R dpsi[3];
+  R lappsi;
+  R hpsi[3][3];
 };
 
 // Isotropic D3Q19 gradient 3 sum_i w_i c_ia f(x+c_i) and Laplacian 6 sum_i w_i (f(x+c_i)-f(x));
 // Hessian of psi: three-point second difference on the diagonal, four corners off it.
-void derivs_at(const Box& B, const double* q5, const double* psi, int x, int y, int z, Derivs& d) {
+template <typename R>
+void derivs_at(const Box& B, const R* q5, const R* psi, int x, int y, int z, Derivs<R>& d) {
   long N = B.n();
   long s = B.at(x, y, z);
-  M3 Q0;
+  M3<R> Q0;
   q_full(q5, N, s, Q0);
-  double p0 = psi[s];
-  std::memset(&d, 0, sizeof(d));
+  R p0 = psi[s];
+  d = Derivs<R>();
   for (int i = 1; i < NQ; ++i) {
     long n = B.at(x + CV[i][0], y + CV[i][1], z + CV[i][2]);
-    M3 Qn;
+    M3<R> Qn;
     q_full(q5, N, n, Qn);
-    double w = wgt(i);
+    R w = wgt(i);
     for (int a = 0; a < 3; ++a) {
       if (CV[i][a] == 0) continue;
       for (int p = 0; p < 3; ++p)
@@ -168,37 +222,39 @@ void derivs_at(const Box& B, const double* q5, const double* psi, int x, int y, 
       if (b == a) continue;
       int eb[3] = {0, 0, 0};
       eb[b] = 1;
-      double spp = psi[B.at(x + ea[0] + eb[0], y + ea[1] + eb[1], z + ea[2] + eb[2])];
-      double spm = psi[B.at(x + ea[0] - eb[0], y + ea[1] - eb[1], z + ea[2] - eb[2])];
-      double smp = psi[B.at(x - ea[0] + eb[0], y - ea[1] + eb[1], z - ea[2] + eb[2])];
-      double smm = psi[B.at(x - ea[0] - eb[0], y - ea[1] - eb[1], z - ea[2] - eb[2])];
+      R spp = psi[B.at(x + ea[0] + eb[0], y + ea[1] + eb[1], z + ea[2] + eb[2])];
+      R spm = psi[B.at(x + ea[0] - eb[0], y + ea[1] - eb[1], z + ea[2] - eb[2])];
+      R smp = psi[B.at(x - ea[0] + eb[0], y - ea[1] + eb[1], z - ea[2] + eb[2])];
+      R smm = psi[B.at(x - ea[0] - eb[0], y - ea[1] - eb[1], z - ea[2] - eb[2])];
       d.hpsi[a][b] = 0.25 * (spp - spm - smp + smm);
     }
   }
 }
 
-// Local quantities at one site: H (Eq. 2, Eq. 5), mu (Eq. 1, Eq. 5), free-energy density
+// Local<R> quantities at one site: H (Eq. 2, Eq. 5), mu (Eq. 1, Eq. 5), free-energy density
 // (Eq. 5) and the three parts of the stress (Eq. 3, Eq. 4).
+template <typename R>
 struct Local {
-  M3 H;
-  double mu;
-  double fden;
-  M3 sE;  // pressure + elastic + interfacial (Ericksen) stress
-  M3 sR;  // reactive Beris-Edwards stress: flow-aligning xi terms + antisymmetric part
-  M3 sA;  // active stress
+  M3<R> H;
+  R mu;
+  R fden;
+  M3<R> sE;  // pressure + elastic + interfacial (Ericksen) stress
+  M3<R> sR;  // reactive Beris-Edwards stress: flow-aligning xi terms + antisymmetric part
+  M3<R> sA;  // active stress
 };
 
-void local_at(const orc_params& P, const M3 Q, double psi, const Derivs& d, Local& L) {
-  const double chi = P.chi0 + P.chis * (1.0 + psi);
-  M3 QQ;
+template <typename R>
+void local_at(const PR<R>& P, const M3<R> Q, R psi, const Derivs<R>& d, Local<R>& L) {
+  const R chi = P.chi0 + P.chis * (1.0 + psi);
+  M3<R> QQ;
   matmul(Q, Q, QQ);
-  const double trQ2 = trace_prod(Q, Q);
-  const double trQ3 = trace_prod(QQ, Q);
+  const R trQ2 = trace_prod(Q, Q);
+  const R trQ3 = trace_prod(QQ, Q);
   // C_ab = eps_amn d_m Q_nb  (the curl of Q)
-  M3 C;
+  M3<R> C;
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) {
-      double s = 0.0;
+      R s = 0.0;
       for (int m = 0; m < 3; ++m)
         for (int n = 0; n < 3; ++n) {
           int e = eps(a, m, n);
@@ -206,12 +262,12 @@ void local_at(const orc_params& P, const M3 Q, double psi, const Derivs& d, Loca
         }
       C[a][b] = s;
     }
-  double g2 = d.dpsi[0] * d.dpsi[0] + d.dpsi[1] * d.dpsi[1] + d.dpsi[2] * d.dpsi[2];
+  R g2 = d.dpsi[0] * d.dpsi[0] + d.dpsi[1] * d.dpsi[1] + d.dpsi[2] * d.dpsi[2];
   // -dF/dQ before projection
-  M3 Hraw;
+  M3<R> Hraw;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      double dij = (i == j) ? 1.0 : 0.0;
+      R dij = (i == j) ? 1.0 : 0.0;
       Hraw[i][j] = -P.A0 * (1.0 - chi / 3.0) * Q[i][j] + P.A0 * chi * (QQ[i][j] - dij * trQ2 / 3.0) -
                    P.A0 * chi * trQ2 * Q[i][j] + P.K * d.lapQ[i][j] - 2.0 * P.K * P.q0 * (C[i][j] + C[j][i]) -
                    4.0 * P.K * P.q0 * P.q0 * Q[i][j] - P.W * (d.dpsi[i] * d.dpsi[j] - dij * g2 / 3.0);
@@ -219,7 +275,7 @@ void local_at(const orc_params& P, const M3 Q, double psi, const Derivs& d, Loca
   sym_traceless(Hraw, L.H);
 
   // mu = dF/dpsi
-  double divQ_dpsi = 0.0, Q_hess = 0.0;
+  R divQ_dpsi = 0.0, Q_hess = 0.0;
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) {
       divQ_dpsi += d.dQ[a][a][b] * d.dpsi[b];
@@ -229,27 +285,27 @@ void local_at(const orc_params& P, const M3 Q, double psi, const Derivs& d, Loca
          P.A0 * P.chis * (-trQ2 / 6.0 - trQ3 / 3.0 + trQ2 * trQ2 / 4.0) - 2.0 * P.W * (divQ_dpsi + Q_hess);
 
   // free-energy density of Eq. 5
-  double grad2 = 0.0;
+  R grad2 = 0.0;
   for (int a = 0; a < 3; ++a)
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) grad2 += d.dQ[a][i][j] * d.dQ[a][i][j];
-  double QC = 0.0;
+  R QC = 0.0;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) QC += Q[i][j] * C[i][j];
-  double anch = 0.0;
+  R anch = 0.0;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) anch += d.dpsi[i] * Q[i][j] * d.dpsi[j];
   L.fden = -0.5 * P.a * psi * psi + 0.25 * P.b * psi * psi * psi * psi + 0.5 * P.kphi * g2 +
            P.A0 * (0.5 * (1.0 - chi / 3.0) * trQ2 - chi / 3.0 * trQ3 + chi / 4.0 * trQ2 * trQ2) +
            0.5 * P.K * grad2 + 2.0 * P.K * P.q0 * QC + 2.0 * P.K * P.q0 * P.q0 * trQ2 + P.W * anch;
-  const double P0 = psi * L.mu - L.fden;
+  const R P0 = psi * L.mu - L.fden;
 
   // Pi_bgn = dF/d(d_b Q_gn) = K d_b Q_gn + 2 K q0 eps_mbg Q_mn
-  double Pi[3][3][3];
+  R Pi[3][3][3];
   for (int b = 0; b < 3; ++b)
     for (int g = 0; g < 3; ++g)
       for (int n = 0; n < 3; ++n) {
-        double s = P.K * d.dQ[b][g][n];
+        R s = P.K * d.dQ[b][g][n];
         for (int m = 0; m < 3; ++m) {
           int e = eps(m, b, g);
           if (e) s += 2.0 * P.K * P.q0 * e * Q[m][n];
@@ -258,64 +314,67 @@ void local_at(const orc_params& P, const M3 Q, double psi, const Derivs& d, Loca
       }
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) {
-      double s = -(a == b ? P0 : 0.0);
+      R s = -(a == b ? P0 : 0.0);
       for (int g = 0; g < 3; ++g)
         for (int n = 0; n < 3; ++n) s -= d.dQ[a][g][n] * Pi[b][g][n];
-      double Qdpsi = 0.0;
+      R Qdpsi = 0.0;
       for (int g = 0; g < 3; ++g) Qdpsi += Q[b][g] * d.dpsi[g];
       s -= d.dpsi[a] * (P.kphi * d.dpsi[b] + 2.0 * P.W * Qdpsi);
       L.sE[a][b] = s;
     }
 
   // reactive stress with Qt = Q + I/3
-  M3 Qt;
+  M3<R> Qt;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) Qt[i][j] = Q[i][j] + (i == j ? 1.0 / 3.0 : 0.0);
-  M3 HQt, QtH, QH, HQ;
+  M3<R> HQt, QtH, QH, HQ;
   matmul(L.H, Qt, HQt);
   matmul(Qt, L.H, QtH);
   matmul(Q, L.H, QH);
   matmul(L.H, Q, HQ);
-  const double trQH = trace_prod(Q, L.H);
+  const R trQH = trace_prod(Q, L.H);
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b)
       L.sR[a][b] = -P.xi * HQt[a][b] - P.xi * QtH[a][b] + 2.0 * P.xi * Qt[a][b] * trQH + QH[a][b] - HQ[a][b];
 
-  const double phic = 0.5 * (1.0 + psi);
+  const R phic = 0.5 * (1.0 + psi);
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) L.sA[a][b] = -P.zeta * phic * Q[a][b];
 }
 
 // Co-rotation term of Beris-Edwards (Eq. 2's strain-rotational part); Wg[a][b] = d_b u_a.
-void corotation(const M3 Wg, const M3 Q, double xi, M3 S) {
-  M3 D, Om, Qt;
+template <typename R>
+void corotation(const M3<R> Wg, const M3<R> Q, R xi, M3<R> S) {
+  M3<R> D, Om, Qt;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
       D[i][j] = 0.5 * (Wg[i][j] + Wg[j][i]);
       Om[i][j] = 0.5 * (Wg[i][j] - Wg[j][i]);
       Qt[i][j] = Q[i][j] + (i == j ? 1.0 / 3.0 : 0.0);
     }
-  M3 A, Bm;
+  M3<R> A, Bm;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
       A[i][j] = xi * D[i][j] + Om[i][j];
       Bm[i][j] = xi * D[i][j] - Om[i][j];
     }
-  M3 T1, T2;
+  M3<R> T1, T2;
   matmul(A, Qt, T1);
   matmul(Qt, Bm, T2);
-  const double trQW = trace_prod(Q, Wg);
+  const R trQW = trace_prod(Q, Wg);
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) S[i][j] = T1[i][j] + T2[i][j] - 2.0 * xi * Qt[i][j] * trQW;
 }
 
 // Isotropic gradient of a vector field at a site: Wg[a][b] = d_b u_a.
-void vec_grad_at(const Box& B, const double* u, int x, int y, int z, M3 Wg) {
+template <typename R>
+void vec_grad_at(const Box& B, const R* u, int x, int y, int z, M3<R> Wg) {
   long N = B.n();
-  std::memset(Wg, 0, sizeof(M3));
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Wg[a][b] = 0.0;
   for (int i = 1; i < NQ; ++i) {
     long n = B.at(x + CV[i][0], y + CV[i][1], z + CV[i][2]);
-    double w = wgt(i);
+    R w = wgt(i);
     for (int b = 0; b < 3; ++b) {
       if (CV[i][b] == 0) continue;
       for (int a = 0; a < 3; ++a) Wg[a][b] += 3.0 * w * CV[i][b] * u[a * N + n];
@@ -323,23 +382,25 @@ void vec_grad_at(const Box& B, const double* u, int x, int y, int z, M3 Wg) {
   }
 }
 
+template <typename R>
 struct Work {
-  std::vector<double> H, mu, sig, F, unew, fnew, rhsQ, rhsP, Qp, Pp;
+  std::vector<R> H, mu, sig, F, unew, fnew, rhsQ, rhsP, Qp, Pp;
 };
 
 // Stage 1-4 over the whole box: H (5), mu, total stress (9) per site.
-void fields_all(const Box& B, const orc_params& P, const double* q5, const double* psi, double* H5, double* mu,
-                double* sig9, double* sE9, double* sR9, double* sA9, double* fden) {
+template <typename R>
+void fields_all(const Box& B, const PR<R>& P, const R* q5, const R* psi, R* H5, R* mu,
+                R* sig9, R* sE9, R* sR9, R* sA9, R* fden) {
   long N = B.n();
   for (int z = 0; z < B.nz; ++z)
     for (int y = 0; y < B.ny; ++y)
       for (int x = 0; x < B.nx; ++x) {
         long s = B.at(x, y, z);
-        Derivs d;
+        Derivs<R> d;
         derivs_at(B, q5, psi, x, y, z, d);
-        M3 Q;
+        M3<R> Q;
         q_full(q5, N, s, Q);
-        Local L;
+        Local<R> L;
         local_at(P, Q, psi[s], d, L);
         if (H5) q_store(L.H, H5, N, s);
         if (mu) mu[s] = L.mu;
@@ -356,16 +417,17 @@ void fields_all(const Box& B, const orc_params& P, const double* q5, const doubl
 }
 
 // Stage 5: F_a = d_b sigma_ab with the isotropic gradient.
-void force_all(const Box& B, const double* sig9, double* F3) {
+template <typename R>
+void force_all(const Box& B, const R* sig9, R* F3) {
   long N = B.n();
   for (int z = 0; z < B.nz; ++z)
     for (int y = 0; y < B.ny; ++y)
       for (int x = 0; x < B.nx; ++x) {
         long s = B.at(x, y, z);
-        double F[3] = {0, 0, 0};
+        R F[3] = {0, 0, 0};
         for (int i = 1; i < NQ; ++i) {
           long n = B.at(x + CV[i][0], y + CV[i][1], z + CV[i][2]);
-          double w = wgt(i);
+          R w = wgt(i);
           for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b)
               if (CV[i][b]) F[a] += 3.0 * w * CV[i][b] * sig9[(3 * a + b) * N + n];
@@ -375,30 +437,31 @@ void force_all(const Box& B, const double* sig9, double* F3) {
 }
 
 // Stage 6: BGK + Guo forcing (Eq. 7 as read), moments (Eq. 8), streaming (Eq. 6).
-void lb_all(const Box& B, const orc_params& P, const double* f, const double* F3, double* fnew, double* unew) {
+template <typename R>
+void lb_all(const Box& B, const PR<R>& P, const R* f, const R* F3, R* fnew, R* unew) {
   long N = B.n();
-  const double tau = P.tau;
+  const R tau = P.tau;
   for (int z = 0; z < B.nz; ++z)
     for (int y = 0; y < B.ny; ++y)
       for (int x = 0; x < B.nx; ++x) {
         long s = B.at(x, y, z);
-        double rho = 0.0, j[3] = {0, 0, 0};
+        R rho = 0.0, j[3] = {0, 0, 0};
         for (int i = 0; i < NQ; ++i) {
-          double fi = f[i * N + s];
+          R fi = f[i * N + s];
           rho += fi;
           for (int a = 0; a < 3; ++a) j[a] += fi * CV[i][a];
         }
-        double F[3] = {F3[0 * N + s], F3[1 * N + s], F3[2 * N + s]};
-        double u[3];
+        R F[3] = {F3[0 * N + s], F3[1 * N + s], F3[2 * N + s]};
+        R u[3];
         for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * F[a]) / rho;
-        double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        R u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
         for (int i = 0; i < NQ; ++i) {
-          double cu = CV[i][0] * u[0] + CV[i][1] * u[1] + CV[i][2] * u[2];
-          double cF = CV[i][0] * F[0] + CV[i][1] * F[1] + CV[i][2] * F[2];
-          double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
-          double feq = wgt(i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * u2);
-          double Fi = (1.0 - 0.5 / tau) * wgt(i) * (3.0 * (cF - uF) + 9.0 * cu * cF);
-          double fstar = f[i * N + s] - (f[i * N + s] - feq) / tau + Fi;
+          R cu = CV[i][0] * u[0] + CV[i][1] * u[1] + CV[i][2] * u[2];
+          R cF = CV[i][0] * F[0] + CV[i][1] * F[1] + CV[i][2] * F[2];
+          R uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+          R feq = wgt(i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * u2);
+          R Fi = (1.0 - 0.5 / tau) * wgt(i) * (3.0 * (cF - uF) + 9.0 * cu * cF);
+          R fstar = f[i * N + s] - (f[i * N + s] - feq) / tau + Fi;
           long d = B.at(x + CV[i][0], y + CV[i][1], z + CV[i][2]);
           fnew[i * N + d] = fstar;
         }
@@ -408,84 +471,87 @@ void lb_all(const Box& B, const orc_params& P, const double* f, const double* F3
 
 // Stage 7 right-hand sides: -upwind advection + co-rotation + Gamma_Q H for Q;
 // -div(upwind flux) + M lap mu for psi.
-void op_rhs(const Box& B, const orc_params& P, const double* q5, const double* psi, const double* uadv,
-            const double* H5, const double* mu, double* rq5, double* rp) {
+template <typename R>
+void op_rhs(const Box& B, const PR<R>& P, const R* q5, const R* psi, const R* uadv,
+            const R* H5, const R* mu, R* rq5, R* rp) {
   long N = B.n();
   for (int z = 0; z < B.nz; ++z)
     for (int y = 0; y < B.ny; ++y)
       for (int x = 0; x < B.nx; ++x) {
         long s = B.at(x, y, z);
         int r[3] = {x, y, z};
-        M3 Q, H, Wg, S;
+        M3<R> Q, H, Wg, S;
         q_full(q5, N, s, Q);
         q_full(H5, N, s, H);
         vec_grad_at(B, uadv, x, y, z, Wg);
         corotation(Wg, Q, P.xi, S);
-        M3 adv;
-        std::memset(adv, 0, sizeof(adv));
-        double div = 0.0;
+        M3<R> adv;
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) adv[i][j] = 0.0;
+        R div = 0.0;
         for (int a = 0; a < 3; ++a) {
           int rp1[3] = {r[0], r[1], r[2]}, rm1[3] = {r[0], r[1], r[2]};
           rp1[a] += 1;
           rm1[a] -= 1;
           long sp = B.at(rp1[0], rp1[1], rp1[2]);
           long sm = B.at(rm1[0], rm1[1], rm1[2]);
-          double ua = uadv[a * N + s];
-          M3 Qp, Qm;
+          R ua = uadv[a * N + s];
+          M3<R> Qp, Qm;
           q_full(q5, N, sp, Qp);
           q_full(q5, N, sm, Qm);
           for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j)
-              adv[i][j] += std::fmax(ua, 0.0) * (Q[i][j] - Qm[i][j]) + std::fmin(ua, 0.0) * (Qp[i][j] - Q[i][j]);
+              adv[i][j] += max0(ua) * (Q[i][j] - Qm[i][j]) + min0(ua) * (Qp[i][j] - Q[i][j]);
           // upwind face fluxes of psi at x + e_a/2 and x - e_a/2
-          double ubp = 0.5 * (ua + uadv[a * N + sp]);
-          double Jp = ubp * (ubp > 0.0 ? psi[s] : psi[sp]);
-          double ubm = 0.5 * (uadv[a * N + sm] + ua);
-          double Jm = ubm * (ubm > 0.0 ? psi[sm] : psi[s]);
+          R ubp = 0.5 * (ua + uadv[a * N + sp]);
+          R Jp = ubp * (ubp > 0.0 ? psi[s] : psi[sp]);
+          R ubm = 0.5 * (uadv[a * N + sm] + ua);
+          R Jm = ubm * (ubm > 0.0 ? psi[sm] : psi[s]);
           div += Jp - Jm;
         }
-        double lapmu = 0.0;
+        R lapmu = 0.0;
         for (int i = 1; i < NQ; ++i) {
           long n = B.at(x + CV[i][0], y + CV[i][1], z + CV[i][2]);
           lapmu += 6.0 * wgt(i) * (mu[n] - mu[s]);
         }
-        M3 R;
+        M3<R> Rm;
         for (int i = 0; i < 3; ++i)
-          for (int j = 0; j < 3; ++j) R[i][j] = -adv[i][j] + S[i][j] + P.gammaQ * H[i][j];
+          for (int j = 0; j < 3; ++j) Rm[i][j] = -adv[i][j] + S[i][j] + P.gammaQ * H[i][j];
         // Q' = ST(Q + R) with ST the symmetric traceless projection; Q is already
         // symmetric traceless and ST is linear, so Q' = Q + ST(R).
-        M3 Rp;
-        sym_traceless(R, Rp);
+        M3<R> Rp;
+        sym_traceless(Rm, Rp);
         q_store(Rp, rq5, N, s);
         rp[s] = -div + P.M * lapmu;
       }
 }
 
-void step_one(const Box& B, const orc_params& P, double* f, double* q5, double* psi, double* uprev, Work& w) {
+template <typename R>
+void step_one(const Box& B, const PR<R>& P, R* f, R* q5, R* psi, R* uprev, Work<R>& w) {
   const long N = B.n();
   w.H.resize(5 * N); w.mu.resize(N); w.sig.resize(9 * N); w.F.resize(3 * N);
   w.unew.resize(3 * N); w.fnew.resize(19 * N); w.rhsQ.resize(5 * N); w.rhsP.resize(N);
-  fields_all(B, P, q5, psi, w.H.data(), w.mu.data(), w.sig.data(), nullptr, nullptr, nullptr, nullptr);
-  force_all(B, w.sig.data(), w.F.data());
-  lb_all(B, P, f, w.F.data(), w.fnew.data(), w.unew.data());
-  const double* uadv = (P.coupling == 1) ? w.unew.data() : uprev;
-  op_rhs(B, P, q5, psi, uadv, w.H.data(), w.mu.data(), w.rhsQ.data(), w.rhsP.data());
+  fields_all<R>(B, P, q5, psi, w.H.data(), w.mu.data(), w.sig.data(), nullptr, nullptr, nullptr, nullptr);
+  force_all<R>(B, w.sig.data(), w.F.data());
+  lb_all<R>(B, P, f, w.F.data(), w.fnew.data(), w.unew.data());
+  const R* uadv = (P.coupling == 1) ? w.unew.data() : uprev;
+  op_rhs<R>(B, P, q5, psi, uadv, w.H.data(), w.mu.data(), w.rhsQ.data(), w.rhsP.data());
   if (P.integrator == 1) {
     // Heun: predictor Q* = Q + R(Q), corrector Q' = Q + (R(Q) + R(Q*))/2, u held fixed.
     w.Qp.resize(5 * N); w.Pp.resize(N);
     for (long k = 0; k < 5 * N; ++k) w.Qp[k] = q5[k] + w.rhsQ[k];
     for (long k = 0; k < N; ++k) w.Pp[k] = psi[k] + w.rhsP[k];
-    std::vector<double> H2(5 * N), mu2(N), rq2(5 * N), rp2(N);
-    fields_all(B, P, w.Qp.data(), w.Pp.data(), H2.data(), mu2.data(), nullptr, nullptr, nullptr, nullptr, nullptr);
-    op_rhs(B, P, w.Qp.data(), w.Pp.data(), uadv, H2.data(), mu2.data(), rq2.data(), rp2.data());
+    std::vector<R> H2(5 * N), mu2(N), rq2(5 * N), rp2(N);
+    fields_all<R>(B, P, w.Qp.data(), w.Pp.data(), H2.data(), mu2.data(), nullptr, nullptr, nullptr, nullptr, nullptr);
+    op_rhs<R>(B, P, w.Qp.data(), w.Pp.data(), uadv, H2.data(), mu2.data(), rq2.data(), rp2.data());
     for (long k = 0; k < 5 * N; ++k) q5[k] += 0.5 * (w.rhsQ[k] + rq2[k]);
     for (long k = 0; k < N; ++k) psi[k] += 0.5 * (w.rhsP[k] + rp2[k]);
   } else {
     for (long k = 0; k < 5 * N; ++k) q5[k] += w.rhsQ[k];
     for (long k = 0; k < N; ++k) psi[k] += w.rhsP[k];
   }
-  std::memcpy(f, w.fnew.data(), sizeof(double) * 19 * N);
-  std::memcpy(uprev, w.unew.data(), sizeof(double) * 3 * N);
+  std::memcpy(f, w.fnew.data(), sizeof(R) * 19 * N);
+  std::memcpy(uprev, w.unew.data(), sizeof(R) * 3 * N);
 }
 
 // SplitMix64 (Steele, Lea & Flood 2014): the stream seeded with `seed` returns, at
@@ -532,7 +598,7 @@ void orc_init(int nx, int ny, int nz, const orc_params* P, uint64_t seed, int in
         double dx = x - P->cx, dy = y - P->cy, dz = z - P->cz;
         double r = std::sqrt(dx * dx + dy * dy + dz * dz);
         psi[s] = std::tanh((P->R - r) / 2.0);
-        M3 Q;
+        M3<double> Q;
         std::memset(Q, 0, sizeof(Q));
         if (r < P->R) {
           double n[3] = {std::cos(P->q0 * dz), std::sin(P->q0 * dz), 0.0};
@@ -552,7 +618,7 @@ void orc_init(int nx, int ny, int nz, const orc_params* P, uint64_t seed, int in
 void orc_fields(int nx, int ny, int nz, const orc_params* P, const double* q5, const double* psi, double* H5,
                 double* mu, double* sig9, double* sE9, double* sR9, double* sA9, double* fden) {
   Box B{nx, ny, nz};
-  fields_all(B, *P, q5, psi, H5, mu, sig9, sE9, sR9, sA9, fden);
+  fields_all<double>(B, promote<double>(*P), q5, psi, H5, mu, sig9, sE9, sR9, sA9, fden);
 }
 
 void orc_force(int nx, int ny, int nz, const double* sig9, double* F3) {
@@ -569,7 +635,7 @@ void orc_stencils(int nx, int ny, int nz, const double* s, double* grad3, double
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
         long k = B.at(x, y, z);
-        Derivs d;
+        Derivs<double> d;
         derivs_at(B, zero.data(), s, x, y, z, d);
         for (int a = 0; a < 3; ++a) grad3[a * N + k] = d.dpsi[a];
         lap[k] = d.lappsi;
@@ -580,7 +646,7 @@ void orc_stencils(int nx, int ny, int nz, const double* s, double* grad3, double
 
 // Per-site co-rotation S(W, Q) (full 3x3 in and out; Wg[a][b] = d_b u_a).
 void orc_corotation(const double* Wg9, const double* Q9, double xi, double* S9) {
-  M3 W, Q, S;
+  M3<double> W, Q, S;
   for (int i = 0; i < 9; ++i) { W[i / 3][i % 3] = Wg9[i]; Q[i / 3][i % 3] = Q9[i]; }
   corotation(W, Q, xi, S);
   for (int i = 0; i < 9; ++i) S9[i] = S[i / 3][i % 3];
@@ -591,14 +657,14 @@ void orc_corotation(const double* Wg9, const double* Q9, double xi, double* S9) 
 void orc_op_rhs(int nx, int ny, int nz, const orc_params* P, const double* q5, const double* psi,
                 const double* uadv, const double* H5, const double* mu, double* rq5, double* rp, double* W9) {
   Box B{nx, ny, nz};
-  op_rhs(B, *P, q5, psi, uadv, H5, mu, rq5, rp);
+  op_rhs<double>(B, promote<double>(*P), q5, psi, uadv, H5, mu, rq5, rp);
   if (W9) {
     long N = B.n();
     for (int z = 0; z < nz; ++z)
       for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
           long s = B.at(x, y, z);
-          M3 Wg;
+          M3<double> Wg;
           vec_grad_at(B, uadv, x, y, z, Wg);
           for (int k = 0; k < 9; ++k) W9[k * N + s] = Wg[k / 3][k % 3];
         }
@@ -610,15 +676,15 @@ void orc_op_rhs(int nx, int ny, int nz, const orc_params* P, const double* q5, c
 void orc_step(int nx, int ny, int nz, const orc_params* P, double* f, double* q5, double* psi, double* uprev,
               long nsteps) {
   Box B{nx, ny, nz};
-  Work w;
-  for (long t = 0; t < nsteps; ++t) step_one(B, *P, f, q5, psi, uprev, w);
+  Work<double> w;
+  for (long t = 0; t < nsteps; ++t) step_one<double>(B, promote<double>(*P), f, q5, psi, uprev, w);
 }
 
 // Stage 6 alone (for LB pins): collide with a given force and stream.
 void orc_lb(int nx, int ny, int nz, const orc_params* P, const double* f, const double* F3, double* fnew,
             double* unew) {
   Box B{nx, ny, nz};
-  lb_all(B, *P, f, F3, fnew, unew);
+  lb_all<double>(B, promote<double>(*P), f, F3, fnew, unew);
 }
 
 // Conserved sums and centroid moments (FP64):
@@ -648,6 +714,30 @@ void orc_observables(int nx, int ny, int nz, const double* f, const double* psi,
         }
         out[11] += pc;
       }
+}
+
+// Forward-mode tangent of nsteps steps.  (f, q5, psi, u) and their tangents (df, dq5,
+// dpsi, du) advance together; the parameters zeta and q0 carry the tangents dzeta and dq0,
+// all other parameters are fixed.  Used as an independent derivative for the adjoint.
+void orc_step_tangent(int nx, int ny, int nz, const orc_params* P, double dzeta, double dq0, double* f,
+                      double* df, double* q5, double* dq5, double* psi, double* dpsi, double* u, double* du,
+                      long nsteps) {
+  Box B{nx, ny, nz};
+  const long N = B.n();
+  std::vector<Dual> F(19 * N), Q(5 * N), S(N), U(3 * N);
+  for (long k = 0; k < 19 * N; ++k) F[k] = Dual(f[k], df[k]);
+  for (long k = 0; k < 5 * N; ++k) Q[k] = Dual(q5[k], dq5[k]);
+  for (long k = 0; k < N; ++k) S[k] = Dual(psi[k], dpsi[k]);
+  for (long k = 0; k < 3 * N; ++k) U[k] = Dual(u[k], du[k]);
+  PR<Dual> pr = promote<Dual>(*P);
+  pr.zeta.d = dzeta;
+  pr.q0.d = dq0;
+  Work<Dual> w;
+  for (long t = 0; t < nsteps; ++t) step_one<Dual>(B, pr, F.data(), Q.data(), S.data(), U.data(), w);
+  for (long k = 0; k < 19 * N; ++k) { f[k] = F[k].v; df[k] = F[k].d; }
+  for (long k = 0; k < 5 * N; ++k) { q5[k] = Q[k].v; dq5[k] = Q[k].d; }
+  for (long k = 0; k < N; ++k) { psi[k] = S[k].v; dpsi[k] = S[k].d; }
+  for (long k = 0; k < 3 * N; ++k) { u[k] = U[k].v; du[k] = U[k].d; }
 }
 
 }  // extern "C"

@@ -81,6 +81,7 @@ def lib():
         L.orc_step.argtypes = [i, i, i, P, dp, dp, dp, dp, ctypes.c_long]
         L.orc_lb.argtypes = [i, i, i, P, dp, dp, dp, dp]
         L.orc_observables.argtypes = [i, i, i, dp, dp, dp]
+        L.orc_step_tangent.argtypes = [i, i, i, P, ctypes.c_double, ctypes.c_double] + [dp] * 8 + [ctypes.c_long]
         _lib = L
     return _lib
 
@@ -125,6 +126,18 @@ class State:
 
     def observables(self):
         return observables(self.f, self.psi)
+
+    def step_tangent(self, n, tangent, dzeta=0.0, dq0=0.0):
+        """Advance n steps carrying the forward-mode tangent `tangent` = dict(f, q, psi, u)
+        (arrays like the state; missing entries are zero) and parameter tangents; returns
+        the tangent of the final state."""
+        nx, ny, nz = self.shape
+        t = {k: np.ascontiguousarray(tangent.get(k, np.zeros_like(getattr(self, k))), dtype=np.float64).copy()
+             for k in ("f", "q", "psi", "u")}
+        lib().orc_step_tangent(nx, ny, nz, ctypes.byref(self.p), float(dzeta), float(dq0), _p(self.f), _p(t["f"]),
+                               _p(self.q), _p(t["q"]), _p(self.psi), _p(t["psi"]), _p(self.u), _p(t["u"]), n)
+        self.t += n
+        return t
 
     def copy(self):
         s = State.__new__(State)

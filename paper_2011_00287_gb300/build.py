@@ -13,7 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblbcad.so")
-UNITS = ["lbcad_runtime.cu", "lbcad_f32.cu", "lbcad_f64.cu", "lbcad_noalloc.cu"]
+UNITS = ["lbcad_runtime.cu", "lbcad_f32.cu", "lbcad_f64.cu", "lbcad_noalloc.cu", "lbcad_adj_f32.cu",
+         "lbcad_adj_f64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

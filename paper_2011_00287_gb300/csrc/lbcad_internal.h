@@ -56,6 +56,7 @@ struct InstDesc {
 template <typename T, bool SHIFT>
 struct Launch {
   static cudaError_t step(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, cudaStream_t s);
+  static cudaError_t fields(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, cudaStream_t s);
   static cudaError_t get_fields(const InstDesc<T>& I, uint32_t mask, double* dst, cudaStream_t s);
   static cudaError_t set_fields(const InstDesc<T>& I, uint32_t mask, const double* src, T* g_target,
                                 T* q_target, T* psi_target, T* u_target, cudaStream_t s);
@@ -83,6 +84,28 @@ struct LaunchFused {
   static cudaError_t step(int cfg_index, const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles,
                           long long total, int grid, cudaStream_t s);
 };
+
+// Buffers of one reverse step of the adjoint (lbcad_adjoint.cuh).
+template <typename T>
+struct AdjDescHost {
+  InstDesc<T> I;                 // state s_t (inputs) and its sigma/mu/H scratch
+  const T *lg, *lq, *lp, *lu;    // cotangent of s_{t+1}
+  T *A, *Bf, *ls;                // work: 88 + 36 + 15 values per site
+  T *og, *oq, *op, *ou;          // cotangent of s_t
+  double* pgrad;                 // per-block partial d/dzeta, d/dq0
+};
+
+template <typename T, bool SHIFT>
+struct LaunchAdj {
+  static cudaError_t reverse_step(const AdjDescHost<T>& h, cudaStream_t s);
+  static cudaError_t seed(const InstDesc<T>& I, const double dX[3], const double ks[3], const double kc[3], T* lp,
+                          cudaStream_t s);
+  static int blocks(long long N);
+  static cudaError_t export_fields(const InstDesc<T>& I, const T* lam, uint32_t mask, double* dst, cudaStream_t s);
+};
+
+// Adds the per-block partial sums of 2 values to total[0..1] (fixed order).
+cudaError_t adj_accumulate(const double* pgrad, int nblocks, double* total, cudaStream_t s);
 
 // Sets the message that lbcad_last_error(NULL) returns on this thread.
 void set_thread_error(const char* msg);

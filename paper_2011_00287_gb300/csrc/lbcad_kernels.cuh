@@ -654,6 +654,13 @@ cudaError_t Launch<T, SHIFT>::step(const InstDesc<T>* d_desc, int ninst, long lo
   return cudaGetLastError();
 }
 
+template <typename T, bool SHIFT>
+cudaError_t Launch<T, SHIFT>::fields(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs,
+                                     cudaStream_t s) {
+  k_fields<T><<<(unsigned)total_blocks, bs, 0, s>>>(d_desc, ninst);
+  return cudaGetLastError();
+}
+
 inline unsigned grid_for(long long N, int bs) {
   long long g = (N + bs - 1) / bs;
   if (g > 152 * 16) g = 152 * 16;

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -77,6 +78,7 @@ struct lbcad_ctx {
   int fused_grid = 0;
   int cfg_index = 0;
   FusedCfg cfg;
+  void* adj_lam = nullptr;  // cotangent of the initial state of the last lbcad_adjoint
   std::string err;
   size_t elem() const { return prec == LBCAD_FP64 ? sizeof(double) : sizeof(float); }
 };
@@ -650,6 +652,191 @@ int lbcad_observables(lbcad_ctx* c, int32_t inst, lbcad_obs* out) {
   out->sum_phic = h[11];
   for (double v : h)
     if (!std::isfinite(v)) return fail(c, LBCAD_E_NAN, "non-finite value in observables");
+  return LBCAD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Copies of one stored state: g (19), Q (5), psi (1), u (3) components of n sites.
+template <typename T>
+struct StateBuf {
+  T* g;
+  T* q;
+  T* p;
+  T* u;
+};
+
+template <typename T>
+StateBuf<T> state_at(T* base, long long N) {
+  return StateBuf<T>{base, base + 19 * N, base + 24 * N, base + 25 * N};
+}
+
+template <typename T>
+InstDesc<T> desc_for(const Inst& I, const StateBuf<T>& in, const StateBuf<T>& out, T* sig, T* mu, T* H) {
+  InstDesc<T> d = make_desc<T>(I, 0);
+  d.blk0 = 0;
+  d.g_in = in.g; d.q_in = in.q; d.psi_in = in.p; d.u_in = in.u;
+  d.g_out = out.g; d.q_out = out.q; d.psi_out = out.p; d.u_out = out.u;
+  d.sig = sig; d.mu = mu; d.H = H;
+  return d;
+}
+
+// Periodic centroid (per-axis circular mean of phi_c) from the FP64 moments.
+void centroid_of(const lbcad_obs& o, const lbcad_grid& g, double X[3]) {
+  const double L[3] = {(double)g.nx, (double)g.ny, (double)g.nz};
+  for (int a = 0; a < 3; ++a) {
+    double ang = std::atan2(o.cm_sin[a], o.cm_cos[a]);
+    if (ang < 0) ang += 2.0 * 3.14159265358979323846;
+    X[a] = ang * L[a] / (2.0 * 3.14159265358979323846);
+  }
+}
+
+template <typename T, bool SHIFT>
+int adjoint_impl(lbcad_ctx* c, int64_t nsteps, int k, double* dzeta, double* dq0, double* dQ0, double* J_out) {
+  Inst& I = c->inst[0];
+  const long long N = I.N;
+  const int S = (int)((nsteps + k - 1) / k);
+  const size_t st = 28 * (size_t)N;  // elements of one stored state
+  // buffers (allocated per call through the context's allocator; released at destroy)
+  T* ck = (T*)dev_alloc(c, (size_t)S * st * sizeof(T));
+  T* seg = (T*)dev_alloc(c, (size_t)k * st * sizeof(T));
+  T* lam = (T*)dev_alloc(c, 2 * st * sizeof(T));
+  T* work = (T*)dev_alloc(c, (88 + 36 + 15 + 15) * (size_t)N * sizeof(T));
+  const int nb = LaunchAdj<T, SHIFT>::blocks(N);
+  double* pg = (double*)dev_alloc(c, (2 * (size_t)nb + 2) * sizeof(double));
+  InstDesc<T>* dd = (InstDesc<T>*)dev_alloc(c, (size_t)k * sizeof(InstDesc<T>));
+  if (!ck || !seg || !lam || !work || !pg || !dd) return fail(c, LBCAD_E_OOM, "adjoint buffers");
+  T* A = work;
+  T* Bf = A + 88 * N;
+  T* ls = Bf + 36 * N;
+  T* sig = ls + 15 * N;
+  T* mu = sig + 9 * N;
+  T* H = mu + N;
+  double* total = pg + 2 * nb;
+  CK(c, cudaMemsetAsync(total, 0, 2 * sizeof(double), c->stream));
+
+  lbcad_obs o0, o1;
+  int r = lbcad_observables(c, 0, &o0);
+  if (r) return r;
+  // forward with a checkpoint at the start of every segment
+  for (int sgi = 0; sgi < S; ++sgi) {
+    const int par = (int)(c->step & 1);
+    const StateBuf<T> cb = state_at<T>(ck + (size_t)sgi * st, N);
+    CK(c, cudaMemcpyAsync(cb.g, I.gb[par], 19 * N * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(cb.q, I.qb[par], 5 * N * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(cb.p, I.pb[par], N * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(cb.u, I.ub[par], 3 * N * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+    const int64_t len = std::min<int64_t>(k, nsteps - (int64_t)sgi * k);
+    r = lbcad_step(c, len);
+    if (r) return r;
+  }
+  r = lbcad_observables(c, 0, &o1);
+  if (r) return r;
+  double X0[3], X1[3], dX[3], ks[3], kc[3];
+  centroid_of(o0, I.g, X0);
+  centroid_of(o1, I.g, X1);
+  const double L[3] = {(double)I.g.nx, (double)I.g.ny, (double)I.g.nz};
+  double J = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    double d = X1[a] - X0[a];
+    d -= L[a] * std::round(d / L[a]);  // minimum image
+    dX[a] = d;
+    J += 0.5 * d * d;
+    const double r2 = o1.cm_cos[a] * o1.cm_cos[a] + o1.cm_sin[a] * o1.cm_sin[a];
+    const double coef = (L[a] / (2.0 * 3.14159265358979323846)) / r2;
+    ks[a] = coef * o1.cm_cos[a];
+    kc[a] = coef * o1.cm_sin[a];
+  }
+  // seed: only psi at the final time enters J
+  StateBuf<T> lcur = state_at<T>(lam, N), lnxt = state_at<T>(lam + st, N);
+  CK(c, cudaMemsetAsync(lam, 0, st * sizeof(T), c->stream));
+  cudaError_t e = LaunchAdj<T, SHIFT>::seed(desc_now<T>(c, 0), dX, ks, kc, lcur.p, c->stream);
+  if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("adjoint seed: ") + cudaGetErrorString(e));
+
+  std::vector<InstDesc<T>> hd(k);
+  for (int sgi = S - 1; sgi >= 0; --sgi) {
+    const int len = (int)std::min<int64_t>(k, nsteps - (int64_t)sgi * k);
+    // replay the segment: states 0 .. len-1 of this segment into seg (state 0 = checkpoint)
+    CK(c, cudaMemcpyAsync(seg, ck + (size_t)sgi * st, st * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+    for (int j = 0; j < len; ++j) {
+      const StateBuf<T> in = state_at<T>(seg + (size_t)j * st, N);
+      const StateBuf<T> out = state_at<T>(seg + (size_t)(j + 1 < len ? j + 1 : j) * st, N);
+      hd[j] = desc_for<T>(I, in, out, sig, mu, H);
+    }
+    CK(c, cudaMemcpyAsync(dd, hd.data(), len * sizeof(InstDesc<T>), cudaMemcpyHostToDevice, c->stream));
+    const long long blocks = (N + kStepBlock - 1) / kStepBlock;
+    for (int j = 0; j + 1 < len; ++j) {
+      e = Launch<T, SHIFT>::step(dd + j, 1, blocks, kStepBlock, c->stream);
+      if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("adjoint replay: ") + cudaGetErrorString(e));
+    }
+    // reverse steps
+    for (int j = len - 1; j >= 0; --j) {
+      e = Launch<T, SHIFT>::fields(dd + j, 1, blocks, kStepBlock, c->stream);
+      if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("adjoint fields: ") + cudaGetErrorString(e));
+      AdjDescHost<T> h;
+      h.I = hd[j];
+      h.lg = lcur.g; h.lq = lcur.q; h.lp = lcur.p; h.lu = lcur.u;
+      h.A = A; h.Bf = Bf; h.ls = ls;
+      h.og = lnxt.g; h.oq = lnxt.q; h.op = lnxt.p; h.ou = lnxt.u;
+      h.pgrad = pg;
+      e = LaunchAdj<T, SHIFT>::reverse_step(h, c->stream);
+      if (e == cudaSuccess) e = adj_accumulate(pg, nb, total, c->stream);
+      if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("adjoint reverse step: ") + cudaGetErrorString(e));
+      std::swap(lcur, lnxt);
+    }
+  }
+  // lcur holds the cotangent of the checkpointed initial state
+  c->adj_lam = lcur.g;
+  double tot[2];
+  CK(c, cudaMemcpyAsync(tot, total, sizeof(tot), cudaMemcpyDeviceToHost, c->stream));
+  std::vector<T> hq(5 * (size_t)N);
+  CK(c, cudaMemcpyAsync(hq.data(), lcur.q, hq.size() * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (dzeta) *dzeta = tot[0];
+  if (dq0) *dq0 = tot[1];
+  if (J_out) *J_out = J;
+  if (dQ0)
+    for (size_t i = 0; i < hq.size(); ++i) dQ0[i] = (double)hq[i];
+  for (double v : tot)
+    if (!std::isfinite(v)) return fail(c, LBCAD_E_NAN, "non-finite adjoint gradient");
+  return LBCAD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbcad_adjoint(lbcad_ctx* c, int64_t nsteps, int32_t ckpt_every, double* dJ_dzeta, double* dJ_dq0,
+                  double* dJ_dQ0, double* J) {
+  if (!c) return LBCAD_E_INVALID_ARG;
+  if (c->inst.size() != 1) return fail(c, LBCAD_E_UNSUPPORTED, "the adjoint runs on single-instance contexts");
+  if (nsteps < 1 || ckpt_every < 1) return fail(c, LBCAD_E_INVALID_ARG, "need nsteps >= 1 and ckpt_every >= 1");
+  DeviceGuard dg(c->device);
+  const int k = (int)std::min<int64_t>(ckpt_every, nsteps);
+  return c->prec == LBCAD_FP64 ? adjoint_impl<double, false>(c, nsteps, k, dJ_dzeta, dJ_dq0, dJ_dQ0, J)
+                               : adjoint_impl<float, true>(c, nsteps, k, dJ_dzeta, dJ_dq0, dJ_dQ0, J);
+}
+
+int lbcad_adjoint_fields(lbcad_ctx* c, uint32_t mask, void* dst, size_t bytes) {
+  if (!c) return LBCAD_E_INVALID_ARG;
+  if (!c->adj_lam) return fail(c, LBCAD_E_INVALID_ARG, "no lbcad_adjoint has run on this context");
+  if (!dst || mask == 0 || (mask & ~29u)) return fail(c, LBCAD_E_INVALID_ARG, "bad dst or mask (G, U, Q, PSI)");
+  const long long N = c->inst[0].N;
+  const size_t need = (size_t)ncomp_of(mask) * N * sizeof(double);
+  if (bytes < need) return fail(c, LBCAD_E_INVALID_ARG, "dst too small");
+  DeviceGuard dg(c->device);
+  int r = ensure_staging(c, need);
+  if (r) return r;
+  cudaError_t e = (c->prec == LBCAD_FP64)
+                      ? LaunchAdj<double, false>::export_fields(desc_now<double>(c, 0), (const double*)c->adj_lam, mask,
+                                                                c->staging, c->stream)
+                      : LaunchAdj<float, true>::export_fields(desc_now<float>(c, 0), (const float*)c->adj_lam, mask,
+                                                              c->staging, c->stream);
+  if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("adjoint export: ") + cudaGetErrorString(e));
+  CK(c, cudaMemcpyAsync(dst, c->staging, need, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
   return LBCAD_OK;
 }
 

@@ -82,6 +82,9 @@ _SIGS = {
     "lbcad_set_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p,
                                         ctypes.c_size_t, ctypes.c_int32]),
     "lbcad_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _P(lbcad_obs)]),
+    "lbcad_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, _P(ctypes.c_double),
+                                     _P(ctypes.c_double), ctypes.c_void_p, _P(ctypes.c_double)]),
+    "lbcad_adjoint_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_size_t]),
     "lbcad_num_instances": (ctypes.c_int, [ctypes.c_void_p]),
     "lbcad_instance_grid": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _P(lbcad_grid)]),
     "lbcad_step_count": (ctypes.c_int64, [ctypes.c_void_p]),
@@ -352,6 +355,33 @@ class Simulation:
             raise ValueError("field sizes do not match the grid")
         _check(library().lbcad_set_fields(self.ctx, inst, mask, ctypes.c_void_p(buf.ctypes.data), buf.nbytes, 0),
                self.ctx)
+
+    def adjoint(self, nsteps: int, ckpt_every: int = 50, want_dQ0: bool = True):
+        """Run nsteps forward (the state advances) and return (J, dJ/dzeta, dJ/dq0,
+        dJ/dQ0 as (5, nz, ny, nx) or None) for J = |centroid displacement|^2 / 2."""
+        nx, ny, nz = self._inst(0)
+        dz, dq, J = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        dQ0 = np.empty((5, nz, ny, nx)) if want_dQ0 else None
+        ptr = ctypes.c_void_p(dQ0.ctypes.data) if want_dQ0 else None
+        _check(library().lbcad_adjoint(self.ctx, int(nsteps), int(ckpt_every), ctypes.byref(dz), ctypes.byref(dq),
+                                       ptr, ctypes.byref(J)), self.ctx)
+        return J.value, dz.value, dq.value, dQ0
+
+    def adjoint_fields(self, mask: int = FIELD_G | FIELD_U | FIELD_Q | FIELD_PSI) -> Dict[str, np.ndarray]:
+        """dJ/d(initial state) of the last adjoint run, in the get_fields layout."""
+        nx, ny, nz = self._inst(0)
+        N = nx * ny * nz
+        ncomp = sum(c for b, c in FIELD_NCOMP.items() if mask & b)
+        buf = np.empty(ncomp * N)
+        _check(library().lbcad_adjoint_fields(self.ctx, mask, ctypes.c_void_p(buf.ctypes.data), buf.nbytes), self.ctx)
+        res, o = {}, 0
+        for b in (FIELD_G, FIELD_U, FIELD_Q, FIELD_PSI):
+            if mask & b:
+                c = FIELD_NCOMP[b]
+                v = buf[o * N:(o + c) * N].reshape(c, nz, ny, nx)
+                res[FIELD_NAMES[b]] = v[0] if b == FIELD_PSI else v
+                o += c
+        return res
 
     def observables(self, inst: int = 0) -> np.ndarray:
         o = lbcad_obs()

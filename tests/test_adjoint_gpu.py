@@ -1,0 +1,198 @@
+"""Adjoint of the hybrid step: J = |centroid displacement|^2 / 2 over n steps.
+
+References, both independent of the CUDA path:
+- The oracle's forward-mode derivative. The FP64 CPU step runs on dual numbers of its own,
+  seeded in zeta, in q0, along a direction of the initial Q, or along a direction of the
+  whole initial state. This differentiates exactly the same arithmetic, so the GPU adjoint
+  must agree to rounding (1e-5 relative).
+- Central finite differences of the GPU FP64 forward (h = 1e-4 relative, 1e-4 relative
+  agreement).
+
+J is only piecewise smooth. The first-order upwind terms of the scheme (Sec. 3) put kinks
+where a face velocity changes sign, and over tens of steps those kinks lie closer together
+than any usable finite-difference step. So the finite-difference comparison runs at a short
+horizon and first checks that J is smooth there: differences with h and 10 h must agree.
+"""
+import numpy as np
+import pytest
+
+import paper_2011_00287_gb300 as L
+from paper_2011_00287_gb300 import observables as OB
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+SHAPE = (16, 16, 16)
+KW = dict(R=5.0, p0=8.0, zeta=0.02, W=0.05)
+NSTEPS = 24
+CKPT = 7  # several segments and a partial one
+SEED = 3
+
+
+def _perm():
+    cl, _ = L.lattice()
+    co, _ = O.lattice()
+    return np.array([int(np.where((co == v).all(1))[0][0]) for v in cl])
+
+
+def _dX(x0, x1):
+    d = x1 - x0
+    return d - np.array(SHAPE) * np.round(d / np.array(SHAPE))
+
+
+def _centroid_tangent(psi, dpsi):
+    """Tangent of the periodic centroid for a tangent dpsi of psi."""
+    nz, ny, nx = psi.shape
+    out = np.zeros(3)
+    for a, n, axis in ((0, nx, 2), (1, ny, 1), (2, nz, 0)):
+        th = 2 * np.pi * np.arange(n) / n
+        shp = [1, 1, 1]
+        shp[axis] = n
+        sn, cs = np.sin(th).reshape(shp), np.cos(th).reshape(shp)
+        pc = 0.5 * (1 + psi)
+        S, C = np.sum(pc * sn), np.sum(pc * cs)
+        dS, dC = np.sum(0.5 * dpsi * sn), np.sum(0.5 * dpsi * cs)
+        out[a] = n / (2 * np.pi) * (C * dS - S * dC) / (C * C + S * S)
+    return out
+
+
+def _oracle_dJ(nsteps=NSTEPS, kw=KW, dzeta=0.0, dq0=0.0, tangent=None, state=None):
+    """(J, dJ) from the oracle's forward-mode tangent."""
+    s = O.State(SHAPE, O.default_params(SHAPE, **kw), seed=SEED)
+    if state is not None:
+        s.f, s.q, s.psi, s.u = (np.ascontiguousarray(state[k]).copy() for k in ("f", "q", "psi", "u"))
+    x0 = OB.centroid(s.observables(), SHAPE)
+    t = s.step_tangent(nsteps, tangent or {}, dzeta=dzeta, dq0=dq0)
+    x1 = OB.centroid(s.observables(), SHAPE)
+    d = _dX(x0, x1)
+    return 0.5 * float(d @ d), float(d @ _centroid_tangent(s.psi, t["psi"]))
+
+
+def _J_gpu(nsteps=NSTEPS, prec=L.FP64, q5=None, **over):
+    kw = dict(KW, **over)
+    sim = L.Simulation([SHAPE], [L.default_params(SHAPE, precision=prec, **kw)], seed=SEED)
+    if q5 is not None:
+        sim.set_fields(0, {"q": q5})
+    x0 = OB.centroid(sim.observables(0), SHAPE)
+    sim.step(nsteps)
+    d = _dX(x0, OB.centroid(sim.observables(0), SHAPE))
+    sim.close()
+    return 0.5 * float(d @ d)
+
+
+def _adjoint(prec=L.FP64, nsteps=NSTEPS, ckpt=CKPT, kw=KW):
+    sim = L.Simulation([SHAPE], [L.default_params(SHAPE, precision=prec, **kw)], seed=SEED)
+    q0 = sim.get_fields(0, L.FIELD_Q)["q"].copy()
+    J, dz, dq, dQ0 = sim.adjoint(nsteps, ckpt)
+    assert sim.step_count == nsteps
+    sim.close()
+    return J, dz, dq, dQ0, q0
+
+
+@pytest.fixture(scope="module")
+def adj64():
+    return _adjoint(L.FP64)
+
+
+def test_objective_matches_forward_and_oracle(adj64):
+    J = adj64[0]
+    assert J > 0 and abs(J - _J_gpu()) <= 1e-12 * J
+    Jo, _ = _oracle_dJ()
+    assert abs(J - Jo) <= 1e-9 * J
+
+
+def test_dJ_dzeta_matches_oracle_forward_mode(adj64):
+    _, dz, _, _, _ = adj64
+    _, ref = _oracle_dJ(dzeta=1.0)
+    assert abs(dz - ref) <= 1e-5 * abs(ref), (dz, ref)
+
+
+def test_dJ_dq0_matches_oracle_forward_mode(adj64):
+    """q0 enters through H and sigma; the initial helix is held fixed."""
+    _, _, dq, _, _ = adj64
+    _, ref = _oracle_dJ(dq0=1.0)
+    assert abs(dq - ref) <= 1e-5 * abs(ref), (dq, ref)
+
+
+def test_dJ_dQ0_matches_oracle_forward_mode(adj64):
+    _, _, _, dQ0, q0 = adj64
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        v = rng.standard_normal(q0.shape)
+        _, ref = _oracle_dJ(tangent={"q": v})
+        ad = float(np.sum(dQ0 * v))
+        assert abs(ad - ref) <= 1e-5 * abs(ref), (ad, ref)
+
+
+def test_gradient_of_the_whole_initial_state_matches_oracle():
+    """lbcad_adjoint_fields from a developed state: dJ/d(f, u, Q, psi) along random
+    directions against the oracle's tangent (the reference centroid X(t0) held fixed)."""
+    sim = L.Simulation([SHAPE], [L.default_params(SHAPE, precision=L.FP64, **KW)], seed=SEED)
+    sim.step(3)
+    st = sim.get_fields(0)
+    sim.adjoint(NSTEPS, CKPT)
+    lam = sim.adjoint_fields()
+    sim.close()
+    perm = _perm()
+    inv = np.argsort(perm)
+    ostate = dict(f=st["g"][inv], q=st["q"], psi=st["psi"], u=st["u"])
+    rng = np.random.default_rng(5)
+    for name, okey in (("g", "f"), ("u", "u"), ("q", "q"), ("psi", "psi")):
+        v = rng.standard_normal(st[name].shape)
+        tv = v[inv] if name == "g" else v
+        s = O.State(SHAPE, O.default_params(SHAPE, **KW), seed=SEED)
+        s.f, s.q, s.psi, s.u = (np.ascontiguousarray(ostate[k]).copy() for k in ("f", "q", "psi", "u"))
+        x0 = OB.centroid(s.observables(), SHAPE)
+        t = s.step_tangent(NSTEPS, {okey: tv})
+        d = _dX(x0, OB.centroid(s.observables(), SHAPE))
+        ref = float(d @ _centroid_tangent(s.psi, t["psi"]))
+        ad = float(np.sum(lam[name] * v))
+        assert abs(ad - ref) <= 1e-5 * abs(ref), (name, ad, ref)
+
+
+def _fd_smooth(fun, x, rel=1e-4):
+    """Central difference at h; asserts the one at 10 h agrees (J smooth here)."""
+    def fd(r):
+        h = r * abs(x)
+        return (fun(x + h) - fun(x - h)) / (2 * h)
+    a, b = fd(rel), fd(10 * rel)
+    assert abs(a - b) <= 1e-4 * abs(a), ("J is not smooth at this point", a, b)
+    return a
+
+
+def test_short_horizon_finite_differences():
+    """At two steps J is smooth in zeta and along a direction of the initial Q: central
+    differences of the GPU forward agree with the adjoint within 1e-4."""
+    n = 2
+    _, dz, _, dQ0, q5 = _adjoint(L.FP64, nsteps=n, ckpt=1)
+    fd = _fd_smooth(lambda v: _J_gpu(nsteps=n, zeta=v), KW["zeta"])
+    assert abs(dz - fd) <= 1e-4 * abs(fd), (dz, fd)
+    v = np.random.default_rng(2).standard_normal(q5.shape) * (np.abs(q5).sum(0) > 0)
+    v *= 1e-2 / np.abs(v).max()  # small direction: curvature of J stays below the check
+    fdv = _fd_smooth(lambda e: _J_gpu(nsteps=n, q5=q5 + (e - 1.0) * v), 1.0, rel=1e-4)
+    ad = float(np.sum(dQ0 * v))
+    assert abs(ad - fdv) <= 1e-4 * abs(fdv), (ad, fdv)
+
+
+def test_fp32_adjoint_close_to_fp64(adj64):
+    _, dz64, dq64, dQ64, _ = adj64
+    _, dz32, dq32, dQ32, _ = _adjoint(L.FP32)
+    assert abs(dz32 - dz64) <= 2e-2 * abs(dz64)
+    assert abs(dq32 - dq64) <= 2e-2 * abs(dq64)
+    assert np.linalg.norm(dQ32 - dQ64) <= 5e-2 * np.linalg.norm(dQ64)
+
+
+def test_torch_autograd_function(adj64):
+    import torch
+    from paper_2011_00287_gb300.autograd import centroid_drift
+    J0, dz, dq, dQ0, q0 = adj64
+    zeta = torch.tensor(KW["zeta"], dtype=torch.float64, requires_grad=True)
+    q0v = torch.tensor(2 * np.pi / KW["p0"], dtype=torch.float64, requires_grad=True)
+    Q0 = torch.tensor(q0, dtype=torch.float64, requires_grad=True)
+    prm = L.default_params(SHAPE, precision=L.FP64, **KW)
+    J = centroid_drift(zeta, q0v, Q0, SHAPE, prm, NSTEPS, CKPT, seed=SEED)
+    (2.0 * J).backward()
+    assert abs(J.item() - J0) <= 1e-12 * J0
+    assert abs(zeta.grad.item() - 2 * dz) <= 1e-12 * abs(dz)
+    assert abs(q0v.grad.item() - 2 * dq) <= 1e-12 * abs(dq)
+    assert np.allclose(Q0.grad.numpy(), 2 * dQ0, rtol=1e-12, atol=0)
