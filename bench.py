@@ -29,7 +29,9 @@ if ROOT not in sys.path:
 
 METRIC = "hybrid-step MLUPS & % of HBM roofline, FP32 vs plain FP64 at stated error"
 BYTES_PER_SITE = {"fp32": 200, "fp64": 400}
-TILE_NAMES = ["32x8", "32x16", "64x8", "32x8-pipelined-8+8", "32x8-pipelined-6+10"]  # state read once + written once: (19 + 5 + 1) x 2 words
+# fused-step schedules offered to the autotuner, in candidate order
+TILE_NAMES = ["32x8", "32x16", "64x8", "32x8-pipelined-8+8", "32x8-pipelined-6+10", "32x6-pipelined-9+7",
+              "32x6-pipelined-10+6"]
 
 
 def workload_params(L, n, prec):

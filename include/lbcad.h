@@ -154,7 +154,8 @@ int lbcad_set_path(lbcad_ctx* c, int32_t path);
  * milliseconds per launch of up to ncfg candidates (-1 for a shape that does not fit).
  * Candidates: 0 = 32x8 tiles (default), 1 = 32x16, 2 = 64x8, 3 and 4 = 32x8 software-pipelined
  * (sigma of plane k+1 on 8 or 6 warps while the other 8 or 10 warps output plane k-1, in
- * one phase); 1-4 are FP32 only. */
+ * one phase), 5 and 6 = 32x6 software-pipelined (9 or 10 sigma warps, one round per
+ * plane); 1-6 are FP32 only. */
 int lbcad_autotune(lbcad_ctx* c, int32_t reps, int32_t* chosen, float* ms_per_cfg, int32_t ncfg);
 
 /* Selects tile shape `cfg` of the fused step explicitly (same candidates as above).

@@ -46,11 +46,32 @@ __device__ __forceinline__ int wrapmod(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
+// Shared-memory Q/psi plane: the six fields in interleaved pairs (Q_xx, Q_xy), (Q_xz, Q_yy),
+// (Q_yz, psi); field f of tile site k sits at element (f >> 1) * 2 QP + 2 k + (f & 1), so a
+// pair is one aligned two-element load.
+template <int QP>
+__device__ __forceinline__ int qidx(int f, int k) {
+  return (f >> 1) * 2 * QP + 2 * k + (f & 1);
+}
+
 template <typename T, int QW, int QP>
 struct SmemFieldsAcc {
-  const T* pl[3];  // centre of the Q/psi planes p-1, p, p+1
-  __device__ __forceinline__ T q(int k, int cx, int cy, int cz) const { return pl[cz + 1][k * QP + cy * QW + cx]; }
-  __device__ __forceinline__ T psi(int cx, int cy, int cz) const { return pl[cz + 1][5 * QP + cy * QW + cx]; }
+  const T* pl[3];  // Q/psi planes p-1, p, p+1
+  int qc;          // tile index of the centre site
+  __device__ __forceinline__ T q(int k, int cx, int cy, int cz) const {
+    return pl[cz + 1][qidx<QP>(k, qc + cy * QW + cx)];
+  }
+  __device__ __forceinline__ T psi(int cx, int cy, int cz) const { return pl[cz + 1][qidx<QP>(5, qc + cy * QW + cx)]; }
+  __device__ __forceinline__ Vec2<T> pair(int j, int cx, int cy, int cz) const {
+    const T* p = pl[cz + 1] + qidx<QP>(2 * j, qc + cy * QW + cx);
+    if constexpr (sizeof(T) == 4) {
+      const float2 v = *reinterpret_cast<const float2*>(p);
+      return Vec2<T>{v.x, v.y};
+    } else {
+      const double2 v = *reinterpret_cast<const double2*>(p);
+      return Vec2<T>{v.x, v.y};
+    }
+  }
 };
 
 template <typename T, int QW, int QP, int SW, int SP>
@@ -58,8 +79,11 @@ struct SmemUpdateAcc {
   const T* qpl[3];
   const T* spl[3];
   const T* upl[3];
-  __device__ __forceinline__ T q(int k, int cx, int cy, int cz) const { return qpl[cz + 1][k * QP + cy * QW + cx]; }
-  __device__ __forceinline__ T psi(int cx, int cy, int cz) const { return qpl[cz + 1][5 * QP + cy * QW + cx]; }
+  int qc;
+  __device__ __forceinline__ T q(int k, int cx, int cy, int cz) const {
+    return qpl[cz + 1][qidx<QP>(k, qc + cy * QW + cx)];
+  }
+  __device__ __forceinline__ T psi(int cx, int cy, int cz) const { return qpl[cz + 1][qidx<QP>(5, qc + cy * QW + cx)]; }
   __device__ __forceinline__ T sig(int k, int cx, int cy, int cz) const { return spl[cz + 1][k * SP + cy * SW + cx]; }
   __device__ __forceinline__ T mu(int cx, int cy, int cz) const { return spl[cz + 1][9 * SP + cy * SW + cx]; }
   __device__ __forceinline__ T u(int a, int cx, int cy, int cz) const { return upl[cz + 1][a * SP + cy * SW + cx]; }
@@ -137,8 +161,8 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
         const int ly = k / QW, lx = k - ly * QW;
         const long long gs = gz + ymap[ly] + xmap[lx];
 #pragma unroll
-        for (int f = 0; f < 5; ++f) dst[f * QP + k] = ld(qin + f * N + gs);
-        dst[5 * QP + k] = ld(pin + gs);
+        for (int f = 0; f < 5; ++f) dst[qidx<QP>(f, k)] = ld(qin + f * N + gs);
+        dst[qidx<QP>(5, k)] = ld(pin + gs);
       }
     };
     auto load_u_all = [&](int p) {
@@ -180,8 +204,8 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
         if (k < QP) {
           const long long gs = gzq + qoff[j];
 #pragma unroll
-          for (int f = 0; f < 5; ++f) dq[f * QP + k] = ld(qin + f * N + gs);
-          dq[5 * QP + k] = ld(pin + gs);
+          for (int f = 0; f < 5; ++f) dq[qidx<QP>(f, k)] = ld(qin + f * N + gs);
+          dq[qidx<QP>(5, k)] = ld(pin + gs);
         }
       }
       T* du = sU + uslot(pu) * G::USLOT;
@@ -199,9 +223,9 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
     // H, mu and sigma of plane p at sigma-tile site (sx, sy); returns H.
     auto sigma_site = [&](int p, int sx, int sy, T H[5]) {
       SmemFieldsAcc<T, QW, QP> acc;
-      const int qc = (sy + 1) * QW + (sx + 1);
+      acc.qc = (sy + 1) * QW + (sx + 1);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) acc.pl[j] = sQ + qslot(p - 1 + j) * G::QSLOT + qc;
+      for (int j = 0; j < 3; ++j) acc.pl[j] = sQ + qslot(p - 1 + j) * G::QSLOT;
       T q0[5], p0, dq[3][5], lapq[5], dp[3], lapp, hp[6];
       gather_fields<T>(acc, q0, p0, dq, lapq, dp, lapp, hp);
       T sig[9], mu;
@@ -238,11 +262,11 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
       __syncthreads();
       if (z >= zb && tl.x0 + tx < nx && tl.y0 + ty < ny) {
         SmemUpdateAcc<T, QW, QP, SW, SP> acc;
-        const int qc = (ty + 2) * QW + (tx + 2);
+        acc.qc = (ty + 2) * QW + (tx + 2);
         const int sc = (ty + 1) * SW + (tx + 1);
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-          acc.qpl[j] = sQ + qslot(z - 1 + j) * G::QSLOT + qc;
+          acc.qpl[j] = sQ + qslot(z - 1 + j) * G::QSLOT;
           acc.spl[j] = sS + sslot(z - 1 + j) * G::SSLOT + sc;
           acc.upl[j] = sU + uslot(z - 1 + j) * G::USLOT + sc;
         }
@@ -277,22 +301,31 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
 }
 
 // ---------------------------------------------------------------- pipelined variant
-// Same per-site arithmetic, different schedule: 32x8 tiles, 16 warps.  The first NS
-// threads compute sigma, mu and H of plane k+1 (the 340 sigma-tile sites in rounds)
-// while the other 512 - NS threads compute the output of plane k-1 (one site each), in
-// the same phase; one barrier per plane.  The output half carries the population pulls
+// Same per-site arithmetic, different schedule: 32xTY tiles, 16 warps.  The first NS
+// threads compute sigma, mu and H of plane k+1 (the 34 x (TY+2) sigma-tile sites, in
+// rounds when NS is smaller) while the other 512 - NS threads compute the output of
+// plane k-1 (one site each), in the same phase; one barrier per plane.  With TY = 6 both
+// groups finish their plane in a single round (272 sigma sites, 192 outputs).  The output half carries the population pulls
 // and the stores, so memory traffic overlaps the sigma arithmetic.  Planes for the next
 // phase arrive by cp.async during the phase.
 // Rings: Q/psi 6 planes (k-2 .. k+3), sigma/mu 4 (k-2 .. k+1), H 3 (k-1 .. k+1),
 // u 4 (k-2 .. k+1).
-template <int NS_>
+template <int TY_, int NS_>
 struct PipeGeom {
-  static constexpr int TX = 32, TY = 8, NT = 512, NS = NS_, NO = NT - NS;
+  static constexpr int TX = 32, TY = TY_, NT = 512, NS = NS_, NO = NT - NS;
   static constexpr int QW = TX + 4, QH = TY + 4, QP = QW * QH;
   static constexpr int SW = TX + 2, SH = TY + 2, SP = SW * SH;
   static constexpr int IP = TX * TY;
   static constexpr int NQS = 6, NSS = 4, NHS = 3, NUS = 4;
   static_assert(QP <= NT && SP <= NT && SP <= 2 * NS && NO >= IP, "site counts per thread");
+  // sigma rounds: NFULL full rounds of NS sites, then the RLAST remaining sites on NWL
+  // warps of LL lanes, NWL a multiple of 4 where possible so that the four schedulers of
+  // the SM each get the same share of the last round
+  static constexpr int NFULL = SP / NS, RLAST = SP - NFULL * NS;
+  static constexpr int NWL0 = ((RLAST + 31) / 32 + 3) / 4 * 4;
+  static constexpr int NWL = NWL0 < NS / 32 ? NWL0 : NS / 32;
+  static constexpr int LL = RLAST > 0 ? (RLAST + NWL - 1) / NWL : 0;
+  static_assert(LL <= 32 && NWL * LL >= RLAST, "last sigma round");
   template <typename T>
   static constexpr size_t bytes() {
     return ((size_t)NQS * 6 * QP + (size_t)NSS * 10 * SP + (size_t)NHS * 5 * IP + (size_t)NUS * 3 * SP) * sizeof(T) +
@@ -316,10 +349,10 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
   if constexpr (sizeof(T) == 4) cp_async4(dst, src); else cp_async8(dst, src);
 }
 
-template <typename T, bool SHIFT, int NS>
+template <typename T, bool SHIFT, int TY, int NS>
 __global__ void __launch_bounds__(512, 1)
     k_step_pipe(const InstDesc<T>* __restrict__ D, const FusedTile* __restrict__ tiles, int ntiles, long long total) {
-  using G = PipeGeom<NS>;
+  using G = PipeGeom<TY, NS>;
   constexpr int QW = G::QW, QP = G::QP, SW = G::SW, SP = G::SP, TX = G::TX;
   constexpr int QSLOT = 6 * QP, SSLOT = 10 * SP, HSLOT = 5 * G::IP, USLOT = 3 * SP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -374,11 +407,11 @@ __global__ void __launch_bounds__(512, 1)
     }
     auto issue_q = [&](int p) {
       if (tid < QP) {
-        T* dst = sQ + q6(p) * QSLOT + tid;
+        T* dst = sQ + q6(p) * QSLOT;
         const long long gs = (long long)wrapmod(p, nz) * plane + qoff;
 #pragma unroll
-        for (int f = 0; f < 5; ++f) cp_async_elem(dst + f * QP, qin + f * N + gs);
-        cp_async_elem(dst + 5 * QP, pin + gs);
+        for (int f = 0; f < 5; ++f) cp_async_elem(dst + qidx<QP>(f, tid), qin + f * N + gs);
+        cp_async_elem(dst + qidx<QP>(5, tid), pin + gs);
       }
     };
     auto issue_u = [&](int p) {
@@ -404,9 +437,9 @@ __global__ void __launch_bounds__(512, 1)
         for (int ss = tid; k + 1 <= ze && ss < SP; ss += G::NS) {
           const int sy = ss / SW, sx = ss - sy * SW;
           SmemFieldsAcc<T, QW, QP> acc;
-          const int qc = (sy + 1) * QW + (sx + 1);
+          acc.qc = (sy + 1) * QW + (sx + 1);
 #pragma unroll
-          for (int j = 0; j < 3; ++j) acc.pl[j] = sQ + q6(k + j) * QSLOT + qc;
+          for (int j = 0; j < 3; ++j) acc.pl[j] = sQ + q6(k + j) * QSLOT;
           T q0[5], p0, dq[3][5], lapq[5], dp[3], lapp, hp[6];
           gather_fields<T>(acc, q0, p0, dq, lapq, dp, lapp, hp);
           T H[5], sig[9], mu;
@@ -430,11 +463,11 @@ __global__ void __launch_bounds__(512, 1)
         const int tx = site % TX, ty = site / TX;
         if (site < G::IP && tl.x0 + tx < nx && tl.y0 + ty < ny) {
           SmemUpdateAcc<T, QW, QP, SW, SP> acc;
-          const int qc = (ty + 2) * QW + (tx + 2);
+          acc.qc = (ty + 2) * QW + (tx + 2);
           const int sc = (ty + 1) * SW + (tx + 1);
 #pragma unroll
           for (int j = 0; j < 3; ++j) {
-            acc.qpl[j] = sQ + q6(z - 1 + j) * QSLOT + qc;
+            acc.qpl[j] = sQ + q6(z - 1 + j) * QSLOT;
             acc.spl[j] = sS + s4(z - 1 + j) * SSLOT + sc;
             acc.upl[j] = sU + s4(z - 1 + j) * USLOT + sc;
           }
@@ -494,13 +527,13 @@ cudaError_t prepare_cfg(FusedCfg* cfg) {
 // 64x8 (one block per SM, fewer redundant halo sites).  FP64 only fits 32x8.
 template <typename T, bool SHIFT>
 int LaunchFused<T, SHIFT>::num_configs() {
-  return sizeof(T) == 4 ? 5 : 1;
+  return sizeof(T) == 4 ? 7 : 1;
 }
 
-template <typename T, bool SHIFT, int NS>
+template <typename T, bool SHIFT, int TY, int NS>
 cudaError_t prepare_pipe(FusedCfg* cfg) {
-  using G = PipeGeom<NS>;
-  auto k = k_step_pipe<T, SHIFT, NS>;
+  using G = PipeGeom<TY, NS>;
+  auto k = k_step_pipe<T, SHIFT, TY, NS>;
   cfg->tx = G::TX;
   cfg->ty = G::TY;
   cfg->threads = G::NT;
@@ -510,11 +543,11 @@ cudaError_t prepare_pipe(FusedCfg* cfg) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cfg->blocks_per_sm, k, G::NT, cfg->smem);
 }
 
-template <typename T, bool SHIFT, int NS>
+template <typename T, bool SHIFT, int TY, int NS>
 cudaError_t launch_pipe(const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles, long long total, int grid,
                         cudaStream_t s) {
-  using G = PipeGeom<NS>;
-  k_step_pipe<T, SHIFT, NS><<<grid, G::NT, G::template bytes<T>(), s>>>(d_desc, tiles, ntiles, total);
+  using G = PipeGeom<TY, NS>;
+  k_step_pipe<T, SHIFT, TY, NS><<<grid, G::NT, G::template bytes<T>(), s>>>(d_desc, tiles, ntiles, total);
   return cudaGetLastError();
 }
 
@@ -523,8 +556,10 @@ cudaError_t LaunchFused<T, SHIFT>::prepare(int cfg_index, FusedCfg* cfg) {
   if constexpr (sizeof(T) == 4) {
     if (cfg_index == 1) return prepare_cfg<T, SHIFT, 32, 16>(cfg);
     if (cfg_index == 2) return prepare_cfg<T, SHIFT, 64, 8>(cfg);
-    if (cfg_index == 3) return prepare_pipe<T, SHIFT, 256>(cfg);
-    if (cfg_index == 4) return prepare_pipe<T, SHIFT, 192>(cfg);
+    if (cfg_index == 3) return prepare_pipe<T, SHIFT, 8, 256>(cfg);
+    if (cfg_index == 4) return prepare_pipe<T, SHIFT, 8, 192>(cfg);
+    if (cfg_index == 5) return prepare_pipe<T, SHIFT, 6, 288>(cfg);
+    if (cfg_index == 6) return prepare_pipe<T, SHIFT, 6, 320>(cfg);
   }
   if (cfg_index == 0) return prepare_cfg<T, SHIFT, 32, 8>(cfg);
   return cudaErrorInvalidValue;
@@ -536,8 +571,10 @@ cudaError_t LaunchFused<T, SHIFT>::step(int cfg_index, const InstDesc<T>* d_desc
   if constexpr (sizeof(T) == 4) {
     if (cfg_index == 1) return launch_cfg<T, SHIFT, 32, 16>(d_desc, tiles, ntiles, total, grid, s);
     if (cfg_index == 2) return launch_cfg<T, SHIFT, 64, 8>(d_desc, tiles, ntiles, total, grid, s);
-    if (cfg_index == 3) return launch_pipe<T, SHIFT, 256>(d_desc, tiles, ntiles, total, grid, s);
-    if (cfg_index == 4) return launch_pipe<T, SHIFT, 192>(d_desc, tiles, ntiles, total, grid, s);
+    if (cfg_index == 3) return launch_pipe<T, SHIFT, 8, 256>(d_desc, tiles, ntiles, total, grid, s);
+    if (cfg_index == 4) return launch_pipe<T, SHIFT, 8, 192>(d_desc, tiles, ntiles, total, grid, s);
+    if (cfg_index == 5) return launch_pipe<T, SHIFT, 6, 288>(d_desc, tiles, ntiles, total, grid, s);
+    if (cfg_index == 6) return launch_pipe<T, SHIFT, 6, 320>(d_desc, tiles, ntiles, total, grid, s);
   }
   if (cfg_index == 0) return launch_cfg<T, SHIFT, 32, 8>(d_desc, tiles, ntiles, total, grid, s);
   return cudaErrorInvalidValue;

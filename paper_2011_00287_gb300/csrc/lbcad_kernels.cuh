@@ -64,6 +64,39 @@ __device__ __forceinline__ void full3(const T q[5], T Q[3][3]) {
   Q[2][0] = q[2]; Q[2][1] = q[4]; Q[2][2] = -q[0] - q[3];
 }
 
+// Two-lane values for packed arithmetic: float2 uses the f32x2 instructions (one issue
+// slot for two lanes); other types fall back to two scalar operations.
+template <typename T>
+struct Vec2 {
+  T x, y;
+};
+template <typename T>
+__device__ __forceinline__ Vec2<T> v2(T a, T b) { return Vec2<T>{a, b}; }
+template <typename T>
+__device__ __forceinline__ Vec2<T> add2(Vec2<T> a, Vec2<T> b) { return Vec2<T>{a.x + b.x, a.y + b.y}; }
+template <typename T>
+__device__ __forceinline__ Vec2<T> sub2(Vec2<T> a, Vec2<T> b) { return Vec2<T>{a.x - b.x, a.y - b.y}; }
+template <typename T>
+__device__ __forceinline__ Vec2<T> fma2(Vec2<T> a, Vec2<T> b, Vec2<T> c) {
+  return Vec2<T>{a.x * b.x + c.x, a.y * b.y + c.y};
+}
+template <typename T>
+__device__ __forceinline__ Vec2<T> mul2(Vec2<T> a, Vec2<T> b) { return Vec2<T>{a.x * b.x, a.y * b.y}; }
+__device__ __forceinline__ float2 f2(Vec2<float> a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ Vec2<float> v2f(float2 a) { return Vec2<float>{a.x, a.y}; }
+template <>
+__device__ __forceinline__ Vec2<float> add2(Vec2<float> a, Vec2<float> b) { return v2f(__fadd2_rn(f2(a), f2(b))); }
+template <>
+__device__ __forceinline__ Vec2<float> sub2(Vec2<float> a, Vec2<float> b) {
+  return v2f(__ffma2_rn(f2(b), make_float2(-1.f, -1.f), f2(a)));  // a - b, one rounding
+}
+template <>
+__device__ __forceinline__ Vec2<float> fma2(Vec2<float> a, Vec2<float> b, Vec2<float> c) {
+  return v2f(__ffma2_rn(f2(a), f2(b), f2(c)));
+}
+template <>
+__device__ __forceinline__ Vec2<float> mul2(Vec2<float> a, Vec2<float> b) { return v2f(__fmul2_rn(f2(a), f2(b))); }
+
 // H (5), mu and the total stress sigma (9, row-major a*3+b) at one site from Q, psi and
 // their stencils: dq[a][k] = d_a of stored component k, lapq[k], dp[a] = d_a psi,
 // lapp, hp = Hessian of psi (xx, yy, zz, xy, xz, yz).
@@ -224,40 +257,55 @@ __device__ __forceinline__ T lap_from_diffs(const T d[19]) {
 }
 
 // a1: gradient and Laplacian of the five Q components and psi, and the Hessian of psi
-// (three-point differences on the diagonal, four corners off it).
+// (three-point differences on the diagonal, four corners off it).  The six fields are
+// taken in pairs (Q_xx, Q_xy), (Q_xz, Q_yy), (Q_yz, psi) through A::pair(j, ...), so one
+// two-lane operation advances two fields.
 template <typename T, class A>
 __device__ __forceinline__ void gather_fields(const A& acc, T q0[5], T& p0, T dq[3][5], T lapq[5], T dp[3],
                                               T& lapp, T hp[6]) {
+  using V = Vec2<T>;
+  const V k2 = v2(T(2), T(2)), k12 = v2(T(1.0 / 12.0), T(1.0 / 12.0)), k6 = v2(T(1.0 / 6.0), T(1.0 / 6.0));
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    T f[19];
+  for (int j = 0; j < 3; ++j) {
+    V f[19];
 #pragma unroll
-    for (int i = 0; i < 19; ++i)
-      f[i] = (k < 5) ? acc.q(k, lat_c(i, 0), lat_c(i, 1), lat_c(i, 2)) : acc.psi(lat_c(i, 0), lat_c(i, 1), lat_c(i, 2));
-    T d[19], D[19];
+    for (int i = 0; i < 19; ++i) f[i] = acc.pair(j, lat_c(i, 0), lat_c(i, 1), lat_c(i, 2));
+    V d[19], D[19];
 #pragma unroll
-    for (int i = 1; i < 19; ++i) d[i] = f[i] - f[0];
+    for (int i = 1; i < 19; ++i) d[i] = sub2(f[i], f[0]);
 #pragma unroll
-    for (int i = 1; i < 19; i += 2) D[i] = d[i] - d[i + 1];
-    T g[3];
-    grad_from_pairs(D, g);
-    const T lp = lap_from_diffs(d);
-    if (k < 5) {
-      q0[k] = f[0];
+    for (int i = 1; i < 19; i += 2) D[i] = sub2(d[i], d[i + 1]);
+    // gradient from opposite pairs: (1/12)[2 D_face + sum of signed edge pairs]
+    V g[3];
+    g[0] = mul2(fma2(D[1], k2, add2(add2(D[7], D[9]), add2(D[11], D[13]))), k12);
+    g[1] = mul2(fma2(D[3], k2, add2(sub2(D[7], D[9]), add2(D[15], D[17]))), k12);
+    g[2] = mul2(fma2(D[5], k2, add2(sub2(D[11], D[13]), sub2(D[15], D[17]))), k12);
+    // Laplacian from differences to the centre: (1/3) faces + (1/6) edges
+    const V sf = add2(add2(add2(d[1], d[2]), add2(d[3], d[4])), add2(d[5], d[6]));
+    const V se = add2(add2(add2(add2(d[7], d[8]), add2(d[9], d[10])), add2(add2(d[11], d[12]), add2(d[13], d[14]))),
+                      add2(add2(d[15], d[16]), add2(d[17], d[18])));
+    const V lp = mul2(fma2(sf, k2, se), k6);
+    const int k0 = 2 * j;
+    q0[k0] = f[0].x;
+    lapq[k0] = lp.x;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) dq[a][k] = g[a];
-      lapq[k] = lp;
+    for (int a = 0; a < 3; ++a) dq[a][k0] = g[a].x;
+    if (j < 2) {
+      q0[k0 + 1] = f[0].y;
+      lapq[k0 + 1] = lp.y;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) dq[a][k0 + 1] = g[a].y;
     } else {
-      p0 = f[0];
+      p0 = f[0].y;
+      lapp = lp.y;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) dp[a] = g[a];
-      lapp = lp;
-      hp[0] = d[1] + d[2];
-      hp[1] = d[3] + d[4];
-      hp[2] = d[5] + d[6];
-      hp[3] = T(0.25) * ((d[7] + d[8]) - (d[9] + d[10]));
-      hp[4] = T(0.25) * ((d[11] + d[12]) - (d[13] + d[14]));
-      hp[5] = T(0.25) * ((d[15] + d[16]) - (d[17] + d[18]));
+      for (int a = 0; a < 3; ++a) dp[a] = g[a].y;
+      hp[0] = d[1].y + d[2].y;
+      hp[1] = d[3].y + d[4].y;
+      hp[2] = d[5].y + d[6].y;
+      hp[3] = T(0.25) * ((d[7].y + d[8].y) - (d[9].y + d[10].y));
+      hp[4] = T(0.25) * ((d[11].y + d[12].y) - (d[13].y + d[14].y));
+      hp[5] = T(0.25) * ((d[15].y + d[16].y) - (d[17].y + d[18].y));
     }
   }
 }
@@ -442,6 +490,11 @@ struct GlobalAcc {
   __device__ __forceinline__ T sig(int k, int cx, int cy, int cz) const { return ld(sg + k * N + nb.off(cx, cy, cz)); }
   __device__ __forceinline__ T mu(int cx, int cy, int cz) const { return ld(mu_ + nb.off(cx, cy, cz)); }
   __device__ __forceinline__ T u(int a, int cx, int cy, int cz) const { return ld(u_ + a * N + nb.off(cx, cy, cz)); }
+  // fields (2j, 2j+1) of the order (Q_xx, Q_xy, Q_xz, Q_yy, Q_yz, psi)
+  __device__ __forceinline__ Vec2<T> pair(int j, int cx, int cy, int cz) const {
+    const long long o = nb.off(cx, cy, cz);
+    return Vec2<T>{ld(q_ + (2 * j) * N + o), j < 2 ? ld(q_ + (2 * j + 1) * N + o) : ld(ps + o)};
+  }
 };
 
 // ---------------------------------------------------------------- k_fields

@@ -262,7 +262,7 @@ def test_tile_shapes_and_autotune_give_identical_results():
     ref = L.Simulation([shape], [_lib_params(shape, L.FP32, **kw)], seed=4)
     ref.step(5)
     fr = ref.get_fields(0)
-    for cfg in range(5):
+    for cfg in range(L.lbcad.N_TILE_CONFIGS):
         s = L.Simulation([shape], [_lib_params(shape, L.FP32, **kw)], seed=4)
         s.set_tiles(cfg)
         s.step(5)
@@ -272,7 +272,7 @@ def test_tile_shapes_and_autotune_give_identical_results():
     s = L.Simulation([shape], [_lib_params(shape, L.FP32, **kw)], seed=4)
     s.step(2)
     chosen, ms = s.autotune(3)
-    assert 0 <= chosen < 5 and s.step_count == 2
+    assert 0 <= chosen < L.lbcad.N_TILE_CONFIGS and s.step_count == 2
     s.step(3)
     f = s.get_fields(0)
     for k in fr:
