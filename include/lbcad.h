@@ -50,9 +50,9 @@ extern "C" {
 #define LBCAD_FP32 0 /* FP32 storage and arithmetic; populations stored as f_i - w_i rho0 */
 #define LBCAD_FP64 1 /* FP64 storage and arithmetic; populations stored unshifted         */
 #define LBCAD_EULER 0
-#define LBCAD_HEUN 1   /* predictor-corrector of Sec. 3 (oracle only for now)             */
+#define LBCAD_HEUN 1   /* predictor-corrector of Sec. 3 (Heun, velocity held fixed)       */
 #define LBCAD_LAGGED 0 /* Q and psi advected with u of the previous step                  */
-#define LBCAD_SYNC 1   /* advected with u of this step (oracle only for now)              */
+#define LBCAD_SYNC 1   /* advected with u of this step                                    */
 
 #define LBCAD_FIELD_G 1u
 #define LBCAD_FIELD_RHO 2u
@@ -90,8 +90,8 @@ typedef struct {
   double S0;       /* scalar order of the initial helix inside the droplet           */
   double noise;    /* amplitude of the seeded uniform noise on Q inside the droplet  */
   int32_t precision;  /* LBCAD_FP32 or LBCAD_FP64                                     */
-  int32_t integrator; /* LBCAD_EULER (LBCAD_HEUN returns LBCAD_E_UNSUPPORTED)          */
-  int32_t coupling;   /* LBCAD_LAGGED (LBCAD_SYNC returns LBCAD_E_UNSUPPORTED)         */
+  int32_t integrator; /* LBCAD_EULER or LBCAD_HEUN; one value for all instances        */
+  int32_t coupling;   /* LBCAD_LAGGED or LBCAD_SYNC; one value for all instances       */
   int32_t device;     /* CUDA device ordinal; -1 = the current device                 */
   void* stream;       /* cudaStream_t for all work; NULL = a private non-blocking stream */
   lbcad_alloc_fn alloc; /* NULL = cudaMalloc                                          */
@@ -145,6 +145,14 @@ int lbcad_step(lbcad_ctx* c, int64_t n);
  * drops a captured graph. */
 #define LBCAD_PATH_FUSED 0
 #define LBCAD_PATH_TWO_KERNEL 1
+/* LBCAD_PATH_STAGED: per-site kernels in the order fields -> LB (force, pull, collision;
+ * writes u of this step) -> order-parameter update, and for LBCAD_HEUN a second fields
+ * pass at the predicted Q, psi and the corrector (Sec. 3).  The only path for LBCAD_HEUN
+ * or LBCAD_SYNC, selected at create; Euler/lagged contexts may select it as a third
+ * cross-check (same per-site arithmetic as the other two).  Scratch: 15 values per site,
+ * 27 with LBCAD_HEUN.  Fused/two-kernel paths, tile shapes, autotune and the adjoint return
+ * LBCAD_E_UNSUPPORTED on Heun or sync contexts. */
+#define LBCAD_PATH_STAGED 2
 int lbcad_set_path(lbcad_ctx* c, int32_t path);
 
 /* Picks the fastest tile shape of the fused step for this context by timing each

@@ -49,6 +49,8 @@ struct InstDesc {
   T* sig;          // scratch: stress [9][N]
   T* mu;           // scratch: chemical potential [N]
   T* H;            // scratch: molecular field [5][N]
+  T* rq;           // staged path, Heun: right-hand side R(Q, psi) at t [6][N] (Q 5, psi 1)
+  T* qp;           // staged path, Heun: predicted Q, psi [6][N]
   Coef<T> c;
 };
 
@@ -57,6 +59,11 @@ template <typename T, bool SHIFT>
 struct Launch {
   static cudaError_t step(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, cudaStream_t s);
   static cudaError_t fields(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, cudaStream_t s);
+  // Staged step: fields -> LB -> order-parameter update (Euler), or fields -> LB ->
+  // predictor -> fields at the predicted state -> corrector (Heun).  sync advects with the
+  // velocity of this step instead of the previous one.
+  static cudaError_t staged(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, bool heun,
+                            bool sync, cudaStream_t s);
   static cudaError_t get_fields(const InstDesc<T>& I, uint32_t mask, double* dst, cudaStream_t s);
   static cudaError_t set_fields(const InstDesc<T>& I, uint32_t mask, const double* src, T* g_target,
                                 T* q_target, T* psi_target, T* u_target, cudaStream_t s);

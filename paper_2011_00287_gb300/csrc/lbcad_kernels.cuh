@@ -310,11 +310,9 @@ __device__ __forceinline__ void gather_fields(const A& acc, T q0[5], T& p0, T dq
   }
 }
 
-// a3 (divergence) and the stencils of a4: F = div sigma, lap mu, W_ab = d_b u_a, and the
-// face values of Q, psi and u for the upwind terms (face slot 2a: +e_a, 2a+1: -e_a).
+// a3 (divergence): F_a = d_b sigma_ab from opposite-pair differences of sigma.
 template <typename T, class A>
-__device__ __forceinline__ void gather_update(const A& acc, T F[3], T& lapmu, T Wg[3][3], T q0[5], T qf[6][5],
-                                              T& p0, T pf[6], T u0[3], T uf[6]) {
+__device__ __forceinline__ void gather_force(const A& acc, T F[3]) {
   // F_a = d_x sigma_ax + d_y sigma_ay + d_z sigma_az
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -334,6 +332,13 @@ __device__ __forceinline__ void gather_update(const A& acc, T F[3], T& lapmu, T 
     }
     F[a] = (T(2) * acc2 + acc1) * T(1.0 / 12.0);
   }
+}
+
+// The stencils of a4: lap mu, W_ab = d_b u_a, and the face values of Q, psi and u for the
+// upwind terms (face slot 2a: +e_a, 2a+1: -e_a).
+template <typename T, class A>
+__device__ __forceinline__ void gather_op(const A& acc, T& lapmu, T Wg[3][3], T q0[5], T qf[6][5], T& p0, T pf[6],
+                                          T u0[3], T uf[6]) {
   // lap mu
   {
     T d[19];
@@ -367,14 +372,21 @@ __device__ __forceinline__ void gather_update(const A& acc, T F[3], T& lapmu, T 
   p0 = acc.psi(0, 0, 0);
 }
 
-// a4 + a5 at one site: Beris-Edwards update of Q (Eq. 2) with the velocity of the
-// previous step, Cahn-Hilliard update of psi (Eq. 1), and BGK + Guo collision of the
-// pulled populations g (Eqs. 6-8; overwritten with the post-collision values).  The
-// equilibrium and forcing terms of opposite velocities c and -c share their even part.
-template <typename T, bool SHIFT>
-__device__ __forceinline__ void update_math(const Coef<T>& c, const T F[3], T lapmu, const T Wg[3][3],
-                                            const T q0[5], const T qf[6][5], T p0, const T pf[6], const T u0[3],
-                                            const T uf[6], const T Hs[5], T g[19], T qn[5], T& pn, T u[3]) {
+// a3 + the stencils of a4, for the one-pass step.
+template <typename T, class A>
+__device__ __forceinline__ void gather_update(const A& acc, T F[3], T& lapmu, T Wg[3][3], T q0[5], T qf[6][5],
+                                              T& p0, T pf[6], T u0[3], T uf[6]) {
+  gather_force<T>(acc, F);
+  gather_op<T>(acc, lapmu, Wg, q0, qf, p0, pf, u0, uf);
+}
+
+// a4 at one site: Beris-Edwards update of Q (Eq. 2) and Cahn-Hilliard update of psi
+// (Eq. 1) with the advecting velocity u0/uf (and its gradient Wg).  RHS = false gives the
+// Euler step Q + R(Q), RHS = true the right-hand side R(Q) alone (for the Heun stages).
+template <typename T, bool RHS>
+__device__ __forceinline__ void op_update(const Coef<T>& c, T lapmu, const T Wg[3][3], const T q0[5],
+                                          const T qf[6][5], T p0, const T pf[6], const T u0[3], const T uf[6],
+                                          const T Hs[5], T qn[5], T& pn) {
   T adv[5] = {T(0), T(0), T(0), T(0), T(0)};
   T divJ = T(0);
 #pragma unroll
@@ -426,10 +438,18 @@ __device__ __forceinline__ void update_math(const Coef<T>& c, const T F[3], T la
     }
     T S = c.xi * (DQ + QD) + c23 * Dm[i][j] + (OQ - QO) + cq * Q[i][j];
     if (i == j) S += cdiag;
-    qn[k] = q0[k] - adv[k] + S + c.gammaQ * Hs[k];
+    if (RHS) qn[k] = -adv[k] + S + c.gammaQ * Hs[k];
+    else qn[k] = q0[k] - adv[k] + S + c.gammaQ * Hs[k];
   }
-  pn = p0 - divJ + c.M * lapmu;
+  if (RHS) pn = -divJ + c.M * lapmu;
+  else pn = p0 - divJ + c.M * lapmu;
+}
 
+// a5 at one site: moments of the pulled populations g and the force F, then BGK + Guo
+// collision (Eqs. 6-8); g is overwritten with the post-collision values, u = velocity.
+// The equilibrium and forcing terms of opposite velocities c and -c share their even part.
+template <typename T, bool SHIFT>
+__device__ __forceinline__ void lb_collide(const Coef<T>& c, const T F[3], T g[19], T u[3]) {
   // moments from opposite pairs
   T m0 = g[0];
   T j[3] = {T(0), T(0), T(0)};
@@ -475,6 +495,16 @@ __device__ __forceinline__ void update_math(const Coef<T>& c, const T F[3], T la
   }
 }
 
+// a4 + a5 of the one-pass step: Euler update of Q and psi with the velocity of the
+// previous step, and the collision of the pulled populations.
+template <typename T, bool SHIFT>
+__device__ __forceinline__ void update_math(const Coef<T>& c, const T F[3], T lapmu, const T Wg[3][3],
+                                            const T q0[5], const T qf[6][5], T p0, const T pf[6], const T u0[3],
+                                            const T uf[6], const T Hs[5], T g[19], T qn[5], T& pn, T u[3]) {
+  op_update<T, false>(c, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hs, qn, pn);
+  lb_collide<T, SHIFT>(c, F, g, u);
+}
+
 // Neighbour reads straight from global memory with periodic wrap (two-kernel path).
 template <typename T>
 struct GlobalAcc {
@@ -498,7 +528,9 @@ struct GlobalAcc {
 };
 
 // ---------------------------------------------------------------- k_fields
-template <typename T>
+// H, mu and sigma of (q_in, psi_in) into the scratch; with PRED, H and mu of the Heun
+// predicted state qp into the (then free) sigma scratch: H at sig[0..5N), mu at sig[5N..6N).
+template <typename T, bool PRED = false>
 __global__ void __launch_bounds__(kStepBlock) k_fields(const InstDesc<T>* __restrict__ D, int ninst) {
   const int ii = find_inst(D, ninst, (long long)blockIdx.x);
   const InstDesc<T>& I = D[ii];
@@ -511,19 +543,110 @@ __global__ void __launch_bounds__(kStepBlock) k_fields(const InstDesc<T>* __rest
   const int y = (int)(t % ny);
   const int z = (int)(t / ny);
   GlobalAcc<T> acc;
-  acc.q_ = I.q_in;
-  acc.ps = I.psi_in;
+  acc.q_ = PRED ? I.qp : I.q_in;
+  acc.ps = PRED ? I.qp + 5 * N : I.psi_in;
   acc.N = N;
   acc.nb = make_nbr(x, y, z, nx, ny, nz);
   T q0[5], p0, dq[3][5], lapq[5], dp[3], lapp, hp[6];
   gather_fields<T>(acc, q0, p0, dq, lapq, dp, lapp, hp);
   T H[5], sig[9], mu;
   local_fields<T>(I.c, q0, p0, dq, lapq, dp, lapp, hp, H, mu, sig);
+  if (PRED) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) I.sig[k * N + s] = H[k];
+    I.sig[5 * N + s] = mu;
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < 5; ++k) I.H[k * N + s] = H[k];
   I.mu[s] = mu;
 #pragma unroll
   for (int k = 0; k < 9; ++k) I.sig[k * N + s] = sig[k];
+}
+
+// ---------------------------------------------------------------- staged path
+// k_lb: F = div sigma from the scratch, pull, moments and collision (a3, a5):
+// g_out, u_out = velocity of this step.
+template <typename T, bool SHIFT>
+__global__ void __launch_bounds__(kStepBlock) k_lb(const InstDesc<T>* __restrict__ D, int ninst) {
+  const int ii = find_inst(D, ninst, (long long)blockIdx.x);
+  const InstDesc<T>& I = D[ii];
+  const long long N = I.N;
+  const long long s = ((long long)blockIdx.x - I.blk0) * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  const int nx = I.nx, ny = I.ny, nz = I.nz;
+  const int x = (int)(s % nx);
+  const long long t = s / nx;
+  const int y = (int)(t % ny);
+  const int z = (int)(t / ny);
+  GlobalAcc<T> acc;
+  acc.sg = I.sig;
+  acc.N = N;
+  acc.nb = make_nbr(x, y, z, nx, ny, nz);
+  T F[3];
+  gather_force<T>(acc, F);
+  T g[19];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) g[i] = ld(I.g_in + i * N + acc.nb.off(-lat_c(i, 0), -lat_c(i, 1), -lat_c(i, 2)));
+  T u[3];
+  lb_collide<T, SHIFT>(I.c, F, g, u);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) I.g_out[i * N + s] = g[i];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) I.u_out[a * N + s] = u[a];
+}
+
+// k_op: the order-parameter update (a4) of the staged path, advecting with u_in (lagged)
+// or u_out (sync, written by k_lb of this step).
+//   STAGE 0  Euler:           q_out = Q + R(Q)                        (H, mu from the scratch)
+//   STAGE 1  Heun predictor:  rq = R(Q), qp = Q + rq
+//   STAGE 2  Heun corrector:  q_out = Q + (rq + R(qp)) / 2            (H, mu of qp in sigma)
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(kStepBlock) k_op(const InstDesc<T>* __restrict__ D, int ninst, int sync) {
+  const int ii = find_inst(D, ninst, (long long)blockIdx.x);
+  const InstDesc<T>& I = D[ii];
+  const long long N = I.N;
+  const long long s = ((long long)blockIdx.x - I.blk0) * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  const int nx = I.nx, ny = I.ny, nz = I.nz;
+  const int x = (int)(s % nx);
+  const long long t = s / nx;
+  const int y = (int)(t % ny);
+  const int z = (int)(t / ny);
+  GlobalAcc<T> acc;
+  acc.q_ = STAGE == 2 ? I.qp : I.q_in;
+  acc.ps = STAGE == 2 ? I.qp + 5 * N : I.psi_in;
+  acc.mu_ = STAGE == 2 ? I.sig + 5 * N : I.mu;
+  acc.u_ = sync ? I.u_out : I.u_in;
+  acc.N = N;
+  acc.nb = make_nbr(x, y, z, nx, ny, nz);
+  T lapmu, Wg[3][3], q0[5], qf[6][5], p0, pf[6], u0[3], uf[6];
+  gather_op<T>(acc, lapmu, Wg, q0, qf, p0, pf, u0, uf);
+  const T* Hsrc = STAGE == 2 ? I.sig : I.H;
+  T Hs[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) Hs[k] = Hsrc[k * N + s];
+  T qn[5], pn;
+  if (STAGE == 0) {
+    op_update<T, false>(I.c, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hs, qn, pn);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) I.q_out[k * N + s] = qn[k];
+    I.psi_out[s] = pn;
+  } else if (STAGE == 1) {
+    op_update<T, true>(I.c, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hs, qn, pn);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      I.rq[k * N + s] = qn[k];
+      I.qp[k * N + s] = q0[k] + qn[k];
+    }
+    I.rq[5 * N + s] = pn;
+    I.qp[5 * N + s] = p0 + pn;
+  } else {
+    op_update<T, true>(I.c, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hs, qn, pn);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) I.q_out[k * N + s] = I.q_in[k * N + s] + T(0.5) * (I.rq[k * N + s] + qn[k]);
+    I.psi_out[s] = I.psi_in[s] + T(0.5) * (I.rq[5 * N + s] + pn);
+  }
 }
 
 // ---------------------------------------------------------------- k_update
@@ -711,6 +834,22 @@ template <typename T, bool SHIFT>
 cudaError_t Launch<T, SHIFT>::fields(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs,
                                      cudaStream_t s) {
   k_fields<T><<<(unsigned)total_blocks, bs, 0, s>>>(d_desc, ninst);
+  return cudaGetLastError();
+}
+
+template <typename T, bool SHIFT>
+cudaError_t Launch<T, SHIFT>::staged(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, bool heun,
+                                     bool sync, cudaStream_t s) {
+  const unsigned g = (unsigned)total_blocks;
+  k_fields<T><<<g, bs, 0, s>>>(d_desc, ninst);
+  k_lb<T, SHIFT><<<g, bs, 0, s>>>(d_desc, ninst);
+  if (!heun) {
+    k_op<T, 0><<<g, bs, 0, s>>>(d_desc, ninst, sync ? 1 : 0);
+  } else {
+    k_op<T, 1><<<g, bs, 0, s>>>(d_desc, ninst, sync ? 1 : 0);
+    k_fields<T, true><<<g, bs, 0, s>>>(d_desc, ninst);
+    k_op<T, 2><<<g, bs, 0, s>>>(d_desc, ninst, sync ? 1 : 0);
+  }
   return cudaGetLastError();
 }
 

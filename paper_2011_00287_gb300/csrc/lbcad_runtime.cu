@@ -31,6 +31,8 @@ struct Inst {
   void* sig = nullptr;
   void* mu = nullptr;
   void* H = nullptr;
+  void* rq = nullptr;  // Heun: right-hand side at t (6 per site)
+  void* qp = nullptr;  // Heun: predicted Q, psi (6 per site)
   long long blk0 = 0, nblk = 0;
 };
 
@@ -70,6 +72,8 @@ struct lbcad_ctx {
   double* staging = nullptr;
   size_t staging_bytes = 0;
   int path = LBCAD_PATH_FUSED;
+  int integrator = LBCAD_EULER;
+  int coupling = LBCAD_LAGGED;
   bool scratch_ready = false;
   FusedTile* tiles = nullptr;
   size_t tiles_cap = 0;
@@ -81,6 +85,8 @@ struct lbcad_ctx {
   void* adj_lam = nullptr;  // cotangent of the initial state of the last lbcad_adjoint
   std::string err;
   size_t elem() const { return prec == LBCAD_FP64 ? sizeof(double) : sizeof(float); }
+  // Heun or sync need the staged path
+  bool staged_only() const { return integrator != LBCAD_EULER || coupling != LBCAD_LAGGED; }
 };
 
 namespace {
@@ -169,6 +175,7 @@ InstDesc<T> make_desc(const Inst& I, int parity) {
   d.psi_in = (const T*)I.pb[a]; d.psi_out = (T*)I.pb[b];
   d.u_in = (const T*)I.ub[a]; d.u_out = (T*)I.ub[b];
   d.sig = (T*)I.sig; d.mu = (T*)I.mu; d.H = (T*)I.H;
+  d.rq = (T*)I.rq; d.qp = (T*)I.qp;
   d.c = coefs<T>(I.p);
   return d;
 }
@@ -232,6 +239,7 @@ int upload_init(lbcad_ctx* c, Inst& I, uint64_t seed, int idx) {
 
 int upload_descs(lbcad_ctx* c);
 int prepare_fused(lbcad_ctx* c, int cfg_index);
+int ensure_scratch(lbcad_ctx* c);
 
 int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint64_t seed, lbcad_ctx** out) {
   g_create_err.clear();
@@ -243,15 +251,15 @@ int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint
     if (!v.empty()) return fail(nullptr, LBCAD_E_INVALID_ARG, "instance " + std::to_string(i) + ": " + v);
     if (params[i].precision != params[0].precision)
       return fail(nullptr, LBCAD_E_INVALID_ARG, "all instances must share one precision");
-    if (params[i].integrator != LBCAD_EULER)
-      return fail(nullptr, LBCAD_E_UNSUPPORTED, "the GPU path implements the Euler integrator only");
-    if (params[i].coupling != LBCAD_LAGGED)
-      return fail(nullptr, LBCAD_E_UNSUPPORTED, "the GPU path implements lagged coupling only");
+    if (params[i].integrator != params[0].integrator || params[i].coupling != params[0].coupling)
+      return fail(nullptr, LBCAD_E_INVALID_ARG, "all instances must share one integrator and one coupling");
   }
   lbcad_ctx* c = new (std::nothrow) lbcad_ctx();
   if (!c) return fail(nullptr, LBCAD_E_OOM, "host allocation failed");
   const lbcad_params& p0 = params[0];
   c->prec = p0.precision;
+  c->integrator = p0.integrator;
+  c->coupling = p0.coupling;
   c->alloc = p0.alloc;
   c->free = p0.free;
   c->user = p0.alloc_user;
@@ -313,6 +321,10 @@ int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint
   if (!c->obs_partial || !c->obs_out) return bail(LBCAD_E_OOM, "device allocation failed");
   if (upload_descs(c) != LBCAD_OK) return bail(LBCAD_E_CUDA, "");
   if ((code = prepare_fused(c, 0)) != LBCAD_OK) return bail(code, "");
+  if (c->staged_only()) {
+    if ((code = ensure_scratch(c)) != LBCAD_OK) return bail(code, "");
+    c->path = LBCAD_PATH_STAGED;
+  }
   for (int i = 0; i < n; ++i) {
     code = (c->prec == LBCAD_FP64) ? upload_init<double>(c, c->inst[i], seed, i)
                                    : upload_init<float>(c, c->inst[i], seed, i);
@@ -340,7 +352,8 @@ int upload_descs(lbcad_ctx* c) {
   return LBCAD_OK;
 }
 
-// Scratch (sigma, mu, H per site) of the two-kernel path, allocated on first use.
+// Scratch (sigma, mu, H per site) of the two-kernel and staged paths, allocated on first
+// use; Heun contexts also hold the right-hand side at t and the predicted state.
 int ensure_scratch(lbcad_ctx* c) {
   if (c->scratch_ready) return LBCAD_OK;
   const size_t es = c->elem();
@@ -349,6 +362,11 @@ int ensure_scratch(lbcad_ctx* c) {
     I.mu = dev_alloc(c, I.N * es);
     I.H = dev_alloc(c, 5 * I.N * es);
     if (!I.sig || !I.mu || !I.H) return fail(c, LBCAD_E_OOM, "scratch allocation failed");
+    if (c->integrator == LBCAD_HEUN) {
+      I.rq = dev_alloc(c, 6 * I.N * es);
+      I.qp = dev_alloc(c, 6 * I.N * es);
+      if (!I.rq || !I.qp) return fail(c, LBCAD_E_OOM, "scratch allocation failed");
+    }
   }
   c->scratch_ready = true;
   return upload_descs(c);
@@ -407,8 +425,15 @@ int launch_steps(lbcad_ctx* c, int64_t n) {
   for (int64_t k = 0; k < n; ++k) {
     const int par = (int)(c->step & 1);
     cudaError_t e;
+    const bool heun = c->integrator == LBCAD_HEUN, sync = c->coupling == LBCAD_SYNC;
     if (c->path == LBCAD_PATH_FUSED) {
       e = launch_fused(c, par);
+    } else if (c->path == LBCAD_PATH_STAGED) {
+      e = (c->prec == LBCAD_FP64)
+              ? Launch<double, false>::staged((const InstDesc<double>*)c->desc[par], (int)c->inst.size(),
+                                              c->total_blocks, kStepBlock, heun, sync, c->stream)
+              : Launch<float, true>::staged((const InstDesc<float>*)c->desc[par], (int)c->inst.size(),
+                                            c->total_blocks, kStepBlock, heun, sync, c->stream);
     } else if (c->prec == LBCAD_FP64)
       e = Launch<double, false>::step((const InstDesc<double>*)c->desc[par], (int)c->inst.size(), c->total_blocks,
                                       kStepBlock, c->stream);
@@ -465,9 +490,12 @@ int lbcad_create_batch(int32_t n, const lbcad_grid* grids, const lbcad_params* p
 
 int lbcad_set_path(lbcad_ctx* c, int32_t path) {
   if (!c) return LBCAD_E_INVALID_ARG;
-  if (path != LBCAD_PATH_FUSED && path != LBCAD_PATH_TWO_KERNEL) return fail(c, LBCAD_E_INVALID_ARG, "unknown path");
+  if (path != LBCAD_PATH_FUSED && path != LBCAD_PATH_TWO_KERNEL && path != LBCAD_PATH_STAGED)
+    return fail(c, LBCAD_E_INVALID_ARG, "unknown path");
+  if (path != LBCAD_PATH_STAGED && c->staged_only())
+    return fail(c, LBCAD_E_UNSUPPORTED, "Heun or sync contexts run on the staged path only");
   DeviceGuard dg(c->device);
-  if (path == LBCAD_PATH_TWO_KERNEL) {
+  if (path != LBCAD_PATH_FUSED) {
     int r = ensure_scratch(c);
     if (r) return r;
   }
@@ -481,6 +509,7 @@ int lbcad_set_path(lbcad_ctx* c, int32_t path) {
 
 int lbcad_autotune(lbcad_ctx* c, int32_t reps, int32_t* chosen, float* ms_per_cfg, int32_t ncfg) {
   if (!c || reps < 1) return LBCAD_E_INVALID_ARG;
+  if (c->staged_only()) return fail(c, LBCAD_E_UNSUPPORTED, "tile shapes belong to the fused path (Euler, lagged)");
   DeviceGuard dg(c->device);
   const int n = (c->prec == LBCAD_FP64) ? LaunchFused<double, false>::num_configs()
                                         : LaunchFused<float, true>::num_configs();
@@ -522,6 +551,7 @@ int lbcad_autotune(lbcad_ctx* c, int32_t reps, int32_t* chosen, float* ms_per_cf
 
 int lbcad_set_tiles(lbcad_ctx* c, int32_t cfg) {
   if (!c) return LBCAD_E_INVALID_ARG;
+  if (c->staged_only()) return fail(c, LBCAD_E_UNSUPPORTED, "tile shapes belong to the fused path (Euler, lagged)");
   DeviceGuard dg(c->device);
   const int n = (c->prec == LBCAD_FP64) ? LaunchFused<double, false>::num_configs()
                                         : LaunchFused<float, true>::num_configs();
@@ -812,6 +842,7 @@ int lbcad_adjoint(lbcad_ctx* c, int64_t nsteps, int32_t ckpt_every, double* dJ_d
                   double* dJ_dQ0, double* J) {
   if (!c) return LBCAD_E_INVALID_ARG;
   if (c->inst.size() != 1) return fail(c, LBCAD_E_UNSUPPORTED, "the adjoint runs on single-instance contexts");
+  if (c->staged_only()) return fail(c, LBCAD_E_UNSUPPORTED, "the adjoint differentiates the Euler, lagged step");
   if (nsteps < 1 || ckpt_every < 1) return fail(c, LBCAD_E_INVALID_ARG, "need nsteps >= 1 and ckpt_every >= 1");
   DeviceGuard dg(c->device);
   const int k = (int)std::min<int64_t>(ckpt_every, nsteps);

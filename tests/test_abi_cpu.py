@@ -57,12 +57,23 @@ def _create(lib, grid, **kw):
     ((8, 8, 8), dict(rho0=-1.0), L.LBCAD_E_INVALID_ARG),
     ((8, 8, 8), dict(zeta=math.nan), L.LBCAD_E_INVALID_ARG),
     ((8, 8, 8), dict(precision=7), L.LBCAD_E_INVALID_ARG),
-    ((8, 8, 8), dict(integrator=L.HEUN), L.LBCAD_E_UNSUPPORTED),
-    ((8, 8, 8), dict(coupling=L.SYNC), L.LBCAD_E_UNSUPPORTED),
+    ((8, 8, 8), dict(integrator=7), L.LBCAD_E_INVALID_ARG),
+    ((8, 8, 8), dict(coupling=5), L.LBCAD_E_INVALID_ARG),
 ])
 def test_create_rejects_bad_arguments_on_the_host(lib, grid, kw, code):
     got, msg = _create(lib, grid, **kw)
     assert got == code and msg
+
+
+def test_batch_with_mixed_integrators_is_rejected_on_the_host(lib):
+    grid = (8, 8, 8)
+    ps = (L.lbcad_params * 2)()
+    ps[0] = L._fill_params(L.default_params(grid), None, 0, None)
+    ps[1] = L._fill_params(L.default_params(grid, integrator=L.HEUN), None, 0, None)
+    gs = (L.lbcad_grid * 2)(L.lbcad_grid(*grid), L.lbcad_grid(*grid))
+    ctx = ctypes.c_void_p()
+    assert lib.lbcad_create_batch(2, gs, ps, 1, ctypes.byref(ctx)) == L.LBCAD_E_INVALID_ARG
+    assert "integrator" in lib.lbcad_last_error(None).decode()
 
 
 def test_null_arguments(lib):

@@ -436,6 +436,109 @@ def test_heun_and_sync_variants_conserve():
         assert abs(m1 - m0) < 1e-14 * 12 ** 3
 
 
+# ---------------------------------------------------------------- integrator and coupling (Sec. 3)
+
+def _uniform_H(q5, prm):
+    """H of a uniform Q (no gradients) with psi = 1, from the sympy derivative of Eq. 5."""
+    st_ = dict(q5=np.asarray(q5, float), dq5=np.zeros((5, 3)), hq5=np.zeros((5, 3, 3)), psi=np.array(1.0),
+               dpsi=np.zeros(3), hpsi=np.zeros((3, 3)))
+    H, _ = OH.analytic_H_mu(st_, prm)
+    return np.array([H[0, 0], H[0, 1], H[0, 2], H[1, 1], H[1, 2]], float)
+
+
+def _bulk_relaxation_state(prm, S, integrator, gammaQ):
+    shp = (4, 4, 4)
+    p = O.default_params(shp, integrator=integrator, gammaQ=gammaQ, zeta=0.0,
+                         **{k: prm[k] for k in ("a", "b", "kphi", "A0", "chi0", "chis", "K", "q0", "W")})
+    s = O.State(shp, p)
+    _, w = O.lattice()
+    s.f = np.ascontiguousarray(w.reshape(19, 1, 1, 1) * np.ones((19, 4, 4, 4)))
+    s.q = np.ascontiguousarray(_uniform_uniaxial(S, shp))
+    s.psi = np.ones((4, 4, 4))
+    s.u = np.zeros((3, 4, 4, 4))
+    return s
+
+
+def test_heun_step_on_uniform_relaxation():
+    """A uniform Q with psi = 1 and fluid at rest: sigma is uniform, F = 0, u stays 0 and
+    Q follows dQ/dt = Gamma_Q H(Q).  One step of the oracle must equal the Euler map
+    Q + Gamma H(Q) (integrator 0) and the Heun map Q + (Gamma H(Q) + Gamma H(Q*))/2 with
+    Q* = Q + Gamma H(Q) (integrator 1), with H from the sympy derivative of Eq. 5."""
+    prm = dict(BASE, q0=2 * np.pi / 16, W=0.02)
+    S = 0.3  # away from S_eq = 0.5 at chi = 3: H != 0
+    for gam in (0.3, 1.0):
+        q = _uniform_uniaxial(S, (4, 4, 4))[:, 0, 0, 0]
+        h1 = gam * _uniform_H(q, prm)
+        euler = q + h1
+        heun = q + 0.5 * (h1 + gam * _uniform_H(q + h1, prm))
+        for integ, ref in ((0, euler), (1, heun)):
+            s = _bulk_relaxation_state(prm, S, integ, gam).step(1)
+            got = s.q[:, 0, 0, 0]
+            assert np.abs(s.q - got.reshape(5, 1, 1, 1)).max() == 0.0  # stays uniform
+            assert np.abs(got - ref).max() < 1e-15, (integ, got - ref)
+            assert np.abs(s.u).max() < 1e-16
+        assert np.abs(heun - euler).max() > 1e-5  # the two maps are distinguishable here
+
+
+def test_heun_is_second_order_in_time():
+    """Local error of one step against the exact flow of dQ/dt = Gamma H(Q) (scipy RK45 at
+    1e-13 tolerance on the sympy H): third order in Gamma for Heun, second for Euler."""
+    from scipy.integrate import solve_ivp
+    prm = dict(BASE, q0=0.0, W=0.02)
+    S = 0.3
+    q = _uniform_uniaxial(S, (4, 4, 4))[:, 0, 0, 0]
+    errs = {0: [], 1: []}
+    gams = (0.4, 0.2, 0.1)
+    for gam in gams:
+        sol = solve_ivp(lambda t, y: gam * _uniform_H(y, prm), (0.0, 1.0), q, rtol=1e-13, atol=1e-15)
+        exact = sol.y[:, -1]
+        for integ in (0, 1):
+            got = _bulk_relaxation_state(prm, S, integ, gam).step(1).q[:, 0, 0, 0]
+            errs[integ].append(np.abs(got - exact).max())
+    for integ, order in ((0, 2), (1, 3)):
+        e = errs[integ]
+        for k in range(len(gams) - 1):
+            assert abs(np.log2(e[k] / e[k + 1]) - order) < 0.25, (integ, e)
+
+
+def test_sync_coupling_advects_with_this_steps_velocity():
+    """Ordered uniform Q (n = x, S = S_eq, q0 = 0 so H = 0), psi = 1, populations at
+    equilibrium with the shear u_x = A sin(2 pi z / L), u_prev = 0.  sigma is uniform, F = 0
+    and the LB velocity of the step is the shear itself.  Lagged coupling advects with
+    u_prev = 0: Q is unchanged.  Sync coupling uses the shear: W_xz = A sin(2 pi/L)
+    cos(2 pi z/L) (central difference of the sine) and the co-rotation of Eq. 2 for this
+    Q and W reduces by hand to S_xz = S_zx = (W_xz/2)[S0 (xi - 1) + 2 xi (1 - S0)/3], the
+    other components zero."""
+    c, w = O.lattice()
+    L, n = 16, 4
+    shp = (n, n, L)
+    xi, A = 0.7, 1e-3
+    S0 = 0.5  # S_eq at chi = 3
+    z = np.arange(L).reshape(L, 1, 1) * np.ones((L, n, n))
+    v = np.zeros((3, L, n, n))
+    v[0] = A * np.sin(2 * np.pi * z / L)
+    Q = S0 * (np.diag([1.0, 0.0, 0.0]) - np.eye(3) / 3)
+    q5 = np.array([Q[0, 0], Q[0, 1], Q[0, 2], Q[1, 1], Q[1, 2]]).reshape(5, 1, 1, 1) * np.ones((5, L, n, n))
+    out = {}
+    for coupling in (0, 1):
+        p = O.default_params(shp, coupling=coupling, q0=0.0, xi=xi, zeta=0.003)
+        s = O.State(shp, p)
+        s.f = np.ascontiguousarray(_feq(np.ones((L, n, n)), v, c, w))
+        s.q = q5.copy()
+        s.psi = np.ones((L, n, n))
+        s.u = np.zeros((3, L, n, n))
+        s.step(1)
+        np.testing.assert_allclose(s.u, v, atol=1e-17)
+        out[coupling] = s.q - q5
+    assert np.abs(out[0]).max() < 1e-16
+    Wxz = A * np.sin(2 * np.pi / L) * np.cos(2 * np.pi * z / L)
+    Sxz = 0.5 * Wxz * (S0 * (xi - 1) + 2 * xi * (1 - S0) / 3)
+    exp = np.zeros_like(q5)
+    exp[2] = Sxz
+    assert np.abs(out[1] - exp).max() < 1e-17, np.abs(out[1] - exp).max()
+    assert np.abs(Sxz).max() > 1e-6
+
+
 def _random_state(n, seed):
     c, w = O.lattice()
     st_ = OH.smooth_state((n, n, n), seed=seed)
