@@ -34,8 +34,8 @@ TILE_NAMES = ["32x8", "32x16", "64x8", "32x8-pipelined-8+8", "32x8-pipelined-6+1
               "32x6-pipelined-10+6"]
 
 
-def workload_params(L, n, prec):
-    return L.default_params((n, n, n), R=n / 4.0, p0=n / 4.0, precision=prec, zeta=0.005)
+def workload_params(L, n, prec, **kw):
+    return L.default_params((n, n, n), R=n / 4.0, p0=n / 4.0, precision=prec, zeta=0.005, **kw)
 
 
 def measured_peaks():
@@ -47,18 +47,23 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def committed_traffic():
-    """DRAM bytes per site-update of the step kernels from the committed ncu summary."""
+def committed_profile_value(key):
+    """A per-site figure ('key: value ...') from the committed ncu summary of the step."""
     p = os.path.join(ROOT, "profiles", "lbcad_step_fp32_128cube.md")
     if not os.path.exists(p):
         return None
     for line in open(p):
-        if line.startswith("traffic_bytes_per_site:"):
+        if line.startswith(key + ":"):
             try:
                 return float(line.split(":", 1)[1].split()[0])
             except ValueError:
                 return None
     return None
+
+
+def committed_traffic():
+    """DRAM bytes per site-update of the step kernels from the committed ncu summary."""
+    return committed_profile_value("traffic_bytes_per_site")
 
 
 class ClockSampler:
@@ -243,6 +248,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-staged", action="store_true", help="skip the Heun / sync staged-path leg")
     ap.add_argument("--workload", default="droplet", choices=["droplet", "batch64"],
                     help="droplet: the 128^3 benchmark line; batch64: 64 uneven droplets in one launch")
     args = ap.parse_args()
@@ -294,6 +300,18 @@ def main():
         fp64 = {"mlups": N / (ms64 * 1e-3) / 1e6, "ms_per_step": ms64, "steps": args.fp64_steps}
         s64.close()
 
+    # the staged path (Sec. 3 predictor-corrector and sync coupling) on the same workload
+    staged = None
+    if not args.no_staged:
+        staged = {}
+        for name, integ, coup, launches in (("euler_sync", L.EULER, L.SYNC, 3), ("heun_sync", L.HEUN, L.SYNC, 5)):
+            sv = L.Simulation([(n, n, n)], [workload_params(L, n, L.FP32, integrator=integ, coupling=coup)],
+                              seed=1 + rank, device=local)
+            sv.step(3)
+            msv = time_steps(sv, torch, 20)
+            staged[name] = {"mlups": N / (msv * 1e-3) / 1e6, "ms_per_step": msv, "kernels_per_step": launches}
+            sv.close()
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -330,6 +348,18 @@ def main():
                 "kernel": "k_step_fused (one launch = one whole hybrid step)", "algorithmic_bytes_per_site": 200,
                 "peak_kind": peak_kind}
 
+    # the bound the step actually meets: warp-instruction issue (one per cycle per SM
+    # sub-partition, 4 per SM, 152 SMs) at the SM clock sampled during the timed region
+    ipsite = committed_profile_value("warp_instructions_per_site")
+    csum = clk.summary()
+    roofline_issue = None
+    if ipsite and csum.get("sm_mhz"):
+        peak_i = 152 * 4 * csum["sm_mhz"] * 1e6
+        ach_i = ipsite * N / (ms * 1e-3)
+        roofline_issue = {"bound": "issue", "achieved": ach_i / 1e12, "peak": peak_i / 1e12,
+                          "unit": "T warp-instructions/s", "frac": ach_i / peak_i,
+                          "warp_instructions_per_site": ipsite}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         rate, steps, el = cpu_oracle_rate(n, budget_s=12.0)
@@ -345,9 +375,9 @@ def main():
                                        "shifted populations" if n == 128 else "droplet %d^3" % n,
                            "box": [n, n, n], "parallelism": "replicas" if world > 1 else "single",
                            "l2": "state %.0f MB per step > 129 MB L2, no flush" % (224 * N / 1e6)},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "roofline_issue": roofline_issue, "cpu_baseline": cpu, "e2e": e2e,
                 "tiles": {"chosen": TILE_NAMES[tile_cfg], "ms_per_cfg": dict(zip(TILE_NAMES, tile_ms))},
-                "gpu_launches": K, "clocks": clk.summary(), "fp64_gpu": fp64,
+                "gpu_launches": K, "clocks": csum, "fp64_gpu": fp64, "staged_fp32": staged,
                 "speedup_fp32_vs_fp64": (value / world / fp64["mlups"]) if fp64 else None,
                 "observables_finite": finite}
         print(json.dumps(line))
