@@ -47,6 +47,9 @@ typedef struct {
   double S0, noise;       // initial scalar order inside the droplet and noise amplitude
   int integrator;         // 0 = Euler, 1 = Heun predictor-corrector (Sec. 3)
   int coupling;           // 0 = advect with u(t-1), 1 = advect with u(t) of this step
+  int lattice;            // LB velocity set: 19 = D3Q19, 15 = D3Q15 (Sec. 3, Fig. 1)
+  int lb_form;            // 0 = whole stress as a body force (Guo), 1 = Eqs. 9-11: symmetric
+                          //     stress in the equilibrium, antisymmetric stress as forcing
 } orc_params;
 
 }  // extern "C"
@@ -67,6 +70,37 @@ double wgt(int i) {
   if (s == 0) return 1.0 / 3.0;
   if (s == 1) return 1.0 / 18.0;
   return 1.0 / 36.0;
+}
+
+// D3Q15 velocity set: rest, six faces, eight corners, opposite velocities adjacent.
+// Weights 2/9, 1/9, 1/72 (c_s^2 = 1/3, isotropic to fourth order like D3Q19).
+const int CV15[15][3] = {
+    {0, 0, 0},
+    {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+    {1, 1, 1}, {-1, -1, -1}, {1, 1, -1}, {-1, -1, 1}, {1, -1, 1}, {-1, 1, -1}, {-1, 1, 1}, {1, -1, -1}};
+
+double wgt15(int i) {
+  int s = CV15[i][0] * CV15[i][0] + CV15[i][1] * CV15[i][1] + CV15[i][2] * CV15[i][2];
+  if (s == 0) return 2.0 / 9.0;
+  if (s == 1) return 1.0 / 9.0;
+  return 1.0 / 72.0;
+}
+
+// The LB velocity set of a run (the finite-difference stencils always use D3Q19).
+struct LBSet {
+  int q;
+  int c[19][3];
+  double w[19];
+};
+
+LBSet lb_set(int lattice) {
+  LBSet L;
+  L.q = (lattice == 15) ? 15 : 19;
+  for (int i = 0; i < L.q; ++i) {
+    for (int a = 0; a < 3; ++a) L.c[i][a] = (L.q == 15) ? CV15[i][a] : CV[i][a];
+    L.w[i] = (L.q == 15) ? wgt15(i) : wgt(i);
+  }
+  return L;
 }
 
 struct Box {
@@ -90,7 +124,7 @@ using M3 = R[3][3];
 template <typename R>
 struct PR {
   R tau, rho0, A0, chi0, chis, K, q0, gammaQ, xi, a, b, kphi, M, W, zeta;
-  int integrator, coupling;
+  int integrator, coupling, lattice, lb_form;
 };
 
 template <typename R>
@@ -100,6 +134,8 @@ PR<R> promote(const orc_params& p) {
   r.gammaQ = p.gammaQ; r.xi = p.xi; r.a = p.a; r.b = p.b; r.kphi = p.kphi; r.M = p.M; r.W = p.W; r.zeta = p.zeta;
   r.integrator = p.integrator;
   r.coupling = p.coupling;
+  r.lattice = p.lattice;
+  r.lb_form = p.lb_form;
   return r;
 }
 
@@ -384,7 +420,7 @@ void vec_grad_at(const Box& B, const R* u, int x, int y, int z, M3<R> Wg) {
 
 template <typename R>
 struct Work {
-  std::vector<R> H, mu, sig, F, unew, fnew, rhsQ, rhsP, Qp, Pp;
+  std::vector<R> H, mu, sig, sigA, F, unew, fnew, rhsQ, rhsP, Qp, Pp;
 };
 
 // Stage 1-4 over the whole box: H (5), mu, total stress (9) per site.
@@ -440,29 +476,76 @@ void force_all(const Box& B, const R* sig9, R* F3) {
 template <typename R>
 void lb_all(const Box& B, const PR<R>& P, const R* f, const R* F3, R* fnew, R* unew) {
   long N = B.n();
+  const LBSet L = lb_set(P.lattice);
   const R tau = P.tau;
   for (int z = 0; z < B.nz; ++z)
     for (int y = 0; y < B.ny; ++y)
       for (int x = 0; x < B.nx; ++x) {
         long s = B.at(x, y, z);
         R rho = 0.0, j[3] = {0, 0, 0};
-        for (int i = 0; i < NQ; ++i) {
+        for (int i = 0; i < L.q; ++i) {
           R fi = f[i * N + s];
           rho += fi;
-          for (int a = 0; a < 3; ++a) j[a] += fi * CV[i][a];
+          for (int a = 0; a < 3; ++a) j[a] += fi * L.c[i][a];
         }
         R F[3] = {F3[0 * N + s], F3[1 * N + s], F3[2 * N + s]};
         R u[3];
         for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * F[a]) / rho;
         R u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        for (int i = 0; i < NQ; ++i) {
-          R cu = CV[i][0] * u[0] + CV[i][1] * u[1] + CV[i][2] * u[2];
-          R cF = CV[i][0] * F[0] + CV[i][1] * F[1] + CV[i][2] * F[2];
+        for (int i = 0; i < L.q; ++i) {
+          R cu = L.c[i][0] * u[0] + L.c[i][1] * u[1] + L.c[i][2] * u[2];
+          R cF = L.c[i][0] * F[0] + L.c[i][1] * F[1] + L.c[i][2] * F[2];
           R uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
-          R feq = wgt(i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * u2);
-          R Fi = (1.0 - 0.5 / tau) * wgt(i) * (3.0 * (cF - uF) + 9.0 * cu * cF);
+          R feq = L.w[i] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * u2);
+          R Fi = (1.0 - 0.5 / tau) * L.w[i] * (3.0 * (cF - uF) + 9.0 * cu * cF);
           R fstar = f[i * N + s] - (f[i * N + s] - feq) / tau + Fi;
-          long d = B.at(x + CV[i][0], y + CV[i][1], z + CV[i][2]);
+          long d = B.at(x + L.c[i][0], y + L.c[i][1], z + L.c[i][2]);
+          fnew[i * N + d] = fstar;
+        }
+        for (int a = 0; a < 3; ++a) unew[a * N + s] = u[a];
+      }
+}
+
+// Stage 6 in the form of Eqs. 9-11: the equilibrium carries the symmetric stress,
+//   f_eq_i = w_i [rho + 3 rho c.u + (9/2)(c c - I/3) : (rho u u - sigma^S)],
+// so that sum f_eq = rho, sum f_eq c = rho u and sum f_eq c c = rho/3 I + rho u u - sigma^S
+// (Eq. 9 with the lattice pressure rho c_s^2 kept); the antisymmetric stress enters
+// through F_i = 3 w_i c . FA, FA = div sigma^A, whose moments are 0, FA and 0 (Eq. 10).
+// Collision f* = f - (f - f_eq)/tau + F_i (Eq. 7), rho u = sum f c (Eq. 8), streaming (Eq. 6).
+template <typename R>
+void lb_all_stress(const Box& B, const PR<R>& P, const R* f, const R* FA3, const R* sig9, R* fnew, R* unew) {
+  long N = B.n();
+  const LBSet L = lb_set(P.lattice);
+  const R tau = P.tau;
+  for (int z = 0; z < B.nz; ++z)
+    for (int y = 0; y < B.ny; ++y)
+      for (int x = 0; x < B.nx; ++x) {
+        long s = B.at(x, y, z);
+        R rho = 0.0, j[3] = {0, 0, 0};
+        for (int i = 0; i < L.q; ++i) {
+          R fi = f[i * N + s];
+          rho += fi;
+          for (int a = 0; a < 3; ++a) j[a] += fi * L.c[i][a];
+        }
+        R u[3];
+        for (int a = 0; a < 3; ++a) u[a] = j[a] / rho;
+        // Pi = rho u u - sigma^S
+        M3<R> Pi;
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b)
+            Pi[a][b] = rho * u[a] * u[b] - 0.5 * (sig9[(3 * a + b) * N + s] + sig9[(3 * b + a) * N + s]);
+        R trPi = Pi[0][0] + Pi[1][1] + Pi[2][2];
+        R FA[3] = {FA3[0 * N + s], FA3[1 * N + s], FA3[2 * N + s]};
+        for (int i = 0; i < L.q; ++i) {
+          R cu = L.c[i][0] * u[0] + L.c[i][1] * u[1] + L.c[i][2] * u[2];
+          R cPc = 0.0;
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) cPc += L.c[i][a] * Pi[a][b] * L.c[i][b];
+          R feq = L.w[i] * (rho + 3.0 * rho * cu + 4.5 * (cPc - trPi / 3.0));
+          R cFA = L.c[i][0] * FA[0] + L.c[i][1] * FA[1] + L.c[i][2] * FA[2];
+          R Fi = 3.0 * L.w[i] * cFA;
+          R fstar = f[i * N + s] - (f[i * N + s] - feq) / tau + Fi;
+          long d = B.at(x + L.c[i][0], y + L.c[i][1], z + L.c[i][2]);
           fnew[i * N + d] = fstar;
         }
         for (int a = 0; a < 3; ++a) unew[a * N + s] = u[a];
@@ -530,10 +613,22 @@ template <typename R>
 void step_one(const Box& B, const PR<R>& P, R* f, R* q5, R* psi, R* uprev, Work<R>& w) {
   const long N = B.n();
   w.H.resize(5 * N); w.mu.resize(N); w.sig.resize(9 * N); w.F.resize(3 * N);
-  w.unew.resize(3 * N); w.fnew.resize(19 * N); w.rhsQ.resize(5 * N); w.rhsP.resize(N);
+  const int q = lb_set(P.lattice).q;
+  w.unew.resize(3 * N); w.fnew.resize(q * N); w.rhsQ.resize(5 * N); w.rhsP.resize(N);
   fields_all<R>(B, P, q5, psi, w.H.data(), w.mu.data(), w.sig.data(), nullptr, nullptr, nullptr, nullptr);
-  force_all<R>(B, w.sig.data(), w.F.data());
-  lb_all<R>(B, P, f, w.F.data(), w.fnew.data(), w.unew.data());
+  if (P.lb_form == 1) {
+    // force of the antisymmetric stress only; the symmetric part enters the equilibrium
+    w.sigA.resize(9 * N);
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        for (long k = 0; k < N; ++k)
+          w.sigA[(3 * a + b) * N + k] = 0.5 * (w.sig[(3 * a + b) * N + k] - w.sig[(3 * b + a) * N + k]);
+    force_all<R>(B, w.sigA.data(), w.F.data());
+    lb_all_stress<R>(B, P, f, w.F.data(), w.sig.data(), w.fnew.data(), w.unew.data());
+  } else {
+    force_all<R>(B, w.sig.data(), w.F.data());
+    lb_all<R>(B, P, f, w.F.data(), w.fnew.data(), w.unew.data());
+  }
   const R* uadv = (P.coupling == 1) ? w.unew.data() : uprev;
   op_rhs<R>(B, P, q5, psi, uadv, w.H.data(), w.mu.data(), w.rhsQ.data(), w.rhsP.data());
   if (P.integrator == 1) {
@@ -550,7 +645,7 @@ void step_one(const Box& B, const PR<R>& P, R* f, R* q5, R* psi, R* uprev, Work<
     for (long k = 0; k < 5 * N; ++k) q5[k] += w.rhsQ[k];
     for (long k = 0; k < N; ++k) psi[k] += w.rhsP[k];
   }
-  std::memcpy(f, w.fnew.data(), sizeof(R) * 19 * N);
+  std::memcpy(f, w.fnew.data(), sizeof(R) * q * N);
   std::memcpy(uprev, w.unew.data(), sizeof(R) * 3 * N);
 }
 
@@ -572,6 +667,15 @@ void orc_lattice(int* c57, double* w19) {
   for (int i = 0; i < NQ; ++i) {
     for (int a = 0; a < 3; ++a) c57[3 * i + a] = CV[i][a];
     w19[i] = wgt(i);
+  }
+}
+
+// The LB velocity set with q = 15 or 19 velocities (c: 3q ints, w: q doubles).
+void orc_lattice_q(int q, int* c, double* w) {
+  const LBSet L = lb_set(q);
+  for (int i = 0; i < L.q; ++i) {
+    for (int a = 0; a < 3; ++a) c[3 * i + a] = L.c[i][a];
+    w[i] = L.w[i];
   }
 }
 
@@ -609,7 +713,8 @@ void orc_init(int nx, int ny, int nz, const orc_params* P, uint64_t seed, int in
         if (r < P->R) {
           for (int c = 0; c < 5; ++c) q5[c * N + s] += P->noise * orc_noise(seed, inst, s, c);
         }
-        for (int i = 0; i < NQ; ++i) f[i * N + s] = wgt(i) * P->rho0;
+        const LBSet L = lb_set(P->lattice);
+        for (int i = 0; i < L.q; ++i) f[i * N + s] = L.w[i] * P->rho0;
         for (int a = 0; a < 3; ++a) u[a * N + s] = 0.0;
       }
 }
@@ -687,11 +792,20 @@ void orc_lb(int nx, int ny, int nz, const orc_params* P, const double* f, const 
   lb_all<double>(B, promote<double>(*P), f, F3, fnew, unew);
 }
 
+// Stage 6 in the form of Eqs. 9-11 alone: FA3 = force of the antisymmetric stress, sig9 =
+// the stress whose symmetric part enters the equilibrium.
+void orc_lb_stress(int nx, int ny, int nz, const orc_params* P, const double* f, const double* FA3,
+                   const double* sig9, double* fnew, double* unew) {
+  Box B{nx, ny, nz};
+  lb_all_stress<double>(B, promote<double>(*P), f, FA3, sig9, fnew, unew);
+}
+
 // Conserved sums and centroid moments (FP64):
 // out[0] = sum rho, out[1] = sum psi, out[2..4] = sum_i f_i c_i, out[5..7] = sum phi_c cos(2 pi x_a/L_a),
 // out[8..10] = sum phi_c sin(2 pi x_a/L_a), out[11] = sum phi_c; phi_c = (1 + psi)/2.
-void orc_observables(int nx, int ny, int nz, const double* f, const double* psi, double* out) {
+void orc_observables_q(int q, int nx, int ny, int nz, const double* f, const double* psi, double* out) {
   Box B{nx, ny, nz};
+  const LBSet V = lb_set(q);
   long N = B.n();
   for (int k = 0; k < 12; ++k) out[k] = 0.0;
   const double PI = 3.14159265358979323846;
@@ -700,10 +814,10 @@ void orc_observables(int nx, int ny, int nz, const double* f, const double* psi,
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
         long s = B.at(x, y, z);
-        for (int i = 0; i < NQ; ++i) {
+        for (int i = 0; i < V.q; ++i) {
           double fi = f[i * N + s];
           out[0] += fi;
-          for (int a = 0; a < 3; ++a) out[2 + a] += fi * CV[i][a];
+          for (int a = 0; a < 3; ++a) out[2 + a] += fi * V.c[i][a];
         }
         out[1] += psi[s];
         double pc = 0.5 * (1.0 + psi[s]);
@@ -716,6 +830,10 @@ void orc_observables(int nx, int ny, int nz, const double* f, const double* psi,
       }
 }
 
+void orc_observables(int nx, int ny, int nz, const double* f, const double* psi, double* out) {
+  orc_observables_q(19, nx, ny, nz, f, psi, out);
+}
+
 // Forward-mode tangent of nsteps steps.  (f, q5, psi, u) and their tangents (df, dq5,
 // dpsi, du) advance together; the parameters zeta and q0 carry the tangents dzeta and dq0,
 // all other parameters are fixed.  Used as an independent derivative for the adjoint.
@@ -724,8 +842,9 @@ void orc_step_tangent(int nx, int ny, int nz, const orc_params* P, double dzeta,
                       long nsteps) {
   Box B{nx, ny, nz};
   const long N = B.n();
-  std::vector<Dual> F(19 * N), Q(5 * N), S(N), U(3 * N);
-  for (long k = 0; k < 19 * N; ++k) F[k] = Dual(f[k], df[k]);
+  const long q = lb_set(P->lattice).q;
+  std::vector<Dual> F(q * N), Q(5 * N), S(N), U(3 * N);
+  for (long k = 0; k < q * N; ++k) F[k] = Dual(f[k], df[k]);
   for (long k = 0; k < 5 * N; ++k) Q[k] = Dual(q5[k], dq5[k]);
   for (long k = 0; k < N; ++k) S[k] = Dual(psi[k], dpsi[k]);
   for (long k = 0; k < 3 * N; ++k) U[k] = Dual(u[k], du[k]);
@@ -734,7 +853,7 @@ void orc_step_tangent(int nx, int ny, int nz, const orc_params* P, double dzeta,
   pr.q0.d = dq0;
   Work<Dual> w;
   for (long t = 0; t < nsteps; ++t) step_one<Dual>(B, pr, F.data(), Q.data(), S.data(), U.data(), w);
-  for (long k = 0; k < 19 * N; ++k) { f[k] = F[k].v; df[k] = F[k].d; }
+  for (long k = 0; k < q * N; ++k) { f[k] = F[k].v; df[k] = F[k].d; }
   for (long k = 0; k < 5 * N; ++k) { q5[k] = Q[k].v; dq5[k] = Q[k].d; }
   for (long k = 0; k < N; ++k) { psi[k] = S[k].v; dpsi[k] = S[k].d; }
   for (long k = 0; k < 3 * N; ++k) { u[k] = U[k].v; du[k] = U[k].d; }

@@ -29,18 +29,20 @@ class orc_params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "tau", "rho0", "A0", "chi0", "chis", "K", "q0", "gammaQ", "xi",
         "a", "b", "kphi", "M", "W", "zeta", "R", "cx", "cy", "cz", "S0", "noise")] + [
-        ("integrator", ctypes.c_int), ("coupling", ctypes.c_int)]
+        ("integrator", ctypes.c_int), ("coupling", ctypes.c_int), ("lattice", ctypes.c_int),
+        ("lb_form", ctypes.c_int)]
 
 
 def default_params(n=(32, 32, 32), R=8.0, p0=16.0, **kw) -> orc_params:
     """Droplet workload parameters (A0=1, chi_in=3, K=0.04, Gamma_Q=0.3, xi=0.7,
     a=b=0.07, M=0.1, zeta=0.005, tau=1) with the readings chi0=2.5, chis=0.25,
-    W=0.02, kphi=2a; centre at the box centre, S0=0.5, noise 1e-3."""
+    W=0.02, kphi=2a; centre at the box centre, S0=0.5, noise 1e-3; D3Q19 LB with the
+    whole stress as a body force (lattice=15 selects D3Q15, lb_form=1 the form of Eqs. 9-11)."""
     nx, ny, nz = n
     d = dict(tau=1.0, rho0=1.0, A0=1.0, chi0=2.5, chis=0.25, K=0.04,
              q0=2.0 * np.pi / p0, gammaQ=0.3, xi=0.7, a=0.07, b=0.07, kphi=0.14,
              M=0.1, W=0.02, zeta=0.005, R=R, cx=nx / 2.0, cy=ny / 2.0, cz=nz / 2.0,
-             S0=0.5, noise=1e-3, integrator=0, coupling=0)
+             S0=0.5, noise=1e-3, integrator=0, coupling=0, lattice=19, lb_form=0)
     d.update(kw)
     p = orc_params()
     for k, v in d.items():
@@ -70,6 +72,9 @@ def lib():
         P = ctypes.POINTER(orc_params)
         i = ctypes.c_int
         L.orc_lattice.argtypes = [ctypes.POINTER(ctypes.c_int), dp]
+        L.orc_lattice_q.argtypes = [i, ctypes.POINTER(ctypes.c_int), dp]
+        L.orc_lb_stress.argtypes = [i, i, i, P, dp, dp, dp, dp, dp]
+        L.orc_observables_q.argtypes = [i, i, i, i, dp, dp, dp]
         L.orc_noise.argtypes = [ctypes.c_uint64, i, ctypes.c_long, i]
         L.orc_noise.restype = ctypes.c_double
         L.orc_init.argtypes = [i, i, i, P, ctypes.c_uint64, i, dp, dp, dp, dp]
@@ -93,23 +98,24 @@ def _p(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def lattice():
-    c = np.zeros(57, dtype=np.int32)
-    w = np.zeros(19)
-    lib().orc_lattice(c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(w))
-    return c.reshape(19, 3), w
+def lattice(q=19):
+    """LB velocities (q, 3) and weights (q,) of D3Q19 (q = 19) or D3Q15 (q = 15)."""
+    c = np.zeros(3 * q, dtype=np.int32)
+    w = np.zeros(q)
+    lib().orc_lattice_q(q, c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(w))
+    return c.reshape(q, 3), w
 
 
 class State:
-    """Oracle state: f (19, nz, ny, nx) pre-collision populations, q (5, ...),
-    psi (nz, ny, nx), u (3, ...) = velocity of the previous step."""
+    """Oracle state: f (q, nz, ny, nx) pre-collision populations (q = params.lattice),
+    q (5, ...), psi (nz, ny, nx), u (3, ...) = velocity of the previous step."""
 
     def __init__(self, shape, params: orc_params, seed: int = 1, inst: int = 0):
         nx, ny, nz = shape
         self.shape = (nx, ny, nz)
         self.p = params
         g = (nz, ny, nx)
-        self.f = np.zeros((19,) + g)
+        self.f = np.zeros((params.lattice,) + g)
         self.q = np.zeros((5,) + g)
         self.psi = np.zeros(g)
         self.u = np.zeros((3,) + g)
@@ -207,8 +213,20 @@ def lb(f, F, params: orc_params):
 def observables(f, psi):
     nz, ny, nx = psi.shape
     out = np.zeros(12)
-    lib().orc_observables(nx, ny, nz, _p(np.ascontiguousarray(f)), _p(np.ascontiguousarray(psi)), _p(out))
+    lib().orc_observables_q(f.shape[0], nx, ny, nz, _p(np.ascontiguousarray(f)), _p(np.ascontiguousarray(psi)),
+                            _p(out))
     return out
+
+
+def lb_stress(f, FA, sig9, params: orc_params):
+    """Collision and streaming in the form of Eqs. 9-11 with the force FA of the
+    antisymmetric stress and the stress sig9 whose symmetric part enters the equilibrium."""
+    nz, ny, nx = f.shape[1:]
+    fn = np.zeros_like(f)
+    un = np.zeros((3, nz, ny, nx))
+    c = np.ascontiguousarray
+    lib().orc_lb_stress(nx, ny, nz, ctypes.byref(params), _p(c(f)), _p(c(FA)), _p(c(sig9)), _p(fn), _p(un))
+    return fn, un
 
 
 def noise(seed, inst, site, comp):

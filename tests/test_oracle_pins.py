@@ -83,7 +83,7 @@ def test_stencils_exact_on_quadratics():
 def _feq(rho, v, c, w):
     cu = np.einsum("ia,a...->i...", c, v)
     v2 = (v * v).sum(0)
-    return w.reshape((19,) + (1,) * rho.ndim) * rho * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * v2)
+    return w.reshape((len(w),) + (1,) * rho.ndim) * rho * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * v2)
 
 
 def test_lb_conservation_unforced():
@@ -407,7 +407,7 @@ def _droplet_state(n=16, R=5.0, **kw):
 
 def _sums(s):
     import math
-    c, _ = O.lattice()
+    c, _ = O.lattice(s.f.shape[0])
     mom = [math.fsum(np.tensordot(c[:, a].astype(float), s.f, axes=(0, 0)).ravel()) for a in range(3)]
     return math.fsum(s.f.ravel()), math.fsum(s.psi.ravel()), np.array(mom)
 
@@ -426,14 +426,115 @@ def test_full_step_conserves_mass_psi_momentum():
     assert np.abs(s.u).max() > 1e-6  # the droplet does drive a flow
 
 
-def test_heun_and_sync_variants_conserve():
-    for kw in (dict(integrator=1), dict(coupling=1)):
+def test_heun_sync_and_lb_variants_conserve():
+    for kw in (dict(integrator=1), dict(coupling=1), dict(lb_form=1), dict(lattice=15),
+               dict(lattice=15, lb_form=1, integrator=1, coupling=1)):
         s = _droplet_state(n=12, R=4.0, **kw)
         m0, p0_, _ = _sums(s)
         s.step(5)
         m1, p1, _ = _sums(s)
         assert abs(p1 - p0_) < 1e-14 * 12 ** 3
         assert abs(m1 - m0) < 1e-14 * 12 ** 3
+
+
+# ---------------------------------------------------------------- D3Q15 and the stress-in-equilibrium form (Eqs. 9-11)
+
+@pytest.mark.parametrize("q", [15, 19])
+def test_velocity_sets_are_isotropic(q):
+    """D3Q15 (Sec. 3, Fig. 1: rest, 6 faces, 8 corners; weights 2/9, 1/9, 1/72) and D3Q19
+    carry the moment conditions that make BGK recover Navier-Stokes: sum w = 1, odd moments
+    zero, sum w c c = I/3, sum w c c c c = (1/9)(dd + dd + dd).  Opposite velocities sit in
+    adjacent slots."""
+    c, w = O.lattice(q)
+    cf = c.astype(float)
+    assert len({tuple(v) for v in c}) == q and (c[0] == 0).all()
+    assert abs(w.sum() - 1) < 1e-15
+    np.testing.assert_allclose(np.einsum("i,ia->a", w, cf), 0, atol=1e-16)
+    np.testing.assert_allclose(np.einsum("i,ia,ib->ab", w, cf, cf), np.eye(3) / 3, atol=1e-16)
+    np.testing.assert_allclose(np.einsum("i,ia,ib,ic->abc", w, cf, cf, cf), 0, atol=1e-16)
+    d = np.eye(3)
+    iso = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d) + np.einsum("ad,bc->abcd", d, d)) / 9
+    np.testing.assert_allclose(np.einsum("i,ia,ib,ic,id->abcd", w, cf, cf, cf, cf), iso, atol=1e-16)
+    for i in range(1, q, 2):
+        assert (c[i] == -c[i + 1]).all()
+
+
+def test_d3q15_shear_wave_decay_matches_viscosity():
+    """The D3Q15 BGK scheme has the same viscosity nu = (tau - 1/2)/3 as D3Q19."""
+    c, w = O.lattice(15)
+    L = 32
+    for tau in (1.0, 0.7):
+        p = O.default_params((4, 4, L), tau=tau, lattice=15)
+        z = np.arange(L).reshape(L, 1, 1) * np.ones((L, 4, 4))
+        v = np.zeros((3, L, 4, 4))
+        v[0] = 1e-4 * np.sin(2 * np.pi * z / L)
+        f = _feq(np.ones((L, 4, 4)), v, c, w)
+        F = np.zeros((3, L, 4, 4))
+        amps = []
+        for t in range(201):
+            f, un = O.lb(f, F, p)
+            amps.append(2 * np.mean(un[0] * np.sin(2 * np.pi * z / L)))
+        rate = -np.polyfit(np.arange(20, 201), np.log(np.array(amps[20:])), 1)[0]
+        assert abs(rate / ((tau - 0.5) / 3 * (2 * np.pi / L) ** 2) - 1) < 0.01
+
+
+@pytest.mark.parametrize("q", [15, 19])
+@pytest.mark.parametrize("tau", [1.0, 0.7])
+def test_stress_form_moments(q, tau):
+    """Eqs. 8-10 for the form with the symmetric stress in the equilibrium.  For a uniform
+    state with arbitrary populations f, stress sigma and antisymmetric force FA, one collision
+    (streaming a uniform state changes nothing) gives sum f* = rho, sum f* c = rho u + FA with
+    rho u = sum f c, and sum f* c c = P_f - (P_f - (rho/3 I + rho u u - sigma^S))/tau with
+    P_f = sum f c c: the equilibrium moment of Eq. 9 with the lattice pressure rho c_s^2 and
+    forcing moments 0, FA, 0 (Eq. 10)."""
+    c, w = O.lattice(q)
+    cf = c.astype(float)
+    rng = np.random.default_rng(q + int(10 * tau))
+    shp = (4, 4, 4)
+    f0 = w * (1 + 0.1 * rng.standard_normal(q))
+    sig = 1e-2 * rng.standard_normal(9)
+    FA = 1e-3 * rng.standard_normal(3)
+    one = np.ones((4, 4, 4))
+    p = O.default_params(shp, tau=tau, lattice=q, lb_form=1)
+    fn, un = O.lb_stress(f0.reshape(q, 1, 1, 1) * one, FA.reshape(3, 1, 1, 1) * one,
+                         sig.reshape(9, 1, 1, 1) * one, p)
+    assert np.abs(fn - fn[:, :1, :1, :1]).max() < 1e-17
+    g = fn[:, 0, 0, 0]
+    rho, j = f0.sum(), cf.T @ f0
+    u = j / rho
+    S = sig.reshape(3, 3)
+    Peq = rho / 3 * np.eye(3) + rho * np.outer(u, u) - 0.5 * (S + S.T)
+    Pf = np.einsum("i,ia,ib->ab", f0, cf, cf)
+    assert abs(g.sum() - rho) < 1e-15
+    np.testing.assert_allclose(cf.T @ g, j + FA, atol=1e-16)
+    np.testing.assert_allclose(un[:, 0, 0, 0], u, atol=1e-16)
+    np.testing.assert_allclose(np.einsum("i,ia,ib->ab", g, cf, cf), Pf - (Pf - Peq) / tau, atol=2e-16)
+
+
+@pytest.mark.parametrize("q", [15, 19])
+def test_lb_forms_agree_without_stress(q):
+    """With Q = 0, psi = 0 and xi = 0 the stress vanishes (mu = 0, f = 0, H = 0) and no order
+    is generated by the shear: both LB forms reduce to the same unforced BGK step, which the
+    LB stage alone reproduces."""
+    c, w = O.lattice(q)
+    L = 16
+    shp = (4, 4, L)
+    z = np.arange(L).reshape(L, 1, 1) * np.ones((L, 4, 4))
+    v = np.zeros((3, L, 4, 4))
+    v[0] = 1e-3 * np.sin(2 * np.pi * z / L)
+    f0 = _feq(np.ones((L, 4, 4)), v, c, w)
+    out = []
+    for form in (0, 1):
+        p = O.default_params(shp, lattice=q, lb_form=form, xi=0.0)
+        s = O.State(shp, p)
+        s.f, s.q, s.psi, s.u = f0.copy(), np.zeros((5, L, 4, 4)), np.zeros((L, 4, 4)), np.zeros((3, L, 4, 4))
+        s.step(5)
+        out.append(s.f.copy())
+    ref = f0.copy()
+    for _ in range(5):
+        ref, _ = O.lb(ref, np.zeros((3, L, 4, 4)), O.default_params(shp, lattice=q))
+    np.testing.assert_allclose(out[0], ref, atol=1e-16)
+    np.testing.assert_allclose(out[1], ref, atol=1e-16)
 
 
 # ---------------------------------------------------------------- integrator and coupling (Sec. 3)
@@ -579,14 +680,16 @@ def test_cubic_symmetry_equivariance(P, name):
         np.testing.assert_allclose(x2, x1, atol=2e-13)
 
 
-def test_cholesteric_helix_is_stationary():
+@pytest.mark.parametrize("lat,form", [(19, 0), (19, 1), (15, 0), (15, 1)])
+def test_cholesteric_helix_is_stationary(lat, form):
     """A uniform helix (psi = 1, Q period pi/q0 commensurate with the box) drives no flow
     with or without activity: rotation by pi about z maps it to itself, so sigma_xz =
-    sigma_yz = 0, and screw symmetry makes sigma_zz uniform.  Its phase does not drift."""
+    sigma_yz = 0, and screw symmetry makes sigma_zz and sigma_xx + sigma_yy uniform.  Its
+    phase does not drift.  This holds for both LB velocity sets and both LB forms."""
     nz = 16
     shp = (4, 4, nz)
     for zeta in (0.0, 0.005):
-        p = O.default_params(shp, p0=16.0, zeta=zeta, R=1e9)
+        p = O.default_params(shp, p0=16.0, zeta=zeta, R=1e9, lattice=lat, lb_form=form)
         s = O.State(shp, p)
         s.psi[:] = 1.0
         z = np.arange(nz).reshape(nz, 1, 1)
