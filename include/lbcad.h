@@ -18,11 +18,12 @@
  *
  * Field layout.  Every field is row-major [component][z][y][x] (x fastest) with
  * n = nx*ny*nz sites per component.  Field masks select, in this order:
- *   LBCAD_FIELD_G   19 components: pre-collision populations f_i at the current time,
- *                   unshifted, in the D3Q19 order returned by lbcad_lattice();
+ *   LBCAD_FIELD_G   19 components (15 for LBCAD_D3Q15): pre-collision populations f_i at
+ *                   the current time, unshifted, in the order of lbcad_velocity_set();
  *   LBCAD_FIELD_RHO  1 component : rho = sum_i f_i;
  *   LBCAD_FIELD_U    3 components: the fluid velocity u computed in the last step
- *                   ((sum_i f_i c_i + F/2)/rho of the previous time level; 0 at t = 0);
+ *                   ((sum_i f_i c_i + F/2)/rho of the previous time level, sum_i f_i c_i/rho
+ *                   with LBCAD_LB_STRESS_EQ; 0 at t = 0);
  *   LBCAD_FIELD_Q    5 components: Q_xx, Q_xy, Q_xz, Q_yy, Q_yz (Q_zz = -Q_xx - Q_yy);
  *   LBCAD_FIELD_PSI  1 component : psi.
  * The exchange type is always double, whatever the compute precision.
@@ -53,6 +54,14 @@ extern "C" {
 #define LBCAD_HEUN 1   /* predictor-corrector of Sec. 3 (Heun, velocity held fixed)       */
 #define LBCAD_LAGGED 0 /* Q and psi advected with u of the previous step                  */
 #define LBCAD_SYNC 1   /* advected with u of this step                                    */
+/* Velocity set of the LB populations (the finite-difference stencils are D3Q19 in both). */
+#define LBCAD_D3Q19 0  /* 19 velocities: rest, 6 faces, 12 edges                          */
+#define LBCAD_D3Q15 1  /* 15 velocities: rest, 6 faces, 8 corners (Sec. 3, Fig. 1)          */
+/* Where the stress enters the LB step. */
+#define LBCAD_LB_BODY_FORCE 0 /* the whole stress as the force F = div sigma, BGK + Guo      */
+#define LBCAD_LB_STRESS_EQ 1  /* Eqs. 9-11: f_eq carries the symmetric stress,
+                               * sum f_eq c c = rho/3 I + rho u u - sigma^S; the antisymmetric
+                               * stress enters as F_i = 3 w_i c . div sigma^A; rho u = sum f c  */
 
 #define LBCAD_FIELD_G 1u
 #define LBCAD_FIELD_RHO 2u
@@ -92,6 +101,8 @@ typedef struct {
   int32_t precision;  /* LBCAD_FP32 or LBCAD_FP64                                     */
   int32_t integrator; /* LBCAD_EULER or LBCAD_HEUN; one value for all instances        */
   int32_t coupling;   /* LBCAD_LAGGED or LBCAD_SYNC; one value for all instances       */
+  int32_t lattice;    /* LBCAD_D3Q19 or LBCAD_D3Q15; one value for all instances        */
+  int32_t lb_form;    /* LBCAD_LB_BODY_FORCE or LBCAD_LB_STRESS_EQ; one for all         */
   int32_t device;     /* CUDA device ordinal; -1 = the current device                 */
   void* stream;       /* cudaStream_t for all work; NULL = a private non-blocking stream */
   lbcad_alloc_fn alloc; /* NULL = cudaMalloc                                          */
@@ -113,6 +124,11 @@ typedef struct lbcad_ctx lbcad_ctx;
 
 /* The D3Q19 velocity order used by LBCAD_FIELD_G: c[3*i + a], weights w[i]. */
 int lbcad_lattice(int32_t* c57, double* w19);
+
+/* The velocity set `lattice` (LBCAD_D3Q19 or LBCAD_D3Q15) in the order of LBCAD_FIELD_G:
+ * c[3*i + a] (room for 57 ints) and w[i] (room for 19 doubles).  Returns the number of
+ * velocities (19 or 15), or LBCAD_E_INVALID_ARG. */
+int lbcad_velocity_set(int32_t lattice, int32_t* c, double* w);
 
 /* Create one instance: validates params, allocates its device state (through
  * params->alloc when given), builds the initial state on the host in FP64 and copies it
@@ -147,11 +163,11 @@ int lbcad_step(lbcad_ctx* c, int64_t n);
 #define LBCAD_PATH_TWO_KERNEL 1
 /* LBCAD_PATH_STAGED: per-site kernels in the order fields -> LB (force, pull, collision;
  * writes u of this step) -> order-parameter update, and for LBCAD_HEUN a second fields
- * pass at the predicted Q, psi and the corrector (Sec. 3).  The only path for LBCAD_HEUN
- * or LBCAD_SYNC, selected at create; Euler/lagged contexts may select it as a third
- * cross-check (same per-site arithmetic as the other two).  Scratch: 15 values per site,
- * 27 with LBCAD_HEUN.  Fused/two-kernel paths, tile shapes, autotune and the adjoint return
- * LBCAD_E_UNSUPPORTED on Heun or sync contexts. */
+ * pass at the predicted Q, psi and the corrector (Sec. 3).  The only path for LBCAD_HEUN,
+ * LBCAD_SYNC, LBCAD_D3Q15 or LBCAD_LB_STRESS_EQ, selected at create; default contexts
+ * may select it as a third cross-check (same per-site arithmetic as the other two).
+ * Scratch: 15 values per site, 27 with LBCAD_HEUN.  Fused/two-kernel paths, tile shapes,
+ * autotune and the adjoint return LBCAD_E_UNSUPPORTED on those contexts. */
 #define LBCAD_PATH_STAGED 2
 int lbcad_set_path(lbcad_ctx* c, int32_t path);
 

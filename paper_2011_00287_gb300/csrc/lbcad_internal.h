@@ -24,6 +24,30 @@ __host__ __device__ constexpr double lat_w(int i) {
   return lat_c2(i) == 0 ? 1.0 / 3.0 : lat_c2(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0;
 }
 
+// D3Q15 velocities of the LB populations (Sec. 3, Fig. 1): rest, six faces (as in D3Q19),
+// eight corners; opposite velocities in adjacent slots.  Weights 2/9, 1/9, 1/72.
+__host__ __device__ constexpr int lat15_c(int i, int a) {
+  return i == 0 ? 0
+       : i <= 6 ? lat_c(i, a)
+       : a == 0 ? ((i == 7 || i == 9 || i == 11 || i == 14) ? 1 : -1)
+       : a == 1 ? ((i == 7 || i == 9 || i == 12 || i == 13) ? 1 : -1)
+                : ((i == 7 || i == 10 || i == 11 || i == 13) ? 1 : -1);
+}
+__host__ __device__ constexpr double lat15_w(int i) { return i == 0 ? 2.0 / 9.0 : i <= 6 ? 1.0 / 9.0 : 1.0 / 72.0; }
+
+// Velocity sets of the populations as template arguments (the finite-difference stencils
+// use D3Q19 in both cases).
+struct VelD3Q19 {
+  static constexpr int Q = 19;
+  __host__ __device__ static constexpr int c(int i, int a) { return lat_c(i, a); }
+  __host__ __device__ static constexpr double w(int i) { return lat_w(i); }
+};
+struct VelD3Q15 {
+  static constexpr int Q = 15;
+  __host__ __device__ static constexpr int c(int i, int a) { return lat15_c(i, a); }
+  __host__ __device__ static constexpr double w(int i) { return lat15_w(i); }
+};
+
 // Per-instance coefficients in the compute type.
 template <typename T>
 struct Coef {
@@ -34,7 +58,8 @@ struct Coef {
 // One instance of a launch: lattice, state buffers of this step parity, scratch.
 template <typename T>
 struct InstDesc {
-  int nx, ny, nz, pad;
+  int nx, ny, nz;
+  int vel;         // velocity set of the populations: 0 = D3Q19, 1 = D3Q15
   long long N;
   long long blk0;  // first block of this instance in per-site launches
   long long nblk;  // number of blocks of this instance
@@ -62,8 +87,10 @@ struct Launch {
   // Staged step: fields -> LB -> order-parameter update (Euler), or fields -> LB ->
   // predictor -> fields at the predicted state -> corrector (Heun).  sync advects with the
   // velocity of this step instead of the previous one.
+  // vel: 0 = D3Q19, 1 = D3Q15 populations; form: 0 = whole stress as a body force (Guo),
+  // 1 = symmetric stress in the equilibrium, antisymmetric stress as forcing (Eqs. 9-11).
   static cudaError_t staged(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, bool heun,
-                            bool sync, cudaStream_t s);
+                            bool sync, int vel, int form, cudaStream_t s);
   static cudaError_t get_fields(const InstDesc<T>& I, uint32_t mask, double* dst, cudaStream_t s);
   static cudaError_t set_fields(const InstDesc<T>& I, uint32_t mask, const double* src, T* g_target,
                                 T* q_target, T* psi_target, T* u_target, cudaStream_t s);

@@ -448,18 +448,18 @@ __device__ __forceinline__ void op_update(const Coef<T>& c, T lapmu, const T Wg[
 // a5 at one site: moments of the pulled populations g and the force F, then BGK + Guo
 // collision (Eqs. 6-8); g is overwritten with the post-collision values, u = velocity.
 // The equilibrium and forcing terms of opposite velocities c and -c share their even part.
-template <typename T, bool SHIFT>
-__device__ __forceinline__ void lb_collide(const Coef<T>& c, const T F[3], T g[19], T u[3]) {
+template <typename T, bool SHIFT, class V = VelD3Q19>
+__device__ __forceinline__ void lb_collide(const Coef<T>& c, const T F[3], T g[V::Q], T u[3]) {
   // moments from opposite pairs
   T m0 = g[0];
   T j[3] = {T(0), T(0), T(0)};
 #pragma unroll
-  for (int i = 1; i < 19; i += 2) {
+  for (int i = 1; i < V::Q; i += 2) {
     m0 += g[i] + g[i + 1];
     const T dg = g[i] - g[i + 1];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-      if (lat_c(i, a)) j[a] += lat_c(i, a) > 0 ? dg : -dg;
+      if (V::c(i, a)) j[a] += V::c(i, a) > 0 ? dg : -dg;
   }
   const T rho = SHIFT ? (c.rho0 + m0) : m0;
   const T rinv = T(1) / rho;
@@ -474,16 +474,16 @@ __device__ __forceinline__ void lb_collide(const Coef<T>& c, const T F[3], T g[1
   const T r3 = T(3) * rho;
   const T om = c.tau_inv;
   {
-    const T w = T(lat_w(0));
+    const T w = T(V::w(0));
     const T geq = w * base;
     const T Fi = -T(3) * c.guo * w * uF;
     g[0] = g[0] - (g[0] - geq) * om + Fi;
   }
 #pragma unroll
-  for (int i = 1; i < 19; i += 2) {
-    const T w = T(lat_w(i));
-    const T cu = T(lat_c(i, 0)) * u[0] + T(lat_c(i, 1)) * u[1] + T(lat_c(i, 2)) * u[2];
-    const T cF = T(lat_c(i, 0)) * F[0] + T(lat_c(i, 1)) * F[1] + T(lat_c(i, 2)) * F[2];
+  for (int i = 1; i < V::Q; i += 2) {
+    const T w = T(V::w(i));
+    const T cu = T(V::c(i, 0)) * u[0] + T(V::c(i, 1)) * u[1] + T(V::c(i, 2)) * u[2];
+    const T cF = T(V::c(i, 0)) * F[0] + T(V::c(i, 1)) * F[1] + T(V::c(i, 2)) * F[2];
     const T Aeq = w * (base + r45 * cu * cu);
     const T Beq = w * r3 * cu;
     const T gw = c.guo * w;
@@ -492,6 +492,59 @@ __device__ __forceinline__ void lb_collide(const Coef<T>& c, const T F[3], T g[1
     const T gp = g[i], gm = g[i + 1];
     g[i] = gp - (gp - (Aeq + Beq)) * om + (Cf + Ef);
     g[i + 1] = gm - (gm - (Aeq - Beq)) * om + (Cf - Ef);
+  }
+}
+
+// a5 in the form of Eqs. 9-11 at one site: the equilibrium carries the symmetric stress,
+//   f_eq_i = w_i [rho + 3 rho c.u + (9/2)(c c - I/3) : (rho u u - sigma^S)],
+// the antisymmetric stress enters as F_i = 3 w_i c . FA with FA = div sigma^A (moments 0, FA,
+// 0: Eq. 10), rho u = sum f c (Eq. 8), f* = f - (f - f_eq)/tau + F_i (Eq. 7).  sig is the full
+// stress at the site (9, row-major).  Opposite velocities share the even part of f_eq.
+template <typename T, bool SHIFT, class V>
+__device__ __forceinline__ void lb_collide_stress(const Coef<T>& c, const T FA[3], const T sig[9], T g[V::Q],
+                                                  T u[3]) {
+  T m0 = g[0];
+  T j[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int i = 1; i < V::Q; i += 2) {
+    m0 += g[i] + g[i + 1];
+    const T dg = g[i] - g[i + 1];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (V::c(i, a)) j[a] += V::c(i, a) > 0 ? dg : -dg;
+  }
+  const T rho = SHIFT ? (c.rho0 + m0) : m0;
+  const T rinv = T(1) / rho;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u[a] = j[a] * rinv;
+  // Pi = rho u u - sigma^S (symmetric: xx, yy, zz, xy, xz, yz)
+  const T Pxx = rho * u[0] * u[0] - sig[0], Pyy = rho * u[1] * u[1] - sig[4], Pzz = rho * u[2] * u[2] - sig[8];
+  const T Pxy = rho * u[0] * u[1] - T(0.5) * (sig[1] + sig[3]);
+  const T Pxz = rho * u[0] * u[2] - T(0.5) * (sig[2] + sig[6]);
+  const T Pyz = rho * u[1] * u[2] - T(0.5) * (sig[5] + sig[7]);
+  const T tr3 = (Pxx + Pyy + Pzz) * T(1.0 / 3.0);
+  // even part: w (rho + 4.5 (c.Pi.c - tr Pi/3)), minus w rho0 when shifted
+  const T base = SHIFT ? m0 : rho;
+  const T om = c.tau_inv;
+  {
+    const T w = T(V::w(0));
+    const T geq = w * (base - T(4.5) * tr3);
+    g[0] = g[0] - (g[0] - geq) * om;
+  }
+#pragma unroll
+  for (int i = 1; i < V::Q; i += 2) {
+    const T w = T(V::w(i));
+    const int cx = V::c(i, 0), cy = V::c(i, 1), cz = V::c(i, 2);
+    const T cPc = T(cx * cx) * Pxx + T(cy * cy) * Pyy + T(cz * cz) * Pzz +
+                  T(2 * cx * cy) * Pxy + T(2 * cx * cz) * Pxz + T(2 * cy * cz) * Pyz;
+    const T cu = T(cx) * u[0] + T(cy) * u[1] + T(cz) * u[2];
+    const T cF = T(cx) * FA[0] + T(cy) * FA[1] + T(cz) * FA[2];
+    const T Aeq = w * (base + T(4.5) * (cPc - tr3));
+    const T Beq = w * T(3) * rho * cu;
+    const T Ef = T(3) * w * cF;
+    const T gp = g[i], gm = g[i + 1];
+    g[i] = gp - (gp - (Aeq + Beq)) * om + Ef;
+    g[i + 1] = gm - (gm - (Aeq - Beq)) * om - Ef;
   }
 }
 
@@ -565,9 +618,24 @@ __global__ void __launch_bounds__(kStepBlock) k_fields(const InstDesc<T>* __rest
 }
 
 // ---------------------------------------------------------------- staged path
-// k_lb: F = div sigma from the scratch, pull, moments and collision (a3, a5):
-// g_out, u_out = velocity of this step.
-template <typename T, bool SHIFT>
+// The antisymmetric part of the stress scratch, for the force of the form of Eqs. 9-11.
+template <typename T>
+struct AntiSigAcc {
+  const T* sg;
+  long long N;
+  Nbr nb;
+  __device__ __forceinline__ T sig(int k, int cx, int cy, int cz) const {
+    const int a = k / 3, b = k - 3 * a;
+    if (a == b) return T(0);
+    const long long o = nb.off(cx, cy, cz);
+    return T(0.5) * (ld(sg + k * N + o) - ld(sg + (3 * b + a) * N + o));
+  }
+};
+
+// k_lb: the force from the stress scratch, pull, moments and collision (a3, a5):
+// g_out, u_out = velocity of this step.  FORM 0: F = div sigma, BGK + Guo (Eqs. 6-8).
+// FORM 1: FA = div sigma^A and the equilibrium with sigma^S (Eqs. 9-11).
+template <typename T, bool SHIFT, class V, int FORM>
 __global__ void __launch_bounds__(kStepBlock) k_lb(const InstDesc<T>* __restrict__ D, int ninst) {
   const int ii = find_inst(D, ninst, (long long)blockIdx.x);
   const InstDesc<T>& I = D[ii];
@@ -579,19 +647,32 @@ __global__ void __launch_bounds__(kStepBlock) k_lb(const InstDesc<T>* __restrict
   const long long t = s / nx;
   const int y = (int)(t % ny);
   const int z = (int)(t / ny);
-  GlobalAcc<T> acc;
-  acc.sg = I.sig;
-  acc.N = N;
-  acc.nb = make_nbr(x, y, z, nx, ny, nz);
+  const Nbr nb = make_nbr(x, y, z, nx, ny, nz);
   T F[3];
-  gather_force<T>(acc, F);
-  T g[19];
+  if (FORM == 0) {
+    GlobalAcc<T> acc;
+    acc.sg = I.sig;
+    acc.N = N;
+    acc.nb = nb;
+    gather_force<T>(acc, F);
+  } else {
+    AntiSigAcc<T> acc{I.sig, N, nb};
+    gather_force<T>(acc, F);
+  }
+  T g[V::Q];
 #pragma unroll
-  for (int i = 0; i < 19; ++i) g[i] = ld(I.g_in + i * N + acc.nb.off(-lat_c(i, 0), -lat_c(i, 1), -lat_c(i, 2)));
+  for (int i = 0; i < V::Q; ++i) g[i] = ld(I.g_in + i * N + nb.off(-V::c(i, 0), -V::c(i, 1), -V::c(i, 2)));
   T u[3];
-  lb_collide<T, SHIFT>(I.c, F, g, u);
+  if (FORM == 0) {
+    lb_collide<T, SHIFT, V>(I.c, F, g, u);
+  } else {
+    T sg[9];
 #pragma unroll
-  for (int i = 0; i < 19; ++i) I.g_out[i * N + s] = g[i];
+    for (int k = 0; k < 9; ++k) sg[k] = I.sig[k * N + s];
+    lb_collide_stress<T, SHIFT, V>(I.c, F, sg, g, u);
+  }
+#pragma unroll
+  for (int i = 0; i < V::Q; ++i) I.g_out[i * N + s] = g[i];
 #pragma unroll
   for (int a = 0; a < 3; ++a) I.u_out[a * N + s] = u[a];
 }
@@ -692,7 +773,7 @@ __global__ void __launch_bounds__(kStepBlock) k_update(const InstDesc<T>* __rest
 // ---------------------------------------------------------------- field exchange
 // dst components, in mask order: G(19) RHO(1) U(3) Q(5) PSI(1); offsets given per group
 // (-1 = not selected).
-template <typename T, bool SHIFT>
+template <typename T, bool SHIFT, class V>
 __global__ void k_get_fields(InstDesc<T> I, long long oG, long long oR, long long oU, long long oQ,
                              long long oP, double* __restrict__ dst) {
   const long long N = I.N;
@@ -706,10 +787,10 @@ __global__ void k_get_fields(InstDesc<T> I, long long oG, long long oR, long lon
       const Nbr nb = make_nbr(x, y, z, nx, ny, nz);
       double rho = 0.0;
 #pragma unroll
-      for (int i = 0; i < 19; ++i) {
-        const long long src = nb.off(-lat_c(i, 0), -lat_c(i, 1), -lat_c(i, 2));
+      for (int i = 0; i < V::Q; ++i) {
+        const long long src = nb.off(-V::c(i, 0), -V::c(i, 1), -V::c(i, 2));
         double fi = (double)I.g_in[i * N + src];
-        if (SHIFT) fi += lat_w(i) * (double)I.c.rho0;
+        if (SHIFT) fi += V::w(i) * (double)I.c.rho0;
         rho += fi;
         if (oG >= 0) dst[oG + i * N + s] = fi;
       }
@@ -725,7 +806,7 @@ __global__ void k_get_fields(InstDesc<T> I, long long oG, long long oR, long lon
 
 // Writes pre-collision populations f_i(x) as the stored post-collision array of the
 // previous step: stored_i(x - c_i) = f_i(x) (- w_i rho0 when SHIFT).
-template <typename T, bool SHIFT>
+template <typename T, bool SHIFT, class V>
 __global__ void k_set_fields(InstDesc<T> I, long long oG, long long oU, long long oQ, long long oP,
                              const double* __restrict__ src, T* g_t, T* q_t, T* p_t, T* u_t) {
   const long long N = I.N;
@@ -738,10 +819,10 @@ __global__ void k_set_fields(InstDesc<T> I, long long oG, long long oU, long lon
     if (oG >= 0) {
       const Nbr nb = make_nbr(x, y, z, nx, ny, nz);
 #pragma unroll
-      for (int i = 0; i < 19; ++i) {
-        const long long d = nb.off(-lat_c(i, 0), -lat_c(i, 1), -lat_c(i, 2));
+      for (int i = 0; i < V::Q; ++i) {
+        const long long d = nb.off(-V::c(i, 0), -V::c(i, 1), -V::c(i, 2));
         double fi = src[oG + i * N + s];
-        if (SHIFT) fi -= lat_w(i) * (double)I.c.rho0;
+        if (SHIFT) fi -= V::w(i) * (double)I.c.rho0;
         g_t[i * N + d] = (T)fi;
       }
     }
@@ -756,7 +837,7 @@ __global__ void k_set_fields(InstDesc<T> I, long long oG, long long oU, long lon
 // ---------------------------------------------------------------- FP64 reductions
 // 12 sums per instance (see lbcad_obs).  Fixed-order block reduction with warp shuffles
 // into partial[block][12]; k_obs_final sums the partials in block order.
-template <typename T, bool SHIFT>
+template <typename T, bool SHIFT, class V>
 __global__ void __launch_bounds__(kObsBlock) k_obs_partial(InstDesc<T> I, double* __restrict__ partial) {
   double acc[12];
 #pragma unroll
@@ -771,14 +852,14 @@ __global__ void __launch_bounds__(kObsBlock) k_obs_partial(InstDesc<T> I, double
     const int z = (int)(t / ny);
     const Nbr nb = make_nbr(x, y, z, nx, ny, nz);
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
-      const long long src = nb.off(-lat_c(i, 0), -lat_c(i, 1), -lat_c(i, 2));
+    for (int i = 0; i < V::Q; ++i) {
+      const long long src = nb.off(-V::c(i, 0), -V::c(i, 1), -V::c(i, 2));
       double fi = (double)I.g_in[i * N + src];
-      if (SHIFT) fi += lat_w(i) * (double)I.c.rho0;
+      if (SHIFT) fi += V::w(i) * (double)I.c.rho0;
       acc[0] += fi;
-      if (lat_c(i, 0)) acc[2] += lat_c(i, 0) * fi;
-      if (lat_c(i, 1)) acc[3] += lat_c(i, 1) * fi;
-      if (lat_c(i, 2)) acc[4] += lat_c(i, 2) * fi;
+      if (V::c(i, 0)) acc[2] += V::c(i, 0) * fi;
+      if (V::c(i, 1)) acc[3] += V::c(i, 1) * fi;
+      if (V::c(i, 2)) acc[4] += V::c(i, 2) * fi;
     }
     const double p = (double)I.psi_in[s];
     acc[1] += p;
@@ -839,10 +920,13 @@ cudaError_t Launch<T, SHIFT>::fields(const InstDesc<T>* d_desc, int ninst, long 
 
 template <typename T, bool SHIFT>
 cudaError_t Launch<T, SHIFT>::staged(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, bool heun,
-                                     bool sync, cudaStream_t s) {
+                                     bool sync, int vel, int form, cudaStream_t s) {
   const unsigned g = (unsigned)total_blocks;
   k_fields<T><<<g, bs, 0, s>>>(d_desc, ninst);
-  k_lb<T, SHIFT><<<g, bs, 0, s>>>(d_desc, ninst);
+  if (vel == 0 && form == 0) k_lb<T, SHIFT, VelD3Q19, 0><<<g, bs, 0, s>>>(d_desc, ninst);
+  else if (vel == 0) k_lb<T, SHIFT, VelD3Q19, 1><<<g, bs, 0, s>>>(d_desc, ninst);
+  else if (form == 0) k_lb<T, SHIFT, VelD3Q15, 0><<<g, bs, 0, s>>>(d_desc, ninst);
+  else k_lb<T, SHIFT, VelD3Q15, 1><<<g, bs, 0, s>>>(d_desc, ninst);
   if (!heun) {
     k_op<T, 0><<<g, bs, 0, s>>>(d_desc, ninst, sync ? 1 : 0);
   } else {
@@ -862,12 +946,13 @@ inline unsigned grid_for(long long N, int bs) {
 template <typename T, bool SHIFT>
 cudaError_t Launch<T, SHIFT>::get_fields(const InstDesc<T>& I, uint32_t mask, double* dst, cudaStream_t s) {
   long long o = 0, oG = -1, oR = -1, oU = -1, oQ = -1, oP = -1;
-  if (mask & 1u) { oG = o; o += 19 * I.N; }
+  if (mask & 1u) { oG = o; o += (I.vel ? 15 : 19) * I.N; }
   if (mask & 2u) { oR = o; o += I.N; }
   if (mask & 4u) { oU = o; o += 3 * I.N; }
   if (mask & 8u) { oQ = o; o += 5 * I.N; }
   if (mask & 16u) { oP = o; o += I.N; }
-  k_get_fields<T, SHIFT><<<grid_for(I.N, 256), 256, 0, s>>>(I, oG, oR, oU, oQ, oP, dst);
+  if (I.vel) k_get_fields<T, SHIFT, VelD3Q15><<<grid_for(I.N, 256), 256, 0, s>>>(I, oG, oR, oU, oQ, oP, dst);
+  else k_get_fields<T, SHIFT, VelD3Q19><<<grid_for(I.N, 256), 256, 0, s>>>(I, oG, oR, oU, oQ, oP, dst);
   return cudaGetLastError();
 }
 
@@ -875,18 +960,22 @@ template <typename T, bool SHIFT>
 cudaError_t Launch<T, SHIFT>::set_fields(const InstDesc<T>& I, uint32_t mask, const double* src, T* g_t, T* q_t,
                                          T* p_t, T* u_t, cudaStream_t s) {
   long long o = 0, oG = -1, oU = -1, oQ = -1, oP = -1;
-  if (mask & 1u) { oG = o; o += 19 * I.N; }
+  if (mask & 1u) { oG = o; o += (I.vel ? 15 : 19) * I.N; }
   if (mask & 4u) { oU = o; o += 3 * I.N; }
   if (mask & 8u) { oQ = o; o += 5 * I.N; }
   if (mask & 16u) { oP = o; o += I.N; }
-  k_set_fields<T, SHIFT><<<grid_for(I.N, 256), 256, 0, s>>>(I, oG, oU, oQ, oP, src, g_t, q_t, p_t, u_t);
+  if (I.vel)
+    k_set_fields<T, SHIFT, VelD3Q15><<<grid_for(I.N, 256), 256, 0, s>>>(I, oG, oU, oQ, oP, src, g_t, q_t, p_t, u_t);
+  else
+    k_set_fields<T, SHIFT, VelD3Q19><<<grid_for(I.N, 256), 256, 0, s>>>(I, oG, oU, oQ, oP, src, g_t, q_t, p_t, u_t);
   return cudaGetLastError();
 }
 
 template <typename T, bool SHIFT>
 cudaError_t Launch<T, SHIFT>::observables(const InstDesc<T>& I, double* partial, int nblocks, double* out,
                                           cudaStream_t s) {
-  k_obs_partial<T, SHIFT><<<nblocks, kObsBlock, 0, s>>>(I, partial);
+  if (I.vel) k_obs_partial<T, SHIFT, VelD3Q15><<<nblocks, kObsBlock, 0, s>>>(I, partial);
+  else k_obs_partial<T, SHIFT, VelD3Q19><<<nblocks, kObsBlock, 0, s>>>(I, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_obs_final<<<1, 32, 0, s>>>(partial, nblocks, out);

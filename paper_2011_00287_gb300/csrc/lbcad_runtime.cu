@@ -74,6 +74,8 @@ struct lbcad_ctx {
   int path = LBCAD_PATH_FUSED;
   int integrator = LBCAD_EULER;
   int coupling = LBCAD_LAGGED;
+  int vel = LBCAD_D3Q19;          // velocity set of the populations
+  int lb_form = LBCAD_LB_BODY_FORCE;
   bool scratch_ready = false;
   FusedTile* tiles = nullptr;
   size_t tiles_cap = 0;
@@ -85,8 +87,12 @@ struct lbcad_ctx {
   void* adj_lam = nullptr;  // cotangent of the initial state of the last lbcad_adjoint
   std::string err;
   size_t elem() const { return prec == LBCAD_FP64 ? sizeof(double) : sizeof(float); }
-  // Heun or sync need the staged path
-  bool staged_only() const { return integrator != LBCAD_EULER || coupling != LBCAD_LAGGED; }
+  // Heun, sync, D3Q15 and the stress-in-equilibrium form run on the staged path only
+  bool staged_only() const {
+    return integrator != LBCAD_EULER || coupling != LBCAD_LAGGED || vel != LBCAD_D3Q19 ||
+           lb_form != LBCAD_LB_BODY_FORCE;
+  }
+  int q() const { return vel == LBCAD_D3Q15 ? 15 : 19; }
 };
 
 namespace {
@@ -146,6 +152,8 @@ std::string validate(const lbcad_grid& g, const lbcad_params& p) {
   if (p.precision != LBCAD_FP32 && p.precision != LBCAD_FP64) return "params: precision must be FP32 or FP64";
   if (p.integrator != LBCAD_EULER && p.integrator != LBCAD_HEUN) return "params: unknown integrator";
   if (p.coupling != LBCAD_LAGGED && p.coupling != LBCAD_SYNC) return "params: unknown coupling";
+  if (p.lattice != LBCAD_D3Q19 && p.lattice != LBCAD_D3Q15) return "params: unknown lattice";
+  if (p.lb_form != LBCAD_LB_BODY_FORCE && p.lb_form != LBCAD_LB_STRESS_EQ) return "params: unknown lb_form";
   return "";
 }
 
@@ -166,6 +174,7 @@ InstDesc<T> make_desc(const Inst& I, int parity) {
   InstDesc<T> d;
   std::memset(&d, 0, sizeof(d));
   d.nx = I.g.nx; d.ny = I.g.ny; d.nz = I.g.nz;
+  d.vel = (I.p.lattice == LBCAD_D3Q15) ? 1 : 0;
   d.N = I.N;
   d.blk0 = I.blk0;
   d.nblk = I.nblk;
@@ -224,12 +233,14 @@ int upload_init(lbcad_ctx* c, Inst& I, uint64_t seed, int idx) {
   for (long long k = 0; k < 5 * N; ++k) tq[k] = (T)q5[k];
   for (long long k = 0; k < N; ++k) tp[k] = (T)psi[k];
   const bool shifted = (c->prec == LBCAD_FP32);
-  std::vector<T> tg(19 * N);
-  for (int i = 0; i < 19; ++i) {
-    const T v = shifted ? T(0) : (T)(lat_w(i) * I.p.rho0);
+  const int q = c->q();
+  std::vector<T> tg(q * N);
+  for (int i = 0; i < q; ++i) {
+    const double w = (q == 15) ? lat15_w(i) : lat_w(i);
+    const T v = shifted ? T(0) : (T)(w * I.p.rho0);
     for (long long s = 0; s < N; ++s) tg[i * N + s] = v;
   }
-  CK(c, cudaMemcpyAsync(I.gb[0], tg.data(), 19 * N * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(I.gb[0], tg.data(), q * N * sizeof(T), cudaMemcpyHostToDevice, c->stream));
   CK(c, cudaMemcpyAsync(I.qb[0], tq.data(), 5 * N * sizeof(T), cudaMemcpyHostToDevice, c->stream));
   CK(c, cudaMemcpyAsync(I.pb[0], tp.data(), N * sizeof(T), cudaMemcpyHostToDevice, c->stream));
   CK(c, cudaMemsetAsync(I.ub[0], 0, 3 * N * sizeof(T), c->stream));
@@ -253,6 +264,8 @@ int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint
       return fail(nullptr, LBCAD_E_INVALID_ARG, "all instances must share one precision");
     if (params[i].integrator != params[0].integrator || params[i].coupling != params[0].coupling)
       return fail(nullptr, LBCAD_E_INVALID_ARG, "all instances must share one integrator and one coupling");
+    if (params[i].lattice != params[0].lattice || params[i].lb_form != params[0].lb_form)
+      return fail(nullptr, LBCAD_E_INVALID_ARG, "all instances must share one lattice and one lb_form");
   }
   lbcad_ctx* c = new (std::nothrow) lbcad_ctx();
   if (!c) return fail(nullptr, LBCAD_E_OOM, "host allocation failed");
@@ -260,6 +273,8 @@ int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint
   c->prec = p0.precision;
   c->integrator = p0.integrator;
   c->coupling = p0.coupling;
+  c->vel = p0.lattice;
+  c->lb_form = p0.lb_form;
   c->alloc = p0.alloc;
   c->free = p0.free;
   c->user = p0.alloc_user;
@@ -302,7 +317,7 @@ int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint
     I.nblk = (I.N + kStepBlock - 1) / kStepBlock;
     blk += I.nblk;
     for (int par = 0; par < 2; ++par) {
-      I.gb[par] = dev_alloc(c, 19 * I.N * es);
+      I.gb[par] = dev_alloc(c, (size_t)c->q() * I.N * es);
       I.qb[par] = dev_alloc(c, 5 * I.N * es);
       I.pb[par] = dev_alloc(c, I.N * es);
       I.ub[par] = dev_alloc(c, 3 * I.N * es);
@@ -431,9 +446,11 @@ int launch_steps(lbcad_ctx* c, int64_t n) {
     } else if (c->path == LBCAD_PATH_STAGED) {
       e = (c->prec == LBCAD_FP64)
               ? Launch<double, false>::staged((const InstDesc<double>*)c->desc[par], (int)c->inst.size(),
-                                              c->total_blocks, kStepBlock, heun, sync, c->stream)
+                                              c->total_blocks, kStepBlock, heun, sync, c->vel, c->lb_form,
+                                              c->stream)
               : Launch<float, true>::staged((const InstDesc<float>*)c->desc[par], (int)c->inst.size(),
-                                            c->total_blocks, kStepBlock, heun, sync, c->stream);
+                                            c->total_blocks, kStepBlock, heun, sync, c->vel, c->lb_form,
+                                            c->stream);
     } else if (c->prec == LBCAD_FP64)
       e = Launch<double, false>::step((const InstDesc<double>*)c->desc[par], (int)c->inst.size(), c->total_blocks,
                                       kStepBlock, c->stream);
@@ -461,8 +478,8 @@ int ensure_staging(lbcad_ctx* c, size_t bytes) {
   return LBCAD_OK;
 }
 
-int ncomp_of(uint32_t mask) {
-  return ((mask & LBCAD_FIELD_G) ? 19 : 0) + ((mask & LBCAD_FIELD_RHO) ? 1 : 0) + ((mask & LBCAD_FIELD_U) ? 3 : 0) +
+int ncomp_of(uint32_t mask, int q = 19) {
+  return ((mask & LBCAD_FIELD_G) ? q : 0) + ((mask & LBCAD_FIELD_RHO) ? 1 : 0) + ((mask & LBCAD_FIELD_U) ? 3 : 0) +
          ((mask & LBCAD_FIELD_Q) ? 5 : 0) + ((mask & LBCAD_FIELD_PSI) ? 1 : 0);
 }
 
@@ -477,6 +494,16 @@ int lbcad_lattice(int32_t* c57, double* w19) {
     w19[i] = lat_w(i);
   }
   return LBCAD_OK;
+}
+
+int lbcad_velocity_set(int32_t lattice, int32_t* c, double* w) {
+  if (!c || !w || (lattice != LBCAD_D3Q19 && lattice != LBCAD_D3Q15)) return LBCAD_E_INVALID_ARG;
+  const int q = (lattice == LBCAD_D3Q15) ? 15 : 19;
+  for (int i = 0; i < q; ++i) {
+    for (int a = 0; a < 3; ++a) c[3 * i + a] = (q == 15) ? lat15_c(i, a) : lat_c(i, a);
+    w[i] = (q == 15) ? lat15_w(i) : lat_w(i);
+  }
+  return q;
 }
 
 int lbcad_create(const lbcad_grid* grid, const lbcad_params* params, uint64_t seed, lbcad_ctx** out) {
@@ -607,7 +634,7 @@ int lbcad_get_fields(lbcad_ctx* c, int32_t inst, uint32_t mask, void* dst, size_
   if (inst < 0 || inst >= (int)c->inst.size()) return fail(c, LBCAD_E_INVALID_ARG, "instance out of range");
   if (!dst || mask == 0 || (mask & ~31u)) return fail(c, LBCAD_E_INVALID_ARG, "bad dst or mask");
   const long long N = c->inst[inst].N;
-  const size_t need = (size_t)ncomp_of(mask) * N * sizeof(double);
+  const size_t need = (size_t)ncomp_of(mask, c->q()) * N * sizeof(double);
   if (bytes < need) return fail(c, LBCAD_E_INVALID_ARG, "dst too small");
   DeviceGuard dg(c->device);
   double* target = (double*)dst;
@@ -632,7 +659,7 @@ int lbcad_set_fields(lbcad_ctx* c, int32_t inst, uint32_t mask, const void* src,
   if (!src || mask == 0 || (mask & ~31u) || (mask & LBCAD_FIELD_RHO))
     return fail(c, LBCAD_E_INVALID_ARG, "bad src or mask (RHO cannot be set)");
   const long long N = c->inst[inst].N;
-  const size_t need = (size_t)ncomp_of(mask) * N * sizeof(double);
+  const size_t need = (size_t)ncomp_of(mask, c->q()) * N * sizeof(double);
   if (bytes < need) return fail(c, LBCAD_E_INVALID_ARG, "src too small");
   DeviceGuard dg(c->device);
   const double* from = (const double*)src;

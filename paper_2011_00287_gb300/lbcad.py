@@ -27,6 +27,8 @@ LBCAD_E_UNSUPPORTED = -6
 FP32, FP64 = 0, 1
 EULER, HEUN = 0, 1
 LAGGED, SYNC = 0, 1
+D3Q19, D3Q15 = 0, 1
+LB_BODY_FORCE, LB_STRESS_EQ = 0, 1
 FIELD_G, FIELD_RHO, FIELD_U, FIELD_Q, FIELD_PSI = 1, 2, 4, 8, 16
 PATH_FUSED, PATH_TWO_KERNEL, PATH_STAGED = 0, 1, 2
 N_TILE_CONFIGS = 7  # candidates of lbcad_autotune / lbcad_set_tiles (FP32; FP64 has one)
@@ -52,7 +54,8 @@ class lbcad_params(ctypes.Structure):
         "tau", "rho0", "A0", "chi0", "chis", "K", "q0", "gammaQ", "xi", "a", "b", "kphi", "M", "W",
         "zeta", "R")] + [("centre", ctypes.c_double * 3), ("S0", ctypes.c_double), ("noise", ctypes.c_double),
                          ("precision", ctypes.c_int32), ("integrator", ctypes.c_int32),
-                         ("coupling", ctypes.c_int32), ("device", ctypes.c_int32),
+                         ("coupling", ctypes.c_int32), ("lattice", ctypes.c_int32), ("lb_form", ctypes.c_int32),
+                         ("device", ctypes.c_int32),
                          ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                          ("alloc_user", ctypes.c_void_p)])
 
@@ -69,6 +72,7 @@ class lbcad_obs(ctypes.Structure):
 _P = ctypes.POINTER
 _SIGS = {
     "lbcad_lattice": (ctypes.c_int, [_P(ctypes.c_int32), _P(ctypes.c_double)]),
+    "lbcad_velocity_set": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_int32), _P(ctypes.c_double)]),
     "lbcad_create": (ctypes.c_int, [_P(lbcad_grid), _P(lbcad_params), ctypes.c_uint64, _P(ctypes.c_void_p)]),
     "lbcad_create_batch": (ctypes.c_int, [ctypes.c_int32, _P(lbcad_grid), _P(lbcad_params), ctypes.c_uint64,
                                           _P(ctypes.c_void_p)]),
@@ -123,11 +127,13 @@ def _check(code: int, ctx=None):
         raise LbcadError(code, msg.decode() if msg else "")
 
 
-def lattice():
+def lattice(velocity_set: int = D3Q19):
+    """Velocities (q, 3) and weights (q,) of the population velocity set (D3Q19 or D3Q15)."""
     c = (ctypes.c_int32 * 57)()
     w = (ctypes.c_double * 19)()
-    _check(library().lbcad_lattice(c, w))
-    return np.array(list(c), dtype=np.int32).reshape(19, 3), np.array(list(w))
+    q = library().lbcad_velocity_set(int(velocity_set), c, w)
+    _check(min(q, 0))
+    return np.array(list(c)[:3 * q], dtype=np.int32).reshape(q, 3), np.array(list(w)[:q])
 
 
 # ---------------------------------------------------------------- parameters
@@ -140,7 +146,7 @@ def default_params(shape=(32, 32, 32), R: float = 8.0, p0: float = 16.0, precisi
     d = dict(tau=1.0, rho0=1.0, A0=1.0, chi0=2.5, chis=0.25, K=0.04, q0=2.0 * math.pi / p0, gammaQ=0.3,
              xi=0.7, a=0.07, b=0.07, kphi=0.14, M=0.1, W=0.02, zeta=0.005, R=R,
              centre=(nx / 2.0, ny / 2.0, nz / 2.0), S0=0.5, noise=1e-3, precision=precision,
-             integrator=EULER, coupling=LAGGED)
+             integrator=EULER, coupling=LAGGED, lattice=D3Q19, lb_form=LB_BODY_FORCE)
     d.update(kw)
     return d
 
@@ -175,7 +181,7 @@ def _fill_params(d: Dict, stream, device: int, allocator: Optional[_TorchAllocat
         if k == "centre":
             for i in range(3):
                 p.centre[i] = float(v[i])
-        elif k in ("precision", "integrator", "coupling"):
+        elif k in ("precision", "integrator", "coupling", "lattice", "lb_form"):
             setattr(p, k, int(v))
         else:
             setattr(p, k, float(v))
@@ -243,6 +249,7 @@ class Simulation:
         self.params = params
         self.device = device
         self.precision = int(params[0].get("precision", FP32))
+        self.q = 15 if int(params[0].get("lattice", D3Q19)) == D3Q15 else 19  # populations per site
 
     # -- lifecycle
     def close(self):
@@ -315,11 +322,14 @@ class Simulation:
             raise LbcadError(LBCAD_E_INVALID_ARG, "instance %d out of range [0, %d)" % (inst, len(self.grids)))
         return self.grids[int(inst)]
 
+    def _ncomp(self, b: int) -> int:
+        return self.q if b == FIELD_G else FIELD_NCOMP[b]
+
     def get_fields(self, inst: int = 0, mask: int = FIELD_G | FIELD_U | FIELD_Q | FIELD_PSI, out=None,
                    on_device: bool = False) -> Dict[str, object]:
         nx, ny, nz = self._inst(inst)
         N = nx * ny * nz
-        ncomp = sum(c for b, c in FIELD_NCOMP.items() if mask & b)
+        ncomp = sum(self._ncomp(b) for b in FIELD_NCOMP if mask & b)
         nbytes = 8 * N * ncomp
         if on_device:
             import torch
@@ -334,7 +344,7 @@ class Simulation:
         res, o = {}, 0
         for b in (FIELD_G, FIELD_RHO, FIELD_U, FIELD_Q, FIELD_PSI):
             if mask & b:
-                c = FIELD_NCOMP[b]
+                c = self._ncomp(b)
                 v = buf[o * N:(o + c) * N].reshape(c, nz, ny, nx)
                 res[FIELD_NAMES[b]] = v[0] if b in (FIELD_RHO, FIELD_PSI) else v
                 o += c
@@ -352,7 +362,7 @@ class Simulation:
         if not mask:
             raise ValueError("no settable field given")
         buf = np.ascontiguousarray(np.concatenate(parts))
-        if buf.size != N * sum(FIELD_NCOMP[b] for b in FIELD_NCOMP if mask & b):
+        if buf.size != N * sum(self._ncomp(b) for b in FIELD_NCOMP if mask & b):
             raise ValueError("field sizes do not match the grid")
         _check(library().lbcad_set_fields(self.ctx, inst, mask, ctypes.c_void_p(buf.ctypes.data), buf.nbytes, 0),
                self.ctx)
