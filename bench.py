@@ -35,7 +35,8 @@ TILE_NAMES = ["32x8", "32x16", "64x8", "32x8-pipelined-8+8", "32x8-pipelined-6+1
 
 
 def workload_params(L, n, prec, **kw):
-    return L.default_params((n, n, n), R=n / 4.0, p0=n / 4.0, precision=prec, zeta=0.005, **kw)
+    kw.setdefault("zeta", 0.005)
+    return L.default_params((n, n, n), R=n / 4.0, p0=n / 4.0, precision=prec, **kw)
 
 
 def measured_peaks():
@@ -312,6 +313,20 @@ def main():
             staged[name] = {"mlups": N / (msv * 1e-3) / 1e6, "ms_per_step": msv, "kernels_per_step": launches}
             sv.close()
 
+    # second workload: bulk active nematic (no droplet, psi = 1), same kernel and schedule
+    bulk = None
+    if not args.no_staged:
+        from paper_2011_00287_gb300 import workloads as WL
+        sb = L.Simulation([(n, n, n)], [workload_params(L, n, L.FP32, zeta=0.008, q0=0.0)], seed=1 + rank,
+                          device=local)
+        sb.set_fields(0, WL.bulk_order((n, n, n), q0=0.0, noise=1e-3, seed=3))
+        sb.set_tiles(tile_cfg)
+        sb.step(3)
+        msb = time_steps(sb, torch, 200)
+        bulk = {"mlups": N / (msb * 1e-3) / 1e6, "ms_per_step": msb,
+                "workload": "bulk active nematic %d^3, psi = 1, zeta = 0.008 (spontaneous-flow regime)" % n}
+        sb.close()
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -377,7 +392,7 @@ def main():
                            "l2": "state %.0f MB per step > 129 MB L2, no flush" % (224 * N / 1e6)},
                 "roofline": roofline, "roofline_issue": roofline_issue, "cpu_baseline": cpu, "e2e": e2e,
                 "tiles": {"chosen": TILE_NAMES[tile_cfg], "ms_per_cfg": dict(zip(TILE_NAMES, tile_ms))},
-                "gpu_launches": K, "clocks": csum, "fp64_gpu": fp64, "staged_fp32": staged,
+                "gpu_launches": K, "clocks": csum, "fp64_gpu": fp64, "staged_fp32": staged, "bulk_fp32": bulk,
                 "speedup_fp32_vs_fp64": (value / world / fp64["mlups"]) if fp64 else None,
                 "observables_finite": finite}
         print(json.dumps(line))

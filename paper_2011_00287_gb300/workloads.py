@@ -27,6 +27,21 @@ def batch_uneven(seed: int = 7, count: int = 64, edges=(48, 64, 80, 96)):
     return out
 
 
+def bulk_order(shape, S0: float = 0.5, q0: float = 0.0, noise: float = 1e-3, seed: int = 1):
+    """Bulk liquid crystal with no droplet (psi = 1 everywhere): Q = S0 (n n - I/3) with the
+    director n = (cos q0 z, sin q0 z, 0) (q0 = 0: a uniform nematic along x; q0 != 0: a
+    cholesteric helix about z), plus noise * U[-1, 1) on each stored component from numpy's
+    PCG64 seeded with `seed`.  Returns {"q": (5, nz, ny, nx), "psi": (nz, ny, nx)}; the
+    populations and the velocity keep the fluid at rest as created."""
+    nx, ny, nz = shape
+    z = np.arange(nz, dtype=np.float64).reshape(nz, 1, 1) * np.ones((nz, ny, nx))
+    n0, n1 = np.cos(q0 * z), np.sin(q0 * z)
+    q = np.array([S0 * (n0 * n0 - 1.0 / 3.0), S0 * n0 * n1, 0.0 * z, S0 * (n1 * n1 - 1.0 / 3.0), 0.0 * z])
+    rng = np.random.default_rng(seed)
+    q += noise * rng.uniform(-1.0, 1.0, size=q.shape)
+    return {"q": np.ascontiguousarray(q), "psi": np.ones((nz, ny, nx))}
+
+
 def shard(count: int, rank: int, world: int):
     """Contiguous share of `count` independent units for `rank` of `world`."""
     lo = (count * rank) // world
