@@ -50,6 +50,8 @@ typedef struct {
   int lattice;            // LB velocity set: 19 = D3Q19, 15 = D3Q15 (Sec. 3, Fig. 1)
   int lb_form;            // 0 = whole stress as a body force (Guo), 1 = Eqs. 9-11: symmetric
                           //     stress in the equilibrium, antisymmetric stress as forcing
+  int stencil;            // finite differences: 0 = isotropic D3Q19 (radius 1), 1 = fourth-order
+                          //     truncation along the axes (radius 2), the other reading of Sec. 3
 } orc_params;
 
 }  // extern "C"
@@ -124,7 +126,7 @@ using M3 = R[3][3];
 template <typename R>
 struct PR {
   R tau, rho0, A0, chi0, chis, K, q0, gammaQ, xi, a, b, kphi, M, W, zeta;
-  int integrator, coupling, lattice, lb_form;
+  int integrator, coupling, lattice, lb_form, stencil;
 };
 
 template <typename R>
@@ -136,6 +138,7 @@ PR<R> promote(const orc_params& p) {
   r.coupling = p.coupling;
   r.lattice = p.lattice;
   r.lb_form = p.lb_form;
+  r.stencil = p.stencil;
   return r;
 }
 
@@ -265,6 +268,72 @@ void derivs_at(const Box& B, const R* q5, const R* psi, int x, int y, int z, Der
       d.hpsi[a][b] = 0.25 * (spp - spm - smp + smm);
     }
   }
+}
+
+// Fourth-order central differences along the axes (radius 2):
+//   d_a f   = [8 (f(+e_a) - f(-e_a)) - (f(+2e_a) - f(-2e_a))] / 12,
+//   d_aa f  = [16 (f(+e_a) + f(-e_a)) - (f(+2e_a) + f(-2e_a)) - 30 f] / 12,
+//   d_a d_b f (a != b) = d_a applied to d_b f (16 points),
+// and the Laplacian as the sum of the three d_aa.
+template <typename R, class G>
+R r2_d1(const G& f, int a) {
+  int e[3] = {0, 0, 0};
+  e[a] = 1;
+  return (8.0 * (f(e[0], e[1], e[2]) - f(-e[0], -e[1], -e[2])) -
+          (f(2 * e[0], 2 * e[1], 2 * e[2]) - f(-2 * e[0], -2 * e[1], -2 * e[2]))) / 12.0;
+}
+
+template <typename R, class G>
+R r2_d2(const G& f, int a) {
+  int e[3] = {0, 0, 0};
+  e[a] = 1;
+  return (16.0 * (f(e[0], e[1], e[2]) + f(-e[0], -e[1], -e[2])) -
+          (f(2 * e[0], 2 * e[1], 2 * e[2]) + f(-2 * e[0], -2 * e[1], -2 * e[2])) - 30.0 * f(0, 0, 0)) / 12.0;
+}
+
+template <typename R, class G>
+R r2_mixed(const G& f, int a, int b) {
+  const R c[5] = {1.0 / 12.0, -8.0 / 12.0, 0.0, 8.0 / 12.0, -1.0 / 12.0};  // weights of -2..2
+  R s = 0.0;
+  for (int i = -2; i <= 2; ++i)
+    for (int j = -2; j <= 2; ++j) {
+      if (i == 0 || j == 0) continue;
+      int o[3] = {0, 0, 0};
+      o[a] += i;
+      o[b] += j;
+      s += c[i + 2] * c[j + 2] * f(o[0], o[1], o[2]);
+    }
+  return s;
+}
+
+template <typename R>
+void derivs_at_r2(const Box& B, const R* q5, const R* psi, int x, int y, int z, Derivs<R>& d) {
+  long N = B.n();
+  d = Derivs<R>();
+  auto fpsi = [&](int dx, int dy, int dz) { return psi[B.at(x + dx, y + dy, z + dz)]; };
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q) {
+      auto fq = [&](int dx, int dy, int dz) {
+        M3<R> Qn;
+        q_full(q5, N, B.at(x + dx, y + dy, z + dz), Qn);
+        return Qn[p][q];
+      };
+      for (int a = 0; a < 3; ++a) {
+        d.dQ[a][p][q] = r2_d1<R>(fq, a);
+        d.lapQ[p][q] += r2_d2<R>(fq, a);
+      }
+    }
+  for (int a = 0; a < 3; ++a) {
+    d.dpsi[a] = r2_d1<R>(fpsi, a);
+    d.lappsi += r2_d2<R>(fpsi, a);
+    for (int b = 0; b < 3; ++b) d.hpsi[a][b] = (a == b) ? r2_d2<R>(fpsi, a) : r2_mixed<R>(fpsi, a, b);
+  }
+}
+
+template <typename R>
+void derivs_any(int stencil, const Box& B, const R* q5, const R* psi, int x, int y, int z, Derivs<R>& d) {
+  if (stencil == 1) derivs_at_r2(B, q5, psi, x, y, z, d);
+  else derivs_at(B, q5, psi, x, y, z, d);
 }
 
 // Local<R> quantities at one site: H (Eq. 2, Eq. 5), mu (Eq. 1, Eq. 5), free-energy density
@@ -419,6 +488,21 @@ void vec_grad_at(const Box& B, const R* u, int x, int y, int z, M3<R> Wg) {
 }
 
 template <typename R>
+void vec_grad_at_r2(const Box& B, const R* u, int x, int y, int z, M3<R> Wg) {
+  long N = B.n();
+  for (int a = 0; a < 3; ++a) {
+    auto fu = [&](int dx, int dy, int dz) { return u[a * N + B.at(x + dx, y + dy, z + dz)]; };
+    for (int b = 0; b < 3; ++b) Wg[a][b] = r2_d1<R>(fu, b);
+  }
+}
+
+template <typename R>
+void vec_grad_any(int stencil, const Box& B, const R* u, int x, int y, int z, M3<R> Wg) {
+  if (stencil == 1) vec_grad_at_r2(B, u, x, y, z, Wg);
+  else vec_grad_at(B, u, x, y, z, Wg);
+}
+
+template <typename R>
 struct Work {
   std::vector<R> H, mu, sig, sigA, F, unew, fnew, rhsQ, rhsP, Qp, Pp;
 };
@@ -433,7 +517,7 @@ void fields_all(const Box& B, const PR<R>& P, const R* q5, const R* psi, R* H5, 
       for (int x = 0; x < B.nx; ++x) {
         long s = B.at(x, y, z);
         Derivs<R> d;
-        derivs_at(B, q5, psi, x, y, z, d);
+        derivs_any(P.stencil, B, q5, psi, x, y, z, d);
         M3<R> Q;
         q_full(q5, N, s, Q);
         Local<R> L;
@@ -452,15 +536,25 @@ void fields_all(const Box& B, const PR<R>& P, const R* q5, const R* psi, R* H5, 
       }
 }
 
-// Stage 5: F_a = d_b sigma_ab with the isotropic gradient.
+// Stage 5: F_a = d_b sigma_ab with the isotropic gradient (stencil 0) or the fourth-order
+// axis differences (stencil 1).
 template <typename R>
-void force_all(const Box& B, const R* sig9, R* F3) {
+void force_all(const Box& B, const R* sig9, R* F3, int stencil = 0) {
   long N = B.n();
   for (int z = 0; z < B.nz; ++z)
     for (int y = 0; y < B.ny; ++y)
       for (int x = 0; x < B.nx; ++x) {
         long s = B.at(x, y, z);
         R F[3] = {0, 0, 0};
+        if (stencil == 1) {
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+              auto fs = [&](int dx, int dy, int dz) { return sig9[(3 * a + b) * N + B.at(x + dx, y + dy, z + dz)]; };
+              F[a] += r2_d1<R>(fs, b);
+            }
+          for (int a = 0; a < 3; ++a) F3[a * N + s] = F[a];
+          continue;
+        }
         for (int i = 1; i < NQ; ++i) {
           long n = B.at(x + CV[i][0], y + CV[i][1], z + CV[i][2]);
           R w = wgt(i);
@@ -566,7 +660,7 @@ void op_rhs(const Box& B, const PR<R>& P, const R* q5, const R* psi, const R* ua
         M3<R> Q, H, Wg, S;
         q_full(q5, N, s, Q);
         q_full(H5, N, s, H);
-        vec_grad_at(B, uadv, x, y, z, Wg);
+        vec_grad_any(P.stencil, B, uadv, x, y, z, Wg);
         corotation(Wg, Q, P.xi, S);
         M3<R> adv;
         for (int i = 0; i < 3; ++i)
@@ -593,9 +687,14 @@ void op_rhs(const Box& B, const PR<R>& P, const R* q5, const R* psi, const R* ua
           div += Jp - Jm;
         }
         R lapmu = 0.0;
-        for (int i = 1; i < NQ; ++i) {
-          long n = B.at(x + CV[i][0], y + CV[i][1], z + CV[i][2]);
-          lapmu += 6.0 * wgt(i) * (mu[n] - mu[s]);
+        if (P.stencil == 1) {
+          auto fm = [&](int dx, int dy, int dz) { return mu[B.at(x + dx, y + dy, z + dz)]; };
+          for (int a = 0; a < 3; ++a) lapmu += r2_d2<R>(fm, a);
+        } else {
+          for (int i = 1; i < NQ; ++i) {
+            long n = B.at(x + CV[i][0], y + CV[i][1], z + CV[i][2]);
+            lapmu += 6.0 * wgt(i) * (mu[n] - mu[s]);
+          }
         }
         M3<R> Rm;
         for (int i = 0; i < 3; ++i)
@@ -623,10 +722,10 @@ void step_one(const Box& B, const PR<R>& P, R* f, R* q5, R* psi, R* uprev, Work<
       for (int b = 0; b < 3; ++b)
         for (long k = 0; k < N; ++k)
           w.sigA[(3 * a + b) * N + k] = 0.5 * (w.sig[(3 * a + b) * N + k] - w.sig[(3 * b + a) * N + k]);
-    force_all<R>(B, w.sigA.data(), w.F.data());
+    force_all<R>(B, w.sigA.data(), w.F.data(), P.stencil);
     lb_all_stress<R>(B, P, f, w.F.data(), w.sig.data(), w.fnew.data(), w.unew.data());
   } else {
-    force_all<R>(B, w.sig.data(), w.F.data());
+    force_all<R>(B, w.sig.data(), w.F.data(), P.stencil);
     lb_all<R>(B, P, f, w.F.data(), w.fnew.data(), w.unew.data());
   }
   const R* uadv = (P.coupling == 1) ? w.unew.data() : uprev;
@@ -731,6 +830,30 @@ void orc_force(int nx, int ny, int nz, const double* sig9, double* F3) {
   force_all(B, sig9, F3);
 }
 
+void orc_force_st(int stencil, int nx, int ny, int nz, const double* sig9, double* F3) {
+  Box B{nx, ny, nz};
+  force_all(B, sig9, F3, stencil);
+}
+
+// Stencils (0 = isotropic radius 1, 1 = fourth-order radius 2) on a scalar field.
+void orc_stencils_st(int stencil, int nx, int ny, int nz, const double* s, double* grad3, double* lap,
+                     double* hess9) {
+  Box B{nx, ny, nz};
+  long N = B.n();
+  std::vector<double> zero(5 * N, 0.0);
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        long k = B.at(x, y, z);
+        Derivs<double> d;
+        derivs_any(stencil, B, zero.data(), s, x, y, z, d);
+        for (int a = 0; a < 3; ++a) grad3[a * N + k] = d.dpsi[a];
+        lap[k] = d.lappsi;
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) hess9[(3 * a + b) * N + k] = d.hpsi[a][b];
+      }
+}
+
 // Stencils on a scalar field (for the stencil pins).
 void orc_stencils(int nx, int ny, int nz, const double* s, double* grad3, double* lap, double* hess9) {
   Box B{nx, ny, nz};
@@ -770,7 +893,7 @@ void orc_op_rhs(int nx, int ny, int nz, const orc_params* P, const double* q5, c
         for (int x = 0; x < nx; ++x) {
           long s = B.at(x, y, z);
           M3<double> Wg;
-          vec_grad_at(B, uadv, x, y, z, Wg);
+          vec_grad_any(P->stencil, B, uadv, x, y, z, Wg);
           for (int k = 0; k < 9; ++k) W9[k * N + s] = Wg[k / 3][k % 3];
         }
   }

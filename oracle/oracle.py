@@ -30,19 +30,20 @@ class orc_params(ctypes.Structure):
         "tau", "rho0", "A0", "chi0", "chis", "K", "q0", "gammaQ", "xi",
         "a", "b", "kphi", "M", "W", "zeta", "R", "cx", "cy", "cz", "S0", "noise")] + [
         ("integrator", ctypes.c_int), ("coupling", ctypes.c_int), ("lattice", ctypes.c_int),
-        ("lb_form", ctypes.c_int)]
+        ("lb_form", ctypes.c_int), ("stencil", ctypes.c_int)]
 
 
 def default_params(n=(32, 32, 32), R=8.0, p0=16.0, **kw) -> orc_params:
     """Droplet workload parameters (A0=1, chi_in=3, K=0.04, Gamma_Q=0.3, xi=0.7,
     a=b=0.07, M=0.1, zeta=0.005, tau=1) with the readings chi0=2.5, chis=0.25,
     W=0.02, kphi=2a; centre at the box centre, S0=0.5, noise 1e-3; D3Q19 LB with the
-    whole stress as a body force (lattice=15 selects D3Q15, lb_form=1 the form of Eqs. 9-11)."""
+    whole stress as a body force (lattice=15 selects D3Q15, lb_form=1 the form of Eqs. 9-11);
+    isotropic radius-1 stencils (stencil=1 selects the fourth-order radius-2 set)."""
     nx, ny, nz = n
     d = dict(tau=1.0, rho0=1.0, A0=1.0, chi0=2.5, chis=0.25, K=0.04,
              q0=2.0 * np.pi / p0, gammaQ=0.3, xi=0.7, a=0.07, b=0.07, kphi=0.14,
              M=0.1, W=0.02, zeta=0.005, R=R, cx=nx / 2.0, cy=ny / 2.0, cz=nz / 2.0,
-             S0=0.5, noise=1e-3, integrator=0, coupling=0, lattice=19, lb_form=0)
+             S0=0.5, noise=1e-3, integrator=0, coupling=0, lattice=19, lb_form=0, stencil=0)
     d.update(kw)
     p = orc_params()
     for k, v in d.items():
@@ -80,6 +81,8 @@ def lib():
         L.orc_init.argtypes = [i, i, i, P, ctypes.c_uint64, i, dp, dp, dp, dp]
         L.orc_fields.argtypes = [i, i, i, P, dp, dp] + [dp] * 7
         L.orc_force.argtypes = [i, i, i, dp, dp]
+        L.orc_force_st.argtypes = [i, i, i, i, dp, dp]
+        L.orc_stencils_st.argtypes = [i, i, i, i, dp, dp, dp, dp]
         L.orc_stencils.argtypes = [i, i, i, dp, dp, dp, dp]
         L.orc_corotation.argtypes = [dp, dp, ctypes.c_double, dp]
         L.orc_op_rhs.argtypes = [i, i, i, P, dp, dp, dp, dp, dp, dp, dp, dp]
@@ -166,20 +169,22 @@ def fields(q, psi, params: orc_params):
     return out
 
 
-def force(sigma9):
+def force(sigma9, stencil=0):
     nz, ny, nx = sigma9.shape[1:]
     F = np.zeros((3, nz, ny, nx))
-    lib().orc_force(nx, ny, nz, _p(np.ascontiguousarray(sigma9)), _p(F))
+    lib().orc_force_st(stencil, nx, ny, nz, _p(np.ascontiguousarray(sigma9)), _p(F))
     return F
 
 
-def stencils(s):
-    """Isotropic gradient (3), Laplacian, Hessian (9 = 3a+b) of a scalar field."""
+def stencils(s, stencil=0):
+    """Gradient (3), Laplacian, Hessian (9 = 3a+b) of a scalar field with the isotropic
+    radius-1 set (stencil 0) or the fourth-order radius-2 set (stencil 1)."""
     nz, ny, nx = s.shape
     g = np.zeros((3,) + s.shape)
     lap = np.zeros(s.shape)
     h = np.zeros((9,) + s.shape)
-    lib().orc_stencils(nx, ny, nz, _p(np.ascontiguousarray(s, dtype=np.float64)), _p(g), _p(lap), _p(h))
+    lib().orc_stencils_st(stencil, nx, ny, nz, _p(np.ascontiguousarray(s, dtype=np.float64)), _p(g), _p(lap),
+                          _p(h))
     return g, lap, h
 
 

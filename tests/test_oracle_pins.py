@@ -78,6 +78,57 @@ def test_stencils_exact_on_quadratics():
             np.testing.assert_allclose(h[3 * a + b][sl], H[a, b], atol=1e-12)
 
 
+@pytest.mark.parametrize("shape", [(5, 5, 5), (6, 7, 9)])
+def test_radius2_stencil_fourier_symbols(shape):
+    """The fourth-order radius-2 set (the other reading of Sec. 3) on exp(i k.x):
+    d_a -> i (8 sin k_a - sin 2k_a)/6, d_aa -> (16 cos k_a - cos 2k_a - 15)/6, Laplacian = sum of
+    the d_aa, d_a d_b -> -(8 sin k_a - sin 2k_a)(8 sin k_b - sin 2k_b)/36 for a != b."""
+    nx, ny, nz = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    for m in [(1, 0, 0), (0, 1, 1), (1, 2, 3), (2, -1, 1)]:
+        k = [2 * np.pi * m[0] / nx, 2 * np.pi * m[1] / ny, 2 * np.pi * m[2] / nz]
+        arg = k[0] * x + k[1] * y + k[2] * z
+        d1 = [(8 * np.sin(v) - np.sin(2 * v)) / 6 for v in k]
+        d2 = [(16 * np.cos(v) - np.cos(2 * v) - 15) / 6 for v in k]
+        for part, fn in (("re", np.cos), ("im", np.sin)):
+            s = fn(arg)
+            g, lap, h = O.stencils(s, stencil=1)
+            ds = -np.sin(arg) if part == "re" else np.cos(arg)
+            for a in range(3):
+                np.testing.assert_allclose(g[a], d1[a] * ds, atol=1e-13)
+            np.testing.assert_allclose(lap, sum(d2) * s, atol=1e-13)
+            for a in range(3):
+                for b in range(3):
+                    hs = d2[a] if a == b else -d1[a] * d1[b]
+                    np.testing.assert_allclose(h[3 * a + b], hs * s, atol=1e-13)
+
+
+def test_radius2_stencils_exact_on_quartics():
+    """Away from the periodic seam, the radius-2 gradient, Laplacian and Hessian are exact on
+    polynomials of degree four (the isotropic set is exact only up to degree two)."""
+    n = 13
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    x, y, z = (v.astype(float) / n for v in (x, y, z))
+    s = 0.3 * x ** 4 - 0.7 * x ** 2 * y ** 2 + 0.2 * z ** 3 * y + 1.1 * x * y * z + 0.5 * y ** 4 - 2 * z + 3.0
+    gx = 1.2 * x ** 3 - 1.4 * x * y ** 2 + 1.1 * y * z
+    gy = -1.4 * x ** 2 * y + 0.2 * z ** 3 + 1.1 * x * z + 2.0 * y ** 3
+    gz = 0.6 * z ** 2 * y + 1.1 * x * y - 2
+    H = [[3.6 * x ** 2 - 1.4 * y ** 2, -2.8 * x * y + 1.1 * z, 1.1 * y],
+         [-2.8 * x * y + 1.1 * z, -1.4 * x ** 2 + 6.0 * y ** 2, 0.6 * z ** 2 + 1.1 * x],
+         [1.1 * y, 0.6 * z ** 2 + 1.1 * x, 1.2 * z * y]]
+    g, lap, h = O.stencils(s, stencil=1)
+    sl = (slice(2, n - 2),) * 3
+    sc = [1.0 / n, 1.0 / n ** 2]  # grid spacing 1 in the index, x = index / n
+    for a, ga in enumerate((gx, gy, gz)):
+        np.testing.assert_allclose(g[a][sl], (ga * sc[0])[sl], atol=1e-12)
+    np.testing.assert_allclose(lap[sl], ((H[0][0] + H[1][1] + H[2][2]) * sc[1])[sl], atol=1e-12)
+    for a in range(3):
+        for b in range(3):
+            np.testing.assert_allclose(h[3 * a + b][sl], (H[a][b] * sc[1])[sl], atol=1e-12)
+    gi, lapi, hi = O.stencils(s, stencil=0)
+    assert np.abs(lapi[sl] - ((H[0][0] + H[1][1] + H[2][2]) * sc[1])[sl]).max() > 1e-6
+
+
 # ---------------------------------------------------------------- LB (Eqs. 6-8, Guo forcing)
 
 def _feq(rho, v, c, w):
@@ -251,24 +302,29 @@ BASE = dict(a=0.07, b=0.07, kphi=0.14, A0=1.0, chi0=2.5, chis=0.25, K=0.04, q0=2
             W=0.1, xi=0.7, zeta=0.0)
 
 
-def test_H_mu_are_variational_derivatives_of_eq5():
-    """The oracle's H and mu converge at second order to -dF/dQ (traceless-symmetric) and
-    dF/dpsi of the free energy of Eq. 5 as written in the paper (curl form of the chiral
-    term, binary term in phi with phi0 = 2), differentiated by sympy."""
+@pytest.mark.parametrize("stencil,order", [(0, 2), (1, 4)])
+def test_H_mu_are_variational_derivatives_of_eq5(stencil, order):
+    """The oracle's H and mu converge to -dF/dQ (traceless-symmetric) and dF/dpsi of the free
+    energy of Eq. 5 as written in the paper (curl form of the chiral term, binary term in phi
+    with phi0 = 2), differentiated by sympy: at second order with the isotropic radius-1
+    stencils, at fourth order with the radius-2 set."""
     Lp = 16.0
     errs_H, errs_mu = [], []
     for n in (16, 32, 64):
         h = Lp / n
         st_ = OH.smooth_state((n, n, n), h=h, seed=5)
         H_a, mu_a = OH.analytic_H_mu(st_, BASE)
-        out = O.fields(np.ascontiguousarray(st_["q5"]), np.ascontiguousarray(st_["psi"]), _scaled_params(BASE, h))
+        prm = _scaled_params(BASE, h)
+        prm.stencil = stencil
+        out = O.fields(np.ascontiguousarray(st_["q5"]), np.ascontiguousarray(st_["psi"]), prm)
         H_o = OH.full_from5(out["H"])
         errs_H.append(np.abs(H_o - H_a).max() / np.abs(H_a).max())
         errs_mu.append(np.abs(out["mu"] - mu_a).max() / np.abs(mu_a).max())
-    # second order: each halving of h cuts the error ~4x
+    # each halving of h cuts the error by ~2^order
+    lo = 0.8 * 2 ** order
     for e in (errs_H, errs_mu):
         assert e[2] < 0.02, e
-        assert e[1] / e[2] > 3.2 and e[0] / e[1] > 3.0, e
+        assert e[1] / e[2] > lo and e[0] / e[1] > 0.75 * 2 ** order, e
 
 
 def test_helix_minimises_chiral_energy():
@@ -428,7 +484,7 @@ def test_full_step_conserves_mass_psi_momentum():
 
 def test_heun_sync_and_lb_variants_conserve():
     for kw in (dict(integrator=1), dict(coupling=1), dict(lb_form=1), dict(lattice=15),
-               dict(lattice=15, lb_form=1, integrator=1, coupling=1)):
+               dict(lattice=15, lb_form=1, integrator=1, coupling=1), dict(stencil=1)):
         s = _droplet_state(n=12, R=4.0, **kw)
         m0, p0_, _ = _sums(s)
         s.step(5)
@@ -680,8 +736,8 @@ def test_cubic_symmetry_equivariance(P, name):
         np.testing.assert_allclose(x2, x1, atol=2e-13)
 
 
-@pytest.mark.parametrize("lat,form", [(19, 0), (19, 1), (15, 0), (15, 1)])
-def test_cholesteric_helix_is_stationary(lat, form):
+@pytest.mark.parametrize("lat,form,stencil", [(19, 0, 0), (19, 1, 0), (15, 0, 0), (15, 1, 0), (19, 0, 1)])
+def test_cholesteric_helix_is_stationary(lat, form, stencil):
     """A uniform helix (psi = 1, Q period pi/q0 commensurate with the box) drives no flow
     with or without activity: rotation by pi about z maps it to itself, so sigma_xz =
     sigma_yz = 0, and screw symmetry makes sigma_zz and sigma_xx + sigma_yy uniform.  Its
@@ -689,7 +745,7 @@ def test_cholesteric_helix_is_stationary(lat, form):
     nz = 16
     shp = (4, 4, nz)
     for zeta in (0.0, 0.005):
-        p = O.default_params(shp, p0=16.0, zeta=zeta, R=1e9, lattice=lat, lb_form=form)
+        p = O.default_params(shp, p0=16.0, zeta=zeta, R=1e9, lattice=lat, lb_form=form, stencil=stencil)
         s = O.State(shp, p)
         s.psi[:] = 1.0
         z = np.arange(nz).reshape(nz, 1, 1)
