@@ -62,6 +62,9 @@ extern "C" {
 #define LBCAD_LB_STRESS_EQ 1  /* Eqs. 9-11: f_eq carries the symmetric stress,
                                * sum f_eq c c = rho/3 I + rho u u - sigma^S; the antisymmetric
                                * stress enters as F_i = 3 w_i c . div sigma^A; rho u = sum f c  */
+/* Finite-difference stencils of the order-parameter and stress derivatives (Sec. 3). */
+#define LBCAD_STENCIL_ISO 0 /* isotropic D3Q19 gradient and Laplacian (radius 1)             */
+#define LBCAD_STENCIL_R2 1  /* fourth-order central differences along the axes (radius 2)   */
 
 #define LBCAD_FIELD_G 1u
 #define LBCAD_FIELD_RHO 2u
@@ -103,6 +106,7 @@ typedef struct {
   int32_t coupling;   /* LBCAD_LAGGED or LBCAD_SYNC; one value for all instances       */
   int32_t lattice;    /* LBCAD_D3Q19 or LBCAD_D3Q15; one value for all instances        */
   int32_t lb_form;    /* LBCAD_LB_BODY_FORCE or LBCAD_LB_STRESS_EQ; one for all         */
+  int32_t stencil;    /* LBCAD_STENCIL_ISO or LBCAD_STENCIL_R2; one for all             */
   int32_t device;     /* CUDA device ordinal; -1 = the current device                 */
   void* stream;       /* cudaStream_t for all work; NULL = a private non-blocking stream */
   lbcad_alloc_fn alloc; /* NULL = cudaMalloc                                          */
@@ -164,7 +168,7 @@ int lbcad_step(lbcad_ctx* c, int64_t n);
 /* LBCAD_PATH_STAGED: per-site kernels in the order fields -> LB (force, pull, collision;
  * writes u of this step) -> order-parameter update, and for LBCAD_HEUN a second fields
  * pass at the predicted Q, psi and the corrector (Sec. 3).  The only path for LBCAD_HEUN,
- * LBCAD_SYNC, LBCAD_D3Q15 or LBCAD_LB_STRESS_EQ, selected at create; default contexts
+ * LBCAD_SYNC, LBCAD_D3Q15, LBCAD_LB_STRESS_EQ or LBCAD_STENCIL_R2, selected at create; default contexts
  * may select it as a third cross-check (same per-site arithmetic as the other two).
  * Scratch: 15 values per site, 27 with LBCAD_HEUN.  Fused/two-kernel paths, tile shapes,
  * autotune and the adjoint return LBCAD_E_UNSUPPORTED on those contexts. */

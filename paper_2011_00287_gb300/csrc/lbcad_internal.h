@@ -88,9 +88,10 @@ struct Launch {
   // predictor -> fields at the predicted state -> corrector (Heun).  sync advects with the
   // velocity of this step instead of the previous one.
   // vel: 0 = D3Q19, 1 = D3Q15 populations; form: 0 = whole stress as a body force (Guo),
-  // 1 = symmetric stress in the equilibrium, antisymmetric stress as forcing (Eqs. 9-11).
+  // 1 = symmetric stress in the equilibrium, antisymmetric stress as forcing (Eqs. 9-11);
+  // stencil: 0 = isotropic D3Q19 finite differences, 1 = fourth-order radius-2 differences.
   static cudaError_t staged(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, bool heun,
-                            bool sync, int vel, int form, cudaStream_t s);
+                            bool sync, int vel, int form, int stencil, cudaStream_t s);
   static cudaError_t get_fields(const InstDesc<T>& I, uint32_t mask, double* dst, cudaStream_t s);
   static cudaError_t set_fields(const InstDesc<T>& I, uint32_t mask, const double* src, T* g_target,
                                 T* q_target, T* psi_target, T* u_target, cudaStream_t s);

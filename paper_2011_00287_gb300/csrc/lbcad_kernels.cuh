@@ -56,6 +56,38 @@ __device__ __forceinline__ Nbr make_nbr(int x, int y, int z, int nx, int ny, int
   return n;
 }
 
+// Periodic offsets of the sites at distance up to 2 along each axis (radius-2 stencils;
+// every edge is >= 4, so one wrap suffices).
+struct NbrR2 {
+  int xo[5];
+  int yo[5];
+  long long zo[5];
+  __device__ __forceinline__ long long off(int dx, int dy, int dz) const {
+    return (long long)xo[dx + 2] + yo[dy + 2] + zo[dz + 2];
+  }
+};
+
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+__device__ __forceinline__ NbrR2 make_nbr_r2(int x, int y, int z, int nx, int ny, int nz) {
+  NbrR2 n;
+  const long long pl = (long long)nx * ny;
+#pragma unroll
+  for (int d = -2; d <= 2; ++d) {
+    n.xo[d + 2] = wrap1(x + d, nx);
+    n.yo[d + 2] = wrap1(y + d, ny) * nx;
+    n.zo[d + 2] = wrap1(z + d, nz) * pl;
+  }
+  return n;
+}
+
+// Neighbour map of stencil set ST: 0 = isotropic D3Q19 (radius 1), 1 = fourth order (radius 2).
+template <int ST>
+__device__ __forceinline__ auto make_nbr_st(int x, int y, int z, int nx, int ny, int nz) {
+  if constexpr (ST == 1) return make_nbr_r2(x, y, z, nx, ny, nz);
+  else return make_nbr(x, y, z, nx, ny, nz);
+}
+
 // Full symmetric traceless tensor from the five stored components xx, xy, xz, yy, yz.
 template <typename T>
 __device__ __forceinline__ void full3(const T q[5], T Q[3][3]) {
@@ -559,7 +591,7 @@ __device__ __forceinline__ void update_math(const Coef<T>& c, const T F[3], T la
 }
 
 // Neighbour reads straight from global memory with periodic wrap (two-kernel path).
-template <typename T>
+template <typename T, class NB = Nbr>
 struct GlobalAcc {
   const T* q_;
   const T* ps;
@@ -567,7 +599,7 @@ struct GlobalAcc {
   const T* mu_;
   const T* u_;
   long long N;
-  Nbr nb;
+  NB nb;
   __device__ __forceinline__ T q(int k, int cx, int cy, int cz) const { return ld(q_ + k * N + nb.off(cx, cy, cz)); }
   __device__ __forceinline__ T psi(int cx, int cy, int cz) const { return ld(ps + nb.off(cx, cy, cz)); }
   __device__ __forceinline__ T sig(int k, int cx, int cy, int cz) const { return ld(sg + k * N + nb.off(cx, cy, cz)); }
@@ -580,10 +612,142 @@ struct GlobalAcc {
   }
 };
 
+// ---------------------------------------------------------------- radius-2 stencils
+// Fourth-order central differences along the axes (the other reading of "fourth-order
+// accurate stencils", Sec. 3):
+//   d_a f = [8 (f(+1) - f(-1)) - (f(+2) - f(-2))] / 12,
+//   d_aa f = [16 (f(+1) + f(-1)) - (f(+2) + f(-2)) - 30 f(0)] / 12 (summed as differences to
+//   f(0)), d_a d_b f = d_a of d_b f (16 points), the Laplacian = sum of the d_aa.
+// F(dx, dy, dz) returns the field at the offset.
+template <typename T, class F>
+__device__ __forceinline__ void r2_axis(const F& f, T c, int a, T& d1, T& d2) {
+  const int ex = a == 0, ey = a == 1, ez = a == 2;
+  const T m2 = f(-2 * ex, -2 * ey, -2 * ez), m1 = f(-ex, -ey, -ez), p1 = f(ex, ey, ez), p2 = f(2 * ex, 2 * ey, 2 * ez);
+  d1 = (T(8) * (p1 - m1) - (p2 - m2)) * T(1.0 / 12.0);
+  // as differences to the centre, so that FP32 does not cancel terms of size 30 f
+  d2 = (T(16) * ((p1 - c) + (m1 - c)) - ((p2 - c) + (m2 - c))) * T(1.0 / 12.0);
+}
+
+template <typename T, class F>
+__device__ __forceinline__ T r2_mixed(const F& f, int a, int b) {
+  const T w[5] = {T(1.0 / 12.0), T(-8.0 / 12.0), T(0), T(8.0 / 12.0), T(-1.0 / 12.0)};
+  T s = T(0);
+#pragma unroll
+  for (int i = -2; i <= 2; ++i) {
+    if (i == 0) continue;
+    T r = T(0);
+#pragma unroll
+    for (int j = -2; j <= 2; ++j) {
+      if (j == 0) continue;
+      const int dx = (a == 0 ? i : 0) + (b == 0 ? j : 0);
+      const int dy = (a == 1 ? i : 0) + (b == 1 ? j : 0);
+      const int dz = (a == 2 ? i : 0) + (b == 2 ? j : 0);
+      r += w[j + 2] * f(dx, dy, dz);
+    }
+    s += w[i + 2] * r;
+  }
+  return s;
+}
+
+// a1 with the radius-2 set: the same outputs as gather_fields.
+template <typename T, class A>
+__device__ __forceinline__ void gather_fields_r2(const A& acc, T q0[5], T& p0, T dq[3][5], T lapq[5], T dp[3],
+                                                 T& lapp, T hp[6]) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    auto f = [&](int dx, int dy, int dz) { return acc.q(k, dx, dy, dz); };
+    const T c = f(0, 0, 0);
+    q0[k] = c;
+    T l = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T d1, d2;
+      r2_axis<T>(f, c, a, d1, d2);
+      dq[a][k] = d1;
+      l += d2;
+    }
+    lapq[k] = l;
+  }
+  auto fp = [&](int dx, int dy, int dz) { return acc.psi(dx, dy, dz); };
+  p0 = fp(0, 0, 0);
+  T l = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    T d1, d2;
+    r2_axis<T>(fp, p0, a, d1, d2);
+    dp[a] = d1;
+    hp[a] = d2;
+    l += d2;
+  }
+  lapp = l;
+  hp[3] = r2_mixed<T>(fp, 0, 1);
+  hp[4] = r2_mixed<T>(fp, 0, 2);
+  hp[5] = r2_mixed<T>(fp, 1, 2);
+}
+
+// a3 with the radius-2 set: F_a = sum_b d_b sigma_ab.
+template <typename T, class A>
+__device__ __forceinline__ void gather_force_r2(const A& acc, T F[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    T s = T(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int k = 3 * a + b;
+      auto f = [&](int dx, int dy, int dz) { return acc.sig(k, dx, dy, dz); };
+      T d1, d2;
+      r2_axis<T>(f, T(0), b, d1, d2);
+      s += d1;
+    }
+    F[a] = s;
+  }
+}
+
+// The stencils of a4 with the radius-2 set; the upwind faces stay at distance 1.
+template <typename T, class A>
+__device__ __forceinline__ void gather_op_r2(const A& acc, T& lapmu, T Wg[3][3], T q0[5], T qf[6][5], T& p0,
+                                             T pf[6], T u0[3], T uf[6]) {
+  {
+    auto f = [&](int dx, int dy, int dz) { return acc.mu(dx, dy, dz); };
+    const T c = f(0, 0, 0);
+    T l = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T d1, d2;
+      r2_axis<T>(f, c, a, d1, d2);
+      l += d2;
+    }
+    lapmu = l;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    auto f = [&](int dx, int dy, int dz) { return acc.u(a, dx, dy, dz); };
+    u0[a] = f(0, 0, 0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      T d1, d2;
+      r2_axis<T>(f, u0[a], b, d1, d2);
+      Wg[a][b] = d1;
+    }
+    uf[2 * a] = f(a == 0, a == 1, a == 2);
+    uf[2 * a + 1] = f(-(a == 0), -(a == 1), -(a == 2));
+  }
+#pragma unroll
+  for (int i = 1; i < 7; ++i) {
+    const int cx = lat_c(i, 0), cy = lat_c(i, 1), cz = lat_c(i, 2);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) qf[i - 1][k] = acc.q(k, cx, cy, cz);
+    pf[i - 1] = acc.psi(cx, cy, cz);
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) q0[k] = acc.q(k, 0, 0, 0);
+  p0 = acc.psi(0, 0, 0);
+}
+
 // ---------------------------------------------------------------- k_fields
 // H, mu and sigma of (q_in, psi_in) into the scratch; with PRED, H and mu of the Heun
 // predicted state qp into the (then free) sigma scratch: H at sig[0..5N), mu at sig[5N..6N).
-template <typename T, bool PRED = false>
+template <typename T, bool PRED = false, int ST = 0>
 __global__ void __launch_bounds__(kStepBlock) k_fields(const InstDesc<T>* __restrict__ D, int ninst) {
   const int ii = find_inst(D, ninst, (long long)blockIdx.x);
   const InstDesc<T>& I = D[ii];
@@ -595,13 +759,14 @@ __global__ void __launch_bounds__(kStepBlock) k_fields(const InstDesc<T>* __rest
   const long long t = s / nx;
   const int y = (int)(t % ny);
   const int z = (int)(t / ny);
-  GlobalAcc<T> acc;
+  GlobalAcc<T, decltype(make_nbr_st<ST>(0, 0, 0, 4, 4, 4))> acc;
   acc.q_ = PRED ? I.qp : I.q_in;
   acc.ps = PRED ? I.qp + 5 * N : I.psi_in;
   acc.N = N;
-  acc.nb = make_nbr(x, y, z, nx, ny, nz);
+  acc.nb = make_nbr_st<ST>(x, y, z, nx, ny, nz);
   T q0[5], p0, dq[3][5], lapq[5], dp[3], lapp, hp[6];
-  gather_fields<T>(acc, q0, p0, dq, lapq, dp, lapp, hp);
+  if constexpr (ST == 1) gather_fields_r2<T>(acc, q0, p0, dq, lapq, dp, lapp, hp);
+  else gather_fields<T>(acc, q0, p0, dq, lapq, dp, lapp, hp);
   T H[5], sig[9], mu;
   local_fields<T>(I.c, q0, p0, dq, lapq, dp, lapp, hp, H, mu, sig);
   if (PRED) {
@@ -619,11 +784,11 @@ __global__ void __launch_bounds__(kStepBlock) k_fields(const InstDesc<T>* __rest
 
 // ---------------------------------------------------------------- staged path
 // The antisymmetric part of the stress scratch, for the force of the form of Eqs. 9-11.
-template <typename T>
+template <typename T, class NB = Nbr>
 struct AntiSigAcc {
   const T* sg;
   long long N;
-  Nbr nb;
+  NB nb;
   __device__ __forceinline__ T sig(int k, int cx, int cy, int cz) const {
     const int a = k / 3, b = k - 3 * a;
     if (a == b) return T(0);
@@ -635,7 +800,7 @@ struct AntiSigAcc {
 // k_lb: the force from the stress scratch, pull, moments and collision (a3, a5):
 // g_out, u_out = velocity of this step.  FORM 0: F = div sigma, BGK + Guo (Eqs. 6-8).
 // FORM 1: FA = div sigma^A and the equilibrium with sigma^S (Eqs. 9-11).
-template <typename T, bool SHIFT, class V, int FORM>
+template <typename T, bool SHIFT, class V, int FORM, int ST>
 __global__ void __launch_bounds__(kStepBlock) k_lb(const InstDesc<T>* __restrict__ D, int ninst) {
   const int ii = find_inst(D, ninst, (long long)blockIdx.x);
   const InstDesc<T>& I = D[ii];
@@ -647,17 +812,20 @@ __global__ void __launch_bounds__(kStepBlock) k_lb(const InstDesc<T>* __restrict
   const long long t = s / nx;
   const int y = (int)(t % ny);
   const int z = (int)(t / ny);
-  const Nbr nb = make_nbr(x, y, z, nx, ny, nz);
+  auto nb = make_nbr_st<ST>(x, y, z, nx, ny, nz);
+  using NB = decltype(nb);
   T F[3];
   if (FORM == 0) {
-    GlobalAcc<T> acc;
+    GlobalAcc<T, NB> acc;
     acc.sg = I.sig;
     acc.N = N;
     acc.nb = nb;
-    gather_force<T>(acc, F);
+    if constexpr (ST == 1) gather_force_r2<T>(acc, F);
+    else gather_force<T>(acc, F);
   } else {
-    AntiSigAcc<T> acc{I.sig, N, nb};
-    gather_force<T>(acc, F);
+    AntiSigAcc<T, NB> acc{I.sig, N, nb};
+    if constexpr (ST == 1) gather_force_r2<T>(acc, F);
+    else gather_force<T>(acc, F);
   }
   T g[V::Q];
 #pragma unroll
@@ -682,7 +850,7 @@ __global__ void __launch_bounds__(kStepBlock) k_lb(const InstDesc<T>* __restrict
 //   STAGE 0  Euler:           q_out = Q + R(Q)                        (H, mu from the scratch)
 //   STAGE 1  Heun predictor:  rq = R(Q), qp = Q + rq
 //   STAGE 2  Heun corrector:  q_out = Q + (rq + R(qp)) / 2            (H, mu of qp in sigma)
-template <typename T, int STAGE>
+template <typename T, int STAGE, int ST>
 __global__ void __launch_bounds__(kStepBlock) k_op(const InstDesc<T>* __restrict__ D, int ninst, int sync) {
   const int ii = find_inst(D, ninst, (long long)blockIdx.x);
   const InstDesc<T>& I = D[ii];
@@ -694,15 +862,16 @@ __global__ void __launch_bounds__(kStepBlock) k_op(const InstDesc<T>* __restrict
   const long long t = s / nx;
   const int y = (int)(t % ny);
   const int z = (int)(t / ny);
-  GlobalAcc<T> acc;
+  GlobalAcc<T, decltype(make_nbr_st<ST>(0, 0, 0, 4, 4, 4))> acc;
   acc.q_ = STAGE == 2 ? I.qp : I.q_in;
   acc.ps = STAGE == 2 ? I.qp + 5 * N : I.psi_in;
   acc.mu_ = STAGE == 2 ? I.sig + 5 * N : I.mu;
   acc.u_ = sync ? I.u_out : I.u_in;
   acc.N = N;
-  acc.nb = make_nbr(x, y, z, nx, ny, nz);
+  acc.nb = make_nbr_st<ST>(x, y, z, nx, ny, nz);
   T lapmu, Wg[3][3], q0[5], qf[6][5], p0, pf[6], u0[3], uf[6];
-  gather_op<T>(acc, lapmu, Wg, q0, qf, p0, pf, u0, uf);
+  if constexpr (ST == 1) gather_op_r2<T>(acc, lapmu, Wg, q0, qf, p0, pf, u0, uf);
+  else gather_op<T>(acc, lapmu, Wg, q0, qf, p0, pf, u0, uf);
   const T* Hsrc = STAGE == 2 ? I.sig : I.H;
   T Hs[5];
 #pragma unroll
@@ -918,23 +1087,30 @@ cudaError_t Launch<T, SHIFT>::fields(const InstDesc<T>* d_desc, int ninst, long 
   return cudaGetLastError();
 }
 
-template <typename T, bool SHIFT>
-cudaError_t Launch<T, SHIFT>::staged(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, bool heun,
-                                     bool sync, int vel, int form, cudaStream_t s) {
-  const unsigned g = (unsigned)total_blocks;
-  k_fields<T><<<g, bs, 0, s>>>(d_desc, ninst);
-  if (vel == 0 && form == 0) k_lb<T, SHIFT, VelD3Q19, 0><<<g, bs, 0, s>>>(d_desc, ninst);
-  else if (vel == 0) k_lb<T, SHIFT, VelD3Q19, 1><<<g, bs, 0, s>>>(d_desc, ninst);
-  else if (form == 0) k_lb<T, SHIFT, VelD3Q15, 0><<<g, bs, 0, s>>>(d_desc, ninst);
-  else k_lb<T, SHIFT, VelD3Q15, 1><<<g, bs, 0, s>>>(d_desc, ninst);
+template <typename T, bool SHIFT, int ST>
+cudaError_t staged_st(const InstDesc<T>* d_desc, int ninst, unsigned g, int bs, bool heun, bool sync, int vel,
+                      int form, cudaStream_t s) {
+  k_fields<T, false, ST><<<g, bs, 0, s>>>(d_desc, ninst);
+  if (vel == 0 && form == 0) k_lb<T, SHIFT, VelD3Q19, 0, ST><<<g, bs, 0, s>>>(d_desc, ninst);
+  else if (vel == 0) k_lb<T, SHIFT, VelD3Q19, 1, ST><<<g, bs, 0, s>>>(d_desc, ninst);
+  else if (form == 0) k_lb<T, SHIFT, VelD3Q15, 0, ST><<<g, bs, 0, s>>>(d_desc, ninst);
+  else k_lb<T, SHIFT, VelD3Q15, 1, ST><<<g, bs, 0, s>>>(d_desc, ninst);
   if (!heun) {
-    k_op<T, 0><<<g, bs, 0, s>>>(d_desc, ninst, sync ? 1 : 0);
+    k_op<T, 0, ST><<<g, bs, 0, s>>>(d_desc, ninst, sync ? 1 : 0);
   } else {
-    k_op<T, 1><<<g, bs, 0, s>>>(d_desc, ninst, sync ? 1 : 0);
-    k_fields<T, true><<<g, bs, 0, s>>>(d_desc, ninst);
-    k_op<T, 2><<<g, bs, 0, s>>>(d_desc, ninst, sync ? 1 : 0);
+    k_op<T, 1, ST><<<g, bs, 0, s>>>(d_desc, ninst, sync ? 1 : 0);
+    k_fields<T, true, ST><<<g, bs, 0, s>>>(d_desc, ninst);
+    k_op<T, 2, ST><<<g, bs, 0, s>>>(d_desc, ninst, sync ? 1 : 0);
   }
   return cudaGetLastError();
+}
+
+template <typename T, bool SHIFT>
+cudaError_t Launch<T, SHIFT>::staged(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, bool heun,
+                                     bool sync, int vel, int form, int stencil, cudaStream_t s) {
+  const unsigned g = (unsigned)total_blocks;
+  if (stencil == 1) return staged_st<T, SHIFT, 1>(d_desc, ninst, g, bs, heun, sync, vel, form, s);
+  return staged_st<T, SHIFT, 0>(d_desc, ninst, g, bs, heun, sync, vel, form, s);
 }
 
 inline unsigned grid_for(long long N, int bs) {

@@ -114,8 +114,8 @@ extern "C" int lbcad_step_noalloc(const lbcad_grid* grid, const lbcad_params* pa
   if (!(p.tau > 0.5) || !(p.rho0 > 0.0)) return reject(LBCAD_E_INVALID_ARG, "params: need tau > 1/2 and rho0 > 0");
   if (p.integrator != LBCAD_EULER || p.coupling != LBCAD_LAGGED)
     return reject(LBCAD_E_UNSUPPORTED, "only the Euler integrator with lagged coupling");
-  if (p.lattice != LBCAD_D3Q19 || p.lb_form != LBCAD_LB_BODY_FORCE)
-    return reject(LBCAD_E_UNSUPPORTED, "only D3Q19 populations with the stress as a body force");
+  if (p.lattice != LBCAD_D3Q19 || p.lb_form != LBCAD_LB_BODY_FORCE || p.stencil != LBCAD_STENCIL_ISO)
+    return reject(LBCAD_E_UNSUPPORTED, "only D3Q19 populations, the stress as a body force, isotropic stencils");
   const size_t es = p.precision == LBCAD_FP64 ? sizeof(double) : sizeof(float);
   const long long N = (long long)g.nx * g.ny * g.nz;
   const size_t part = ((size_t)N * es + 255) & ~(size_t)255;

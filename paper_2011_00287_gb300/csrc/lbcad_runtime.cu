@@ -76,6 +76,7 @@ struct lbcad_ctx {
   int coupling = LBCAD_LAGGED;
   int vel = LBCAD_D3Q19;          // velocity set of the populations
   int lb_form = LBCAD_LB_BODY_FORCE;
+  int stencil = LBCAD_STENCIL_ISO;
   bool scratch_ready = false;
   FusedTile* tiles = nullptr;
   size_t tiles_cap = 0;
@@ -90,7 +91,7 @@ struct lbcad_ctx {
   // Heun, sync, D3Q15 and the stress-in-equilibrium form run on the staged path only
   bool staged_only() const {
     return integrator != LBCAD_EULER || coupling != LBCAD_LAGGED || vel != LBCAD_D3Q19 ||
-           lb_form != LBCAD_LB_BODY_FORCE;
+           lb_form != LBCAD_LB_BODY_FORCE || stencil != LBCAD_STENCIL_ISO;
   }
   int q() const { return vel == LBCAD_D3Q15 ? 15 : 19; }
 };
@@ -154,6 +155,7 @@ std::string validate(const lbcad_grid& g, const lbcad_params& p) {
   if (p.coupling != LBCAD_LAGGED && p.coupling != LBCAD_SYNC) return "params: unknown coupling";
   if (p.lattice != LBCAD_D3Q19 && p.lattice != LBCAD_D3Q15) return "params: unknown lattice";
   if (p.lb_form != LBCAD_LB_BODY_FORCE && p.lb_form != LBCAD_LB_STRESS_EQ) return "params: unknown lb_form";
+  if (p.stencil != LBCAD_STENCIL_ISO && p.stencil != LBCAD_STENCIL_R2) return "params: unknown stencil";
   return "";
 }
 
@@ -264,8 +266,9 @@ int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint
       return fail(nullptr, LBCAD_E_INVALID_ARG, "all instances must share one precision");
     if (params[i].integrator != params[0].integrator || params[i].coupling != params[0].coupling)
       return fail(nullptr, LBCAD_E_INVALID_ARG, "all instances must share one integrator and one coupling");
-    if (params[i].lattice != params[0].lattice || params[i].lb_form != params[0].lb_form)
-      return fail(nullptr, LBCAD_E_INVALID_ARG, "all instances must share one lattice and one lb_form");
+    if (params[i].lattice != params[0].lattice || params[i].lb_form != params[0].lb_form ||
+        params[i].stencil != params[0].stencil)
+      return fail(nullptr, LBCAD_E_INVALID_ARG, "all instances must share one lattice, lb_form and stencil");
   }
   lbcad_ctx* c = new (std::nothrow) lbcad_ctx();
   if (!c) return fail(nullptr, LBCAD_E_OOM, "host allocation failed");
@@ -275,6 +278,7 @@ int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint
   c->coupling = p0.coupling;
   c->vel = p0.lattice;
   c->lb_form = p0.lb_form;
+  c->stencil = p0.stencil;
   c->alloc = p0.alloc;
   c->free = p0.free;
   c->user = p0.alloc_user;
@@ -447,10 +451,10 @@ int launch_steps(lbcad_ctx* c, int64_t n) {
       e = (c->prec == LBCAD_FP64)
               ? Launch<double, false>::staged((const InstDesc<double>*)c->desc[par], (int)c->inst.size(),
                                               c->total_blocks, kStepBlock, heun, sync, c->vel, c->lb_form,
-                                              c->stream)
+                                              c->stencil, c->stream)
               : Launch<float, true>::staged((const InstDesc<float>*)c->desc[par], (int)c->inst.size(),
                                             c->total_blocks, kStepBlock, heun, sync, c->vel, c->lb_form,
-                                            c->stream);
+                                            c->stencil, c->stream);
     } else if (c->prec == LBCAD_FP64)
       e = Launch<double, false>::step((const InstDesc<double>*)c->desc[par], (int)c->inst.size(), c->total_blocks,
                                       kStepBlock, c->stream);

@@ -29,6 +29,7 @@ EULER, HEUN = 0, 1
 LAGGED, SYNC = 0, 1
 D3Q19, D3Q15 = 0, 1
 LB_BODY_FORCE, LB_STRESS_EQ = 0, 1
+STENCIL_ISO, STENCIL_R2 = 0, 1
 FIELD_G, FIELD_RHO, FIELD_U, FIELD_Q, FIELD_PSI = 1, 2, 4, 8, 16
 PATH_FUSED, PATH_TWO_KERNEL, PATH_STAGED = 0, 1, 2
 N_TILE_CONFIGS = 7  # candidates of lbcad_autotune / lbcad_set_tiles (FP32; FP64 has one)
@@ -55,6 +56,7 @@ class lbcad_params(ctypes.Structure):
         "zeta", "R")] + [("centre", ctypes.c_double * 3), ("S0", ctypes.c_double), ("noise", ctypes.c_double),
                          ("precision", ctypes.c_int32), ("integrator", ctypes.c_int32),
                          ("coupling", ctypes.c_int32), ("lattice", ctypes.c_int32), ("lb_form", ctypes.c_int32),
+                         ("stencil", ctypes.c_int32),
                          ("device", ctypes.c_int32),
                          ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                          ("alloc_user", ctypes.c_void_p)])
@@ -146,7 +148,7 @@ def default_params(shape=(32, 32, 32), R: float = 8.0, p0: float = 16.0, precisi
     d = dict(tau=1.0, rho0=1.0, A0=1.0, chi0=2.5, chis=0.25, K=0.04, q0=2.0 * math.pi / p0, gammaQ=0.3,
              xi=0.7, a=0.07, b=0.07, kphi=0.14, M=0.1, W=0.02, zeta=0.005, R=R,
              centre=(nx / 2.0, ny / 2.0, nz / 2.0), S0=0.5, noise=1e-3, precision=precision,
-             integrator=EULER, coupling=LAGGED, lattice=D3Q19, lb_form=LB_BODY_FORCE)
+             integrator=EULER, coupling=LAGGED, lattice=D3Q19, lb_form=LB_BODY_FORCE, stencil=STENCIL_ISO)
     d.update(kw)
     return d
 
@@ -181,7 +183,7 @@ def _fill_params(d: Dict, stream, device: int, allocator: Optional[_TorchAllocat
         if k == "centre":
             for i in range(3):
                 p.centre[i] = float(v[i])
-        elif k in ("precision", "integrator", "coupling", "lattice", "lb_form"):
+        elif k in ("precision", "integrator", "coupling", "lattice", "lb_form", "stencil"):
             setattr(p, k, int(v))
         else:
             setattr(p, k, float(v))
