@@ -74,20 +74,58 @@ struct SmemFieldsAcc {
   }
 };
 
+// Shared-memory sigma/mu plane: five pairs (see sig_pair), pair j of tile site k at
+// elements j * 2 SP + 2 k (+1).  Velocity plane: (u_x, u_y) of site k at 2 k (+1), u_z at
+// 2 SP + k.
+template <int SP>
+__device__ __forceinline__ int uidx(int a, int k) {
+  return a < 2 ? 2 * k + a : 2 * SP + k;
+}
+
+template <typename T>
+__device__ __forceinline__ Vec2<T> lds2(const T* p) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    return Vec2<T>{v.x, v.y};
+  } else {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    return Vec2<T>{v.x, v.y};
+  }
+}
+
 template <typename T, int QW, int QP, int SW, int SP>
 struct SmemUpdateAcc {
   const T* qpl[3];
   const T* spl[3];
   const T* upl[3];
-  int qc;
+  int qc;  // tile index of the centre site in the Q/psi plane
+  int sc;  // ... in the sigma and u planes
   __device__ __forceinline__ T q(int k, int cx, int cy, int cz) const {
     return qpl[cz + 1][qidx<QP>(k, qc + cy * QW + cx)];
   }
   __device__ __forceinline__ T psi(int cx, int cy, int cz) const { return qpl[cz + 1][qidx<QP>(5, qc + cy * QW + cx)]; }
-  __device__ __forceinline__ T sig(int k, int cx, int cy, int cz) const { return spl[cz + 1][k * SP + cy * SW + cx]; }
-  __device__ __forceinline__ T mu(int cx, int cy, int cz) const { return spl[cz + 1][9 * SP + cy * SW + cx]; }
-  __device__ __forceinline__ T u(int a, int cx, int cy, int cz) const { return upl[cz + 1][a * SP + cy * SW + cx]; }
+  __device__ __forceinline__ Vec2<T> spair(int j, int cx, int cy, int cz) const {
+    return lds2(spl[cz + 1] + j * 2 * SP + 2 * (sc + cy * SW + cx));
+  }
+  __device__ __forceinline__ Vec2<T> upair(int cx, int cy, int cz) const {
+    return lds2(upl[cz + 1] + 2 * (sc + cy * SW + cx));
+  }
+  __device__ __forceinline__ T u(int a, int cx, int cy, int cz) const {
+    return upl[cz + 1][uidx<SP>(a, sc + cy * SW + cx)];
+  }
 };
+
+// The stress and mu of tile site k into a sigma plane as five pairs (two-element stores).
+template <typename T, int SP>
+__device__ __forceinline__ void store_sigma(T* plane, int k, const T sig[9], T mu) {
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    T* p = plane + j * 2 * SP + 2 * k;
+    const T a = sig[pair_c0(j)], b = j == 4 ? mu : sig[pair_c1(j)];
+    if constexpr (sizeof(T) == 4) *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    else *reinterpret_cast<double2*>(p) = make_double2(a, b);
+  }
+}
 
 // Ring slots of plane p (p >= -2).
 __device__ __forceinline__ int qslot(int p) { return (p + 10) % 5; }
@@ -172,7 +210,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
         const int sy = k / SW, sx = k - sy * SW;
         const long long gs = gz + ymap[sy + 1] + xmap[sx + 1];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) dst[a * SP + k] = ld(uin + a * N + gs);
+        for (int a = 0; a < 3; ++a) dst[uidx<SP>(a, k)] = ld(uin + a * N + gs);
       }
     };
     int qoff[G::QLD], uoff[G::ULD];
@@ -216,7 +254,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
         if (k < SP) {
           const long long gs = gzu + uoff[j];
 #pragma unroll
-          for (int a = 0; a < 3; ++a) du[a * SP + k] = ld(uin + a * N + gs);
+          for (int a = 0; a < 3; ++a) du[uidx<SP>(a, k)] = ld(uin + a * N + gs);
         }
       }
     };
@@ -230,10 +268,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
       gather_fields<T>(acc, q0, p0, dq, lapq, dp, lapp, hp);
       T sig[9], mu;
       local_fields<T>(cf, q0, p0, dq, lapq, dp, lapp, hp, H, mu, sig);
-      T* dst = sS + sslot(p) * G::SSLOT + sy * SW + sx;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) dst[k * SP] = sig[k];
-      dst[9 * SP] = mu;
+      store_sigma<T, SP>(sS + sslot(p) * G::SSLOT, sy * SW + sx, sig, mu);
     };
 
     load_q_all(zb - 2);
@@ -263,12 +298,12 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
       if (z >= zb && tl.x0 + tx < nx && tl.y0 + ty < ny) {
         SmemUpdateAcc<T, QW, QP, SW, SP> acc;
         acc.qc = (ty + 2) * QW + (tx + 2);
-        const int sc = (ty + 1) * SW + (tx + 1);
+        acc.sc = (ty + 1) * SW + (tx + 1);
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
           acc.qpl[j] = sQ + qslot(z - 1 + j) * G::QSLOT;
-          acc.spl[j] = sS + sslot(z - 1 + j) * G::SSLOT + sc;
-          acc.upl[j] = sU + uslot(z - 1 + j) * G::USLOT + sc;
+          acc.spl[j] = sS + sslot(z - 1 + j) * G::SSLOT;
+          acc.upl[j] = sU + uslot(z - 1 + j) * G::USLOT;
         }
         T F[3], lapmu, Wg[3][3], q0[5], qf[6][5], p0, pf[6], u0[3], uf[6];
         gather_update<T>(acc, F, lapmu, Wg, q0, qf, p0, pf, u0, uf);
@@ -416,10 +451,10 @@ __global__ void __launch_bounds__(512, 1)
     };
     auto issue_u = [&](int p) {
       if (tid < SP) {
-        T* dst = sU + s4(p) * USLOT + tid;
+        T* dst = sU + s4(p) * USLOT;
         const long long gs = (long long)wrapmod(p, nz) * plane + uoff;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) cp_async_elem(dst + a * SP, uin + a * N + gs);
+        for (int a = 0; a < 3; ++a) cp_async_elem(dst + uidx<SP>(a, tid), uin + a * N + gs);
       }
     };
     issue_q(zb - 2);
@@ -444,10 +479,7 @@ __global__ void __launch_bounds__(512, 1)
           gather_fields<T>(acc, q0, p0, dq, lapq, dp, lapp, hp);
           T H[5], sig[9], mu;
           local_fields<T>(cf, q0, p0, dq, lapq, dp, lapp, hp, H, mu, sig);
-          T* dst = sS + s4(k + 1) * SSLOT + sy * SW + sx;
-#pragma unroll
-          for (int c = 0; c < 9; ++c) dst[c * SP] = sig[c];
-          dst[9 * SP] = mu;
+          store_sigma<T, SP>(sS + s4(k + 1) * SSLOT, sy * SW + sx, sig, mu);
           if (sx >= 1 && sx <= TX && sy >= 1 && sy <= G::TY) {
             T* hd = sH + h3(k + 1) * HSLOT + (sy - 1) * TX + (sx - 1);
 #pragma unroll
@@ -464,12 +496,12 @@ __global__ void __launch_bounds__(512, 1)
         if (site < G::IP && tl.x0 + tx < nx && tl.y0 + ty < ny) {
           SmemUpdateAcc<T, QW, QP, SW, SP> acc;
           acc.qc = (ty + 2) * QW + (tx + 2);
-          const int sc = (ty + 1) * SW + (tx + 1);
+          acc.sc = (ty + 1) * SW + (tx + 1);
 #pragma unroll
           for (int j = 0; j < 3; ++j) {
             acc.qpl[j] = sQ + q6(z - 1 + j) * QSLOT;
-            acc.spl[j] = sS + s4(z - 1 + j) * SSLOT + sc;
-            acc.upl[j] = sU + s4(z - 1 + j) * USLOT + sc;
+            acc.spl[j] = sS + s4(z - 1 + j) * SSLOT;
+            acc.upl[j] = sU + s4(z - 1 + j) * USLOT;
           }
           T F[3], lapmu, Wg[3][3], q0[5], qf[6][5], p0, pf[6], u0[3], uf[6];
           gather_update<T>(acc, F, lapmu, Wg, q0, qf, p0, pf, u0, uf);

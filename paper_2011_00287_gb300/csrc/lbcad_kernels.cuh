@@ -129,6 +129,26 @@ __device__ __forceinline__ Vec2<float> fma2(Vec2<float> a, Vec2<float> b, Vec2<f
 template <>
 __device__ __forceinline__ Vec2<float> mul2(Vec2<float> a, Vec2<float> b) { return v2f(__fmul2_rn(f2(a), f2(b))); }
 
+// Gradient (1/12)[2 D_face + signed edge pairs] from opposite-pair differences D[i] =
+// f(c_i) - f(c_{i+1}), two fields at once.
+template <typename T>
+__device__ __forceinline__ void grad2_from_pairs(const Vec2<T> D[19], Vec2<T> g[3]) {
+  const Vec2<T> k2 = v2(T(2), T(2)), k12 = v2(T(1.0 / 12.0), T(1.0 / 12.0));
+  g[0] = mul2(fma2(D[1], k2, add2(add2(D[7], D[9]), add2(D[11], D[13]))), k12);
+  g[1] = mul2(fma2(D[3], k2, add2(sub2(D[7], D[9]), add2(D[15], D[17]))), k12);
+  g[2] = mul2(fma2(D[5], k2, add2(sub2(D[11], D[13]), sub2(D[15], D[17]))), k12);
+}
+
+// Stress and chemical potential as five pairs, the unit of the tiles in shared memory:
+// pair j of a site holds (sigma_xb, sigma_yb) for j = b = 0, 1, 2, (sigma_zx, sigma_zy) for
+// j = 3 and (sigma_zz, mu) for j = 4.  sig_pair(c) = j and sig_lane(c) = lane of sigma_c
+// (c = 3a + b); mu sits in pair 4, lane 1.
+__host__ __device__ constexpr int sig_pair(int c) { return c < 6 ? c % 3 : (c < 8 ? 3 : 4); }
+__host__ __device__ constexpr int sig_lane(int c) { return c < 6 ? c / 3 : (c < 8 ? c - 6 : 0); }
+// the two stress components of pair j (the second is -1 for mu)
+__host__ __device__ constexpr int pair_c0(int j) { return j < 3 ? j : (j == 3 ? 6 : 8); }
+__host__ __device__ constexpr int pair_c1(int j) { return j < 3 ? j + 3 : (j == 3 ? 7 : -1); }
+
 // H (5), mu and the total stress sigma (9, row-major a*3+b) at one site from Q, psi and
 // their stencils: dq[a][k] = d_a of stored component k, lapq[k], dp[a] = d_a psi,
 // lapp, hp = Hessian of psi (xx, yy, zz, xy, xz, yz).
@@ -296,7 +316,7 @@ template <typename T, class A>
 __device__ __forceinline__ void gather_fields(const A& acc, T q0[5], T& p0, T dq[3][5], T lapq[5], T dp[3],
                                               T& lapp, T hp[6]) {
   using V = Vec2<T>;
-  const V k2 = v2(T(2), T(2)), k12 = v2(T(1.0 / 12.0), T(1.0 / 12.0)), k6 = v2(T(1.0 / 6.0), T(1.0 / 6.0));
+  const V k2 = v2(T(2), T(2)), k6 = v2(T(1.0 / 6.0), T(1.0 / 6.0));
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     V f[19];
@@ -307,11 +327,8 @@ __device__ __forceinline__ void gather_fields(const A& acc, T q0[5], T& p0, T dq
     for (int i = 1; i < 19; ++i) d[i] = sub2(f[i], f[0]);
 #pragma unroll
     for (int i = 1; i < 19; i += 2) D[i] = sub2(d[i], d[i + 1]);
-    // gradient from opposite pairs: (1/12)[2 D_face + sum of signed edge pairs]
     V g[3];
-    g[0] = mul2(fma2(D[1], k2, add2(add2(D[7], D[9]), add2(D[11], D[13]))), k12);
-    g[1] = mul2(fma2(D[3], k2, add2(sub2(D[7], D[9]), add2(D[15], D[17]))), k12);
-    g[2] = mul2(fma2(D[5], k2, add2(sub2(D[11], D[13]), sub2(D[15], D[17]))), k12);
+    grad2_from_pairs<T>(D, g);
     // Laplacian from differences to the centre: (1/3) faces + (1/6) edges
     const V sf = add2(add2(add2(d[1], d[2]), add2(d[3], d[4])), add2(d[5], d[6]));
     const V se = add2(add2(add2(add2(d[7], d[8]), add2(d[9], d[10])), add2(add2(d[11], d[12]), add2(d[13], d[14]))),
@@ -342,28 +359,51 @@ __device__ __forceinline__ void gather_fields(const A& acc, T q0[5], T& p0, T dq
   }
 }
 
-// a3 (divergence): F_a = d_b sigma_ab from opposite-pair differences of sigma.
+// a3 (divergence): F_a = d_b sigma_ab from opposite-pair differences of sigma, through the
+// stress pairs A::spair(j, ...): (F_x, F_y) from pairs 0-2 two lanes at a time, F_z from
+// pair 3 (sigma_zx, sigma_zy) and lane 0 of pair 4 (sigma_zz).
 template <typename T, class A>
 __device__ __forceinline__ void gather_force(const A& acc, T F[3]) {
-  // F_a = d_x sigma_ax + d_y sigma_ay + d_z sigma_az
+  using V = Vec2<T>;
+  V a2 = v2(T(0), T(0)), a1 = v2(T(0), T(0));
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    T acc2 = T(0), acc1 = T(0);
+  for (int b = 0; b < 3; ++b) {
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const int k = 3 * a + b;
+    for (int i = 1; i < 19; i += 2) {
+      const int cb = lat_c(i, b);
+      if (cb == 0) continue;
+      const V D = sub2(acc.spair(b, lat_c(i, 0), lat_c(i, 1), lat_c(i, 2)),
+                       acc.spair(b, lat_c(i + 1, 0), lat_c(i + 1, 1), lat_c(i + 1, 2)));
+      if (lat_c2(i) == 1) a2 = cb > 0 ? add2(a2, D) : sub2(a2, D);
+      else a1 = cb > 0 ? add2(a1, D) : sub2(a1, D);
+    }
+  }
+  const V fxy = mul2(fma2(a2, v2(T(2), T(2)), a1), v2(T(1.0 / 12.0), T(1.0 / 12.0)));
+  F[0] = fxy.x;
+  F[1] = fxy.y;
+  T z2 = T(0), z1 = T(0);
 #pragma unroll
-      for (int i = 1; i < 19; i += 2) {
-        const int cb = lat_c(i, b);
-        if (cb == 0) continue;
-        const T Di = acc.sig(k, lat_c(i, 0), lat_c(i, 1), lat_c(i, 2)) -
-                     acc.sig(k, lat_c(i + 1, 0), lat_c(i + 1, 1), lat_c(i + 1, 2));
-        if (lat_c2(i) == 1) acc2 += (cb > 0 ? Di : -Di);
-        else acc1 += (cb > 0 ? Di : -Di);
+  for (int i = 1; i < 19; i += 2) {
+    const int cx = lat_c(i, 0), cy = lat_c(i, 1), cz = lat_c(i, 2);
+    const bool face = lat_c2(i) == 1;
+    if (cx || cy) {
+      const V D = sub2(acc.spair(3, cx, cy, cz), acc.spair(3, -cx, -cy, -cz));
+      if (cx) {
+        const T d = cx > 0 ? D.x : -D.x;
+        if (face) z2 += d; else z1 += d;
+      }
+      if (cy) {
+        const T d = cy > 0 ? D.y : -D.y;
+        if (face) z2 += d; else z1 += d;
       }
     }
-    F[a] = (T(2) * acc2 + acc1) * T(1.0 / 12.0);
+    if (cz) {
+      const T Dz = acc.spair(4, cx, cy, cz).x - acc.spair(4, -cx, -cy, -cz).x;
+      const T d = cz > 0 ? Dz : -Dz;
+      if (face) z2 += d; else z1 += d;
+    }
   }
+  F[2] = (T(2) * z2 + z1) * T(1.0 / 12.0);
 }
 
 // The stencils of a4: lap mu, W_ab = d_b u_a, and the face values of Q, psi and u for the
@@ -371,26 +411,45 @@ __device__ __forceinline__ void gather_force(const A& acc, T F[3]) {
 template <typename T, class A>
 __device__ __forceinline__ void gather_op(const A& acc, T& lapmu, T Wg[3][3], T q0[5], T qf[6][5], T& p0, T pf[6],
                                           T u0[3], T uf[6]) {
-  // lap mu
+  // lap mu (lane 1 of stress pair 4, so that the loads are shared with the force)
   {
     T d[19];
-    const T m0 = acc.mu(0, 0, 0);
+    const T m0 = acc.spair(4, 0, 0, 0).y;
 #pragma unroll
-    for (int i = 1; i < 19; ++i) d[i] = acc.mu(lat_c(i, 0), lat_c(i, 1), lat_c(i, 2)) - m0;
+    for (int i = 1; i < 19; ++i) d[i] = acc.spair(4, lat_c(i, 0), lat_c(i, 1), lat_c(i, 2)).y - m0;
     lapmu = lap_from_diffs(d);
   }
-  // grad u and the axial face velocities
+  // grad u and the axial face velocities: (u_x, u_y) as pairs, u_z alone
+  {
+    using V = Vec2<T>;
+    V f[19], D[19], g[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
+    for (int i = 0; i < 19; ++i) f[i] = acc.upair(lat_c(i, 0), lat_c(i, 1), lat_c(i, 2));
+#pragma unroll
+    for (int i = 1; i < 19; i += 2) D[i] = sub2(f[i], f[i + 1]);
+    grad2_from_pairs<T>(D, g);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      Wg[0][b] = g[b].x;
+      Wg[1][b] = g[b].y;
+    }
+    u0[0] = f[0].x;
+    u0[1] = f[0].y;
+    uf[0] = f[1].x;
+    uf[1] = f[2].x;
+    uf[2] = f[3].y;
+    uf[3] = f[4].y;
+  }
+  {
     T f[19], D[19];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) f[i] = acc.u(a, lat_c(i, 0), lat_c(i, 1), lat_c(i, 2));
+    for (int i = 0; i < 19; ++i) f[i] = acc.u(2, lat_c(i, 0), lat_c(i, 1), lat_c(i, 2));
 #pragma unroll
     for (int i = 1; i < 19; i += 2) D[i] = f[i] - f[i + 1];
-    grad_from_pairs(D, Wg[a]);
-    u0[a] = f[0];
-    uf[2 * a] = f[1 + 2 * a];
-    uf[2 * a + 1] = f[2 + 2 * a];
+    grad_from_pairs(D, Wg[2]);
+    u0[2] = f[0];
+    uf[4] = f[5];
+    uf[5] = f[6];
   }
 #pragma unroll
   for (int i = 1; i < 7; ++i) {
@@ -610,6 +669,15 @@ struct GlobalAcc {
     const long long o = nb.off(cx, cy, cz);
     return Vec2<T>{ld(q_ + (2 * j) * N + o), j < 2 ? ld(q_ + (2 * j + 1) * N + o) : ld(ps + o)};
   }
+  // stress pair j (see sig_pair) and the velocity pair (u_x, u_y)
+  __device__ __forceinline__ Vec2<T> spair(int j, int cx, int cy, int cz) const {
+    const long long o = nb.off(cx, cy, cz);
+    return Vec2<T>{ld(sg + pair_c0(j) * N + o), j == 4 ? ld(mu_ + o) : ld(sg + pair_c1(j) * N + o)};
+  }
+  __device__ __forceinline__ Vec2<T> upair(int cx, int cy, int cz) const {
+    const long long o = nb.off(cx, cy, cz);
+    return Vec2<T>{ld(u_ + o), ld(u_ + N + o)};
+  }
 };
 
 // ---------------------------------------------------------------- radius-2 stencils
@@ -794,6 +862,11 @@ struct AntiSigAcc {
     if (a == b) return T(0);
     const long long o = nb.off(cx, cy, cz);
     return T(0.5) * (ld(sg + k * N + o) - ld(sg + (3 * b + a) * N + o));
+  }
+  // pair 4 holds sigma^A_zz = 0 (and no mu: the force does not read lane 1)
+  __device__ __forceinline__ Vec2<T> spair(int j, int cx, int cy, int cz) const {
+    if (j == 4) return Vec2<T>{T(0), T(0)};
+    return Vec2<T>{sig(pair_c0(j), cx, cy, cz), sig(pair_c1(j), cx, cy, cz)};
   }
 };
 
