@@ -250,6 +250,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-staged", action="store_true", help="skip the Heun / sync staged-path leg")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg (64^3, 500 steps)")
     ap.add_argument("--workload", default="droplet", choices=["droplet", "batch64"],
                     help="droplet: the 128^3 benchmark line; batch64: 64 uneven droplets in one launch")
     args = ap.parse_args()
@@ -327,6 +328,30 @@ def main():
                 "workload": "bulk active nematic %d^3, psi = 1, zeta = 0.008 (spontaneous-flow regime)" % n}
         sb.close()
 
+    # adjoint of J = |centroid drift|^2 / 2 over 500 steps of a 64^3 droplet (R = 16, pitch 16),
+    # checkpoints every 50 steps: wall time of the whole gradient against the forward run alone
+    adjoint = None
+    if not args.no_adjoint:
+        na = 64
+        pa = L.default_params((na, na, na), R=16.0, p0=16.0, precision=L.FP32, zeta=0.005)
+        sf = L.Simulation([(na, na, na)], [pa], seed=1 + rank, device=local)
+        sf.step(5)
+        sf.sync()
+        t0 = time.perf_counter()
+        sf.step(500)
+        sf.sync()
+        t_fwd = time.perf_counter() - t0
+        sf.close()
+        sa = L.Simulation([(na, na, na)], [pa], seed=1 + rank, device=local)
+        sa.adjoint(20, 10)  # warm-up (allocations)
+        t0 = time.perf_counter()
+        Ja, dz, dq, _ = sa.adjoint(500, 50)
+        t_adj = time.perf_counter() - t0
+        sa.close()
+        adjoint = {"workload": "droplet 64^3, R = 16, pitch 16, 500 steps, checkpoints every 50, FP32",
+                   "seconds": t_adj, "forward_seconds": t_fwd, "ratio_to_forward": t_adj / t_fwd,
+                   "site_steps_per_s": na ** 3 * 500 / t_adj, "dJ_dzeta": dz, "finite": bool(math.isfinite(dz))}
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -392,7 +417,7 @@ def main():
                            "l2": "state %.0f MB per step > 129 MB L2, no flush" % (224 * N / 1e6)},
                 "roofline": roofline, "roofline_issue": roofline_issue, "cpu_baseline": cpu, "e2e": e2e,
                 "tiles": {"chosen": TILE_NAMES[tile_cfg], "ms_per_cfg": dict(zip(TILE_NAMES, tile_ms))},
-                "gpu_launches": K, "clocks": csum, "fp64_gpu": fp64, "staged_fp32": staged, "bulk_fp32": bulk,
+                "gpu_launches": K, "clocks": csum, "fp64_gpu": fp64, "staged_fp32": staged, "bulk_fp32": bulk, "adjoint_fp32": adjoint,
                 "speedup_fp32_vs_fp64": (value / world / fp64["mlups"]) if fp64 else None,
                 "observables_finite": finite}
         print(json.dumps(line))
