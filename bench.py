@@ -245,7 +245,7 @@ def main():
     ap.add_argument("--impl", default="lbcad", choices=["lbcad", "reference"])
     ap.add_argument("--size", type=int, default=128)
     ap.add_argument("--fp64-steps", type=int, default=10)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -352,33 +352,28 @@ def main():
                    "seconds": t_adj, "forward_seconds": t_fwd, "ratio_to_forward": t_adj / t_fwd,
                    "site_steps_per_s": na ** 3 * 500 / t_adj, "dJ_dzeta": dz, "finite": bool(math.isfinite(dz))}
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: every step sets the whole state
+    # from pinned host memory (lbcad_set_state, the storage precision), advances one step and
+    # reads the whole state back (lbcad_get_state)
     e2e = None
     if not args.no_e2e:
-        mask = L.FIELD_G | L.FIELD_U | L.FIELD_Q | L.FIELD_PSI
-        host = torch.empty(28 * N, dtype=torch.float64).pin_memory()
-        got = sim.get_fields(0, mask, out=host)
-        state = {k: v for k, v in got.items()}
-        state_np = {k: v.numpy().copy() for k, v in state.items()}
-        pinned_in = torch.empty(28 * N, dtype=torch.float64).pin_memory()
-        o = 0
-        for k, c in (("g", 19), ("u", 3), ("q", 5), ("psi", 1)):
-            pinned_in[o * N:(o + c) * N] = torch.from_numpy(state_np[k].reshape(-1))
-            o += c
-        lib = L.library()
-        import ctypes
+        nb = sim.state_bytes(0)
+        host_in = torch.empty(nb, dtype=torch.uint8).pin_memory()
+        host_out = torch.empty(nb, dtype=torch.uint8).pin_memory()
+        sim.get_state(0, out=host_in)
+        sim.set_state(0, host_in)
+        sim.step(1)
+        sim.get_state(0, out=host_out)
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            rc = lib.lbcad_set_fields(sim.ctx, 0, mask, ctypes.c_void_p(pinned_in.data_ptr()), 28 * N * 8, 0)
-            assert rc == 0
+            sim.set_state(0, host_in)
             sim.step(1)
-            rc = lib.lbcad_get_fields(sim.ctx, 0, mask, ctypes.c_void_p(host.data_ptr()), 28 * N * 8, 0)
-            assert rc == 0
+            sim.get_state(0, out=host_out)
         el = time.perf_counter() - t0
-        e2e = {"value": N * args.e2e_steps / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 28 * N * 8,
-               "d2h_bytes_per_step": 28 * N * 8,
-               "note": "per step: full state (g, u, Q, psi as FP64) set from pinned host memory, one step, "
-                       "full state read back to pinned host memory"}
+        e2e = {"value": N * args.e2e_steps / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb,
+               "note": "per step: whole state (populations, Q, psi, u in the storage precision, FP32) set from "
+                       "pinned host memory, one step, whole state read back to pinned host memory"}
 
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_SITE["fp32"] * N / (ms * 1e-3) / 1e9

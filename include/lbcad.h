@@ -208,6 +208,19 @@ int lbcad_set_fields(lbcad_ctx* c, int32_t inst, uint32_t mask, const void* src,
  * reduced value is not finite.  Synchronises the context's stream. */
 int lbcad_observables(lbcad_ctx* c, int32_t inst, lbcad_obs* out);
 
+/* Raw state of instance `inst` in the context's storage precision (float for LBCAD_FP32,
+ * double for LBCAD_FP64), for exact checkpoints and for moving the state without
+ * conversion.  The layout is the library's own: the stored population array ([q][n], the
+ * post-collision values of the previous step at their source sites; FP32 subtracts
+ * w_i rho0), then Q [5][n], psi [n] and u [3][n], each [z][y][x].  lbcad_set_state of what
+ * lbcad_get_state returned restores the instance bit for bit (the step counter is not part
+ * of the state).  *bytes receives (q + 9) n times the element size.  dst/src are host
+ * pointers (pageable or pinned) unless *_is_device; the copies run on the context's stream,
+ * and both calls synchronise it before returning. */
+int lbcad_state_bytes(lbcad_ctx* c, int32_t inst, size_t* bytes);
+int lbcad_get_state(lbcad_ctx* c, int32_t inst, void* dst, size_t bytes, int32_t dst_is_device);
+int lbcad_set_state(lbcad_ctx* c, int32_t inst, const void* src, size_t bytes, int32_t src_is_device);
+
 /* Adjoint (reverse mode) of nsteps hybrid steps of a single-instance context.
  * Objective: J = |X(t0 + nsteps) - X(t0)|^2 / 2, X the droplet centroid (per-axis circular
  * mean of phi_c = (1 + psi)/2, minimum-image displacement), t0 the current step.

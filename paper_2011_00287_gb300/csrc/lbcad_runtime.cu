@@ -687,6 +687,50 @@ int lbcad_set_fields(lbcad_ctx* c, int32_t inst, uint32_t mask, const void* src,
   return LBCAD_OK;
 }
 
+int lbcad_state_bytes(lbcad_ctx* c, int32_t inst, size_t* bytes) {
+  if (!c || !bytes) return LBCAD_E_INVALID_ARG;
+  if (inst < 0 || inst >= (int)c->inst.size()) return fail(c, LBCAD_E_INVALID_ARG, "instance out of range");
+  *bytes = (size_t)(c->q() + 9) * (size_t)c->inst[inst].N * c->elem();
+  return LBCAD_OK;
+}
+
+namespace {
+// Copies the current-parity state buffers of one instance to/from a contiguous buffer.
+int copy_state(lbcad_ctx* c, int inst, void* ext, size_t bytes, bool ext_is_device, bool to_ext) {
+  if (inst < 0 || inst >= (int)c->inst.size()) return fail(c, LBCAD_E_INVALID_ARG, "instance out of range");
+  size_t need = 0;
+  lbcad_state_bytes(c, inst, &need);
+  if (!ext || bytes < need) return fail(c, LBCAD_E_INVALID_ARG, "state buffer missing or too small");
+  DeviceGuard dg(c->device);
+  Inst& I = c->inst[inst];
+  const int par = (int)(c->step & 1);
+  const size_t es = c->elem(), N = (size_t)I.N;
+  void* parts[4] = {I.gb[par], I.qb[par], I.pb[par], I.ub[par]};
+  const size_t sizes[4] = {(size_t)c->q() * N * es, 5 * N * es, N * es, 3 * N * es};
+  const cudaMemcpyKind kind = to_ext ? (ext_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost)
+                                     : (ext_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+  size_t off = 0;
+  for (int k = 0; k < 4; ++k) {
+    char* e = (char*)ext + off;
+    if (to_ext) CK(c, cudaMemcpyAsync(e, parts[k], sizes[k], kind, c->stream));
+    else CK(c, cudaMemcpyAsync(parts[k], e, sizes[k], kind, c->stream));
+    off += sizes[k];
+  }
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LBCAD_OK;
+}
+}  // namespace
+
+int lbcad_get_state(lbcad_ctx* c, int32_t inst, void* dst, size_t bytes, int32_t dst_is_device) {
+  if (!c) return LBCAD_E_INVALID_ARG;
+  return copy_state(c, inst, dst, bytes, dst_is_device != 0, true);
+}
+
+int lbcad_set_state(lbcad_ctx* c, int32_t inst, const void* src, size_t bytes, int32_t src_is_device) {
+  if (!c) return LBCAD_E_INVALID_ARG;
+  return copy_state(c, inst, const_cast<void*>(src), bytes, src_is_device != 0, false);
+}
+
 int lbcad_observables(lbcad_ctx* c, int32_t inst, lbcad_obs* out) {
   if (!c || !out) return LBCAD_E_INVALID_ARG;
   if (inst < 0 || inst >= (int)c->inst.size()) return fail(c, LBCAD_E_INVALID_ARG, "instance out of range");

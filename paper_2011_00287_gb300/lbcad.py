@@ -75,6 +75,11 @@ _P = ctypes.POINTER
 _SIGS = {
     "lbcad_lattice": (ctypes.c_int, [_P(ctypes.c_int32), _P(ctypes.c_double)]),
     "lbcad_velocity_set": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_int32), _P(ctypes.c_double)]),
+    "lbcad_state_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _P(ctypes.c_size_t)]),
+    "lbcad_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
+                                       ctypes.c_int32]),
+    "lbcad_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
+                                       ctypes.c_int32]),
     "lbcad_create": (ctypes.c_int, [_P(lbcad_grid), _P(lbcad_params), ctypes.c_uint64, _P(ctypes.c_void_p)]),
     "lbcad_create_batch": (ctypes.c_int, [ctypes.c_int32, _P(lbcad_grid), _P(lbcad_params), ctypes.c_uint64,
                                           _P(ctypes.c_void_p)]),
@@ -395,6 +400,31 @@ class Simulation:
                 res[FIELD_NAMES[b]] = v[0] if b == FIELD_PSI else v
                 o += c
         return res
+
+    def state_bytes(self, inst: int = 0) -> int:
+        n = ctypes.c_size_t()
+        _check(library().lbcad_state_bytes(self.ctx, inst, ctypes.byref(n)), self.ctx)
+        return n.value
+
+    def get_state(self, inst: int = 0, out=None):
+        """Raw state in the storage precision (exact checkpoint): a uint8 numpy array, or
+        `out` (a host or CUDA tensor/array of at least state_bytes bytes) filled in place."""
+        n = self.state_bytes(inst)
+        buf = out if out is not None else np.empty(n, dtype=np.uint8)
+        on_dev = hasattr(buf, "is_cuda") and buf.is_cuda
+        ptr = buf.data_ptr() if hasattr(buf, "data_ptr") else buf.ctypes.data
+        _check(library().lbcad_get_state(self.ctx, inst, ctypes.c_void_p(ptr), n, 1 if on_dev else 0), self.ctx)
+        return buf
+
+    def set_state(self, inst: int, buf):
+        """Restore a state returned by get_state (bit for bit)."""
+        n = self.state_bytes(inst)
+        on_dev = hasattr(buf, "is_cuda") and buf.is_cuda
+        ptr = buf.data_ptr() if hasattr(buf, "data_ptr") else buf.ctypes.data
+        size = buf.nbytes if hasattr(buf, "nbytes") else buf.numel() * buf.element_size()
+        if size < n:
+            raise ValueError("state buffer too small")
+        _check(library().lbcad_set_state(self.ctx, inst, ctypes.c_void_p(ptr), n, 1 if on_dev else 0), self.ctx)
 
     def observables(self, inst: int = 0) -> np.ndarray:
         o = lbcad_obs()

@@ -277,3 +277,28 @@ def test_tile_shapes_and_autotune_give_identical_results():
     f = s.get_fields(0)
     for k in fr:
         assert np.array_equal(f[k], fr[k]), k
+
+
+@pytest.mark.parametrize("prec", [L.FP32, L.FP64])
+def test_raw_state_checkpoint_restores_bit_for_bit(prec):
+    """lbcad_get_state / lbcad_set_state: an exact checkpoint in the storage precision, through
+    host memory and through a device buffer."""
+    import torch
+    shape = (20, 12, 10)
+    kw = dict(R=4.0, p0=8.0, zeta=0.01)
+    sim = L.Simulation([shape], [_lib_params(shape, prec, **kw)], seed=7)
+    sim.step(3)
+    n = sim.state_bytes(0)
+    assert n == (19 + 9) * 20 * 12 * 10 * (8 if prec == L.FP64 else 4)
+    host = sim.get_state(0)
+    dev = sim.get_state(0, out=torch.empty(n, dtype=torch.uint8, device="cuda"))
+    sim.step(5)
+    ref = sim.get_fields(0)
+    for src in (host, dev):
+        sim.set_state(0, src)
+        sim.step(5)
+        got = sim.get_fields(0)
+        for k in ref:
+            assert np.array_equal(got[k], ref[k]), k
+    with pytest.raises(ValueError):
+        sim.set_state(0, host[:10])
