@@ -83,3 +83,33 @@ def test_null_arguments(lib):
     assert lib.lbcad_step_count(None) == -1
     lib.lbcad_destroy(None)
     assert lib.lbcad_lattice(None, None) == L.LBCAD_E_INVALID_ARG
+
+
+def test_null_arguments_of_the_exchange_and_option_calls(lib):
+    n = ctypes.c_size_t()
+    assert lib.lbcad_state_bytes(None, 0, ctypes.byref(n)) == L.LBCAD_E_INVALID_ARG
+    assert lib.lbcad_get_state(None, 0, None, 0, 0) == L.LBCAD_E_INVALID_ARG
+    assert lib.lbcad_set_state(None, 0, None, 0, 0) == L.LBCAD_E_INVALID_ARG
+    assert lib.lbcad_set_path(None, 0) == L.LBCAD_E_INVALID_ARG
+    assert lib.lbcad_set_tiles(None, 0) == L.LBCAD_E_INVALID_ARG
+    assert lib.lbcad_autotune(None, 1, None, None, 0) == L.LBCAD_E_INVALID_ARG
+
+
+@pytest.mark.parametrize("code,q", [(L.D3Q19, 19), (L.D3Q15, 15)])
+def test_velocity_sets_on_the_host(lib, code, q):
+    """lbcad_velocity_set needs no GPU: the tables, their isotropy, and rejection of an
+    unknown set."""
+    import numpy as np
+    c, w = L.lattice(code)
+    assert c.shape == (q, 3) and abs(w.sum() - 1.0) < 1e-15
+    cf = c.astype(float)
+    assert np.allclose((w[:, None, None] * cf[:, :, None] * cf[:, None, :]).sum(0), np.eye(3) / 3)
+    cc = (ctypes.c_int32 * 57)()
+    ww = (ctypes.c_double * 19)()
+    assert lib.lbcad_velocity_set(7, cc, ww) == L.LBCAD_E_INVALID_ARG
+
+
+@pytest.mark.parametrize("kw", [dict(lattice=7), dict(lb_form=3), dict(stencil=2)])
+def test_create_rejects_unknown_scheme_options_on_the_host(lib, kw):
+    got, msg = _create(lib, (8, 8, 8), **kw)
+    assert got == L.LBCAD_E_INVALID_ARG and msg
