@@ -48,9 +48,9 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def committed_profile_value(key):
-    """A per-site figure ('key: value ...') from the committed ncu summary of the step."""
-    p = os.path.join(ROOT, "profiles", "lbcad_step_fp32_128cube.md")
+def committed_profile_value(key, name="lbcad_step_fp32_128cube.md"):
+    """A figure ('key: value ...') from a committed ncu summary of the step."""
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     for line in open(p):
@@ -300,6 +300,15 @@ def main():
         s64.step(3)
         ms64 = time_steps(s64, torch, args.fp64_steps)
         fp64 = {"mlups": N / (ms64 * 1e-3) / 1e6, "ms_per_step": ms64, "steps": args.fp64_steps}
+        # bound by the FP64 pipe: flops per site from the committed ncu counters, peak the
+        # nominal FP64 rate of the part (1.25 TFLOP/s)
+        fl = committed_profile_value("fp64_flops_per_site", "lbcad_step_fp64_128cube.md")
+        if fl:
+            ach = fl * N / (ms64 * 1e-3) / 1e12
+            fp64["roofline"] = {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
+                                "peak_kind": "nominal FP64 rate", "flops_per_site": fl,
+                                "fp64_pipe_active_pct": committed_profile_value(
+                                    "fp64_pipe_active_pct", "lbcad_step_fp64_128cube.md")}
         s64.close()
 
     # the staged path (Sec. 3 predictor-corrector and sync coupling) on the same workload
@@ -381,7 +390,11 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (traffic_site * N) if traffic_site else None,
                 "kernel": "k_step_fused (one launch = one whole hybrid step)", "algorithmic_bytes_per_site": 200,
-                "peak_kind": peak_kind}
+                "peak_kind": peak_kind,
+                # the design floor also moves u in and out (224 B per site)
+                "design_bytes_per_site": 224, "design_frac": 224 * N / (ms * 1e-3) / 1e9 / peak,
+                "ncu_dram_throughput_pct": committed_profile_value("dram_throughput_pct"),
+                "ncu_fma_pipe_active_pct": committed_profile_value("fma_pipe_active_pct")}
 
     # the bound the step actually meets: warp-instruction issue (one per cycle per SM
     # sub-partition, 4 per SM, 152 SMs) at the SM clock sampled during the timed region
