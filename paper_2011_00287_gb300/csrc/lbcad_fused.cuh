@@ -41,6 +41,10 @@ struct FusedGeom {
   static constexpr int ULD = (SP + NLOAD - 1) / NLOAD;
 };
 
+// Periodic plane index for p in [-n, 2n): the planes a column segment touches lie in
+// [-2, nz + 3] and every edge is >= 4, so one add or subtract suffices (no division).
+__device__ __forceinline__ int wrap_plane(int p, int n) { return p < 0 ? p + n : (p >= n ? p - n : p); }
+
 __device__ __forceinline__ int wrapmod(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
@@ -194,7 +198,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
     // global offsets are computed once per segment
     auto load_q_all = [&](int p) {  // every thread (prologue)
       T* dst = sQ + qslot(p) * G::QSLOT;
-      const long long gz = (long long)wrapmod(p, nz) * plane;
+      const long long gz = (long long)wrap_plane(p, nz) * plane;
       for (int k = tid; k < QP; k += NT) {
         const int ly = k / QW, lx = k - ly * QW;
         const long long gs = gz + ymap[ly] + xmap[lx];
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
     };
     auto load_u_all = [&](int p) {
       T* dst = sU + uslot(p) * G::USLOT;
-      const long long gz = (long long)wrapmod(p, nz) * plane;
+      const long long gz = (long long)wrap_plane(p, nz) * plane;
       for (int k = tid; k < SP; k += NT) {
         const int sy = k / SW, sx = k - sy * SW;
         const long long gs = gz + ymap[sy + 1] + xmap[sx + 1];
@@ -235,7 +239,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
     // prefetch by the loader threads: Q/psi plane pq and u plane pu
     auto prefetch = [&](int pq, int pu) {
       T* dq = sQ + qslot(pq) * G::QSLOT;
-      const long long gzq = (long long)wrapmod(pq, nz) * plane;
+      const long long gzq = (long long)wrap_plane(pq, nz) * plane;
 #pragma unroll
       for (int j = 0; j < G::QLD; ++j) {
         const int k = lt + j * G::NLOAD;
@@ -247,7 +251,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
         }
       }
       T* du = sU + uslot(pu) * G::USLOT;
-      const long long gzu = (long long)wrapmod(pu, nz) * plane;
+      const long long gzu = (long long)wrap_plane(pu, nz) * plane;
 #pragma unroll
       for (int j = 0; j < G::ULD; ++j) {
         const int k = lt + j * G::NLOAD;
@@ -307,8 +311,8 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
         }
         T F[3], lapmu, Wg[3][3], q0[5], qf[6][5], p0, pf[6], u0[3], uf[6];
         gather_update<T>(acc, F, lapmu, Wg, q0, qf, p0, pf, u0, uf);
-        const long long zo[3] = {(long long)wrapmod(z - 1, nz) * plane, (long long)z * plane,
-                                 (long long)wrapmod(z + 1, nz) * plane};
+        const long long zo[3] = {(long long)wrap_plane(z - 1, nz) * plane, (long long)z * plane,
+                                 (long long)wrap_plane(z + 1, nz) * plane};
         // in-plane offsets of this thread's output site and its x, y neighbours (pull)
         const int pxo[3] = {xmap[tx + 1], xmap[tx + 2], xmap[tx + 3]};
         const int pyo[3] = {ymap[ty + 1], ymap[ty + 2], ymap[ty + 3]};
@@ -443,7 +447,7 @@ __global__ void __launch_bounds__(512, 1)
     auto issue_q = [&](int p) {
       if (tid < QP) {
         T* dst = sQ + q6(p) * QSLOT;
-        const long long gs = (long long)wrapmod(p, nz) * plane + qoff;
+        const long long gs = (long long)wrap_plane(p, nz) * plane + qoff;
 #pragma unroll
         for (int f = 0; f < 5; ++f) cp_async_elem(dst + qidx<QP>(f, tid), qin + f * N + gs);
         cp_async_elem(dst + qidx<QP>(5, tid), pin + gs);
@@ -452,7 +456,7 @@ __global__ void __launch_bounds__(512, 1)
     auto issue_u = [&](int p) {
       if (tid < SP) {
         T* dst = sU + s4(p) * USLOT;
-        const long long gs = (long long)wrapmod(p, nz) * plane + uoff;
+        const long long gs = (long long)wrap_plane(p, nz) * plane + uoff;
 #pragma unroll
         for (int a = 0; a < 3; ++a) cp_async_elem(dst + uidx<SP>(a, tid), uin + a * N + gs);
       }
@@ -489,8 +493,8 @@ __global__ void __launch_bounds__(512, 1)
       } else if (k - 1 >= zb) {
         // output of plane z = k-1
         const int z = k - 1;
-        const long long zo[3] = {(long long)wrapmod(z - 1, nz) * plane, (long long)z * plane,
-                                 (long long)wrapmod(z + 1, nz) * plane};
+        const long long zo[3] = {(long long)wrap_plane(z - 1, nz) * plane, (long long)z * plane,
+                                 (long long)wrap_plane(z + 1, nz) * plane};
         const int site = tid - G::NS;
         const int tx = site % TX, ty = site / TX;
         if (site < G::IP && tl.x0 + tx < nx && tl.y0 + ty < ny) {
