@@ -4,14 +4,15 @@
 // lam_{t+1} of s_{t+1}, four gather-form kernels produce lam_t:
 //   RK1 k_adj_update : per site, VJP of update_math (upwind/co-rotation Q update,
 //                      Cahn-Hilliard psi update, BGK + Guo collision) with respect to its
-//                      88 inputs (F, lap mu, grad u, Q and psi faces, u faces, H, pulled g)
+//                      88 inputs (F, lap mu, grad u, Q and psi faces, u faces, H, pulled g),
+//                      by a hand-written reverse sweep (update_math_vjp)
 //   RK2 k_adj_spread : transposes of the stencils that fed update_math: div sigma -> sigma,
 //                      lap mu -> mu, grad u -> u, face reads -> Q/psi/u, the pull -> g*
 //   RK3 k_adj_fields : per site, VJP of local_fields (H, mu, sigma of Eqs. 2-5) with respect
 //                      to its 36 inputs (Q, psi and their stencils) and to zeta and q0
 //   RK4 k_adj_gather : transposes of the Q/psi stencils (gradient, Laplacian, Hessian)
-// The per-site VJPs run the forward device functions on dual numbers carrying K tangents
-// (forward mode, K input directions per pass), so they differentiate exactly the
+// The VJP of local_fields runs the forward device function on dual numbers carrying K
+// tangents (forward mode, K input directions per pass), so it differentiates exactly the
 // arithmetic the step executes.  Stencil transposes use the negated offsets on the
 // periodic lattice, so no site is written by two threads.
 #pragma once
@@ -117,8 +118,243 @@ struct AdjDesc {
 
 constexpr int kAdjBlock = 128;
 
+// ---------------------------------------------------------------- reverse mode of update_math
+// Vector-Jacobian product of update_math (D3Q19 body-force collision, Euler update) at one
+// site, by a hand-written reverse sweep over the forward arithmetic: in = the 88 inputs
+// (layout of k_adj_update), lo = the cotangents of the 28 outputs (qn 0-4, pn 5, u 6-8,
+// g 9-27), out = the cotangents of the 88 inputs.  The branches (upwind selection, face
+// fluxes) take the side the forward takes, as forward-mode differentiation of the same
+// code would.
+template <typename T, bool SHIFT>
+__device__ __forceinline__ void update_math_vjp(const Coef<T>& c, const T in[88], const T lo[28], T out[88]) {
+  const T* F = in;
+  const T lapmu_unused = in[3];
+  (void)lapmu_unused;
+  T W[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) W[a][b] = in[4 + 3 * a + b];
+  const T* q0 = in + 13;
+  const T* qfl = in + 18;  // qf[f][k] = qfl[5 f + k]
+  const T p0 = in[48];
+  const T* pf = in + 49;
+  const T* u0 = in + 55;
+  const T* uf = in + 58;
+  const T* g = in + 69;
+#pragma unroll
+  for (int j = 0; j < 88; ++j) out[j] = T(0);
+
+  // ---- LB collision (outputs u 6-8, g 9-27)
+  T m0 = g[0];
+  T jm[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int i = 1; i < 19; i += 2) {
+    m0 += g[i] + g[i + 1];
+    const T dg = g[i] - g[i + 1];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (lat_c(i, a)) jm[a] += lat_c(i, a) > 0 ? dg : -dg;
+  }
+  const T rho = SHIFT ? (c.rho0 + m0) : m0;
+  const T rinv = T(1) / rho;
+  T u[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u[a] = (jm[a] + T(0.5) * F[a]) * rinv;
+  const T u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const T r45 = T(4.5) * rho, r3 = T(3) * rho, om = c.tau_inv;
+  T lu[3] = {lo[6], lo[7], lo[8]};
+  T lF[3] = {T(0), T(0), T(0)};
+  T lbase = T(0), lr45 = T(0), lr3 = T(0), luF = T(0);
+  {
+    const T w = T(lat_w(0));
+    const T l0 = lo[9];
+    out[69] += (T(1) - om) * l0;
+    lbase += om * w * l0;
+    luF += -T(3) * c.guo * w * l0;
+  }
+#pragma unroll
+  for (int i = 1; i < 19; i += 2) {
+    const T w = T(lat_w(i)), gw = c.guo * w;
+    const T cu = T(lat_c(i, 0)) * u[0] + T(lat_c(i, 1)) * u[1] + T(lat_c(i, 2)) * u[2];
+    const T cF = T(lat_c(i, 0)) * F[0] + T(lat_c(i, 1)) * F[1] + T(lat_c(i, 2)) * F[2];
+    const T lp = lo[9 + i], lm = lo[10 + i];
+    out[69 + i] += (T(1) - om) * lp;
+    out[70 + i] += (T(1) - om) * lm;
+    const T lA = om * (lp + lm), lB = om * (lp - lm), lC = lp + lm, lE = lp - lm;
+    lbase += w * lA;
+    lr45 += w * cu * cu * lA;
+    lr3 += w * cu * lB;
+    luF += -T(3) * gw * lC;
+    const T lcu = T(2) * w * r45 * cu * lA + w * r3 * lB + T(9) * gw * cF * lC;
+    const T lcF = T(9) * gw * cu * lC + T(3) * gw * lE;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (lat_c(i, a)) {
+        lu[a] += T(lat_c(i, a)) * lcu;
+        lF[a] += T(lat_c(i, a)) * lcF;
+      }
+    }
+  }
+  // base = m0 - 1.5 rho u2 (shifted) or rho - 1.5 rho u2; r45 = 4.5 rho; r3 = 3 rho
+  T lm0 = T(0), lrho = T(0), lu2 = T(0);
+  if (SHIFT) lm0 += lbase; else lrho += lbase;
+  lrho += -T(1.5) * u2 * lbase + T(4.5) * lr45 + T(3) * lr3;
+  lu2 += -T(1.5) * rho * lbase;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lu[a] += T(2) * u[a] * lu2 + F[a] * luF;
+    lF[a] += u[a] * luF;
+  }
+  // u = (j + F/2) / rho
+  T lrinv = T(0), lj[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lrinv += (jm[a] + T(0.5) * F[a]) * lu[a];
+    lj[a] = rinv * lu[a];
+    lF[a] += T(0.5) * rinv * lu[a];
+  }
+  lrho += -rinv * rinv * lrinv;
+  lm0 += lrho;
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    T v = lm0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (lat_c(i, a)) v += T(lat_c(i, a)) * lj[a];
+    out[69 + i] += v;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) out[a] += lF[a];
+
+  // ---- order-parameter update (outputs qn 0-4, pn 5)
+  const T xi = c.xi;
+  T lq0[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    lq0[k] = lo[k];
+    out[64 + k] += c.gammaQ * lo[k];
+  }
+  out[48] += lo[5];              // p0
+  out[3] += c.M * lo[5];         // lap mu
+  const T ldivJ = -lo[5];
+  // co-rotation S of the five stored components
+  T Q[3][3];
+  full3(q0, Q);
+  T Dm[3][3], Om[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Dm[i][j] = T(0.5) * (W[i][j] + W[j][i]);
+      Om[i][j] = T(0.5) * (W[i][j] - W[j][i]);
+    }
+  T trQW = T(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) trQW += Q[i][j] * W[j][i];
+  const T cq = -T(2) * xi * trQW;
+  const T c23 = T(2) * xi / T(3);
+  T lQ[3][3], lD[3][3], lO[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) lQ[i][j] = lD[i][j] = lO[i][j] = T(0);
+  T lcq = T(0), lcdiag = T(0);
+  const int I5[5] = {0, 0, 0, 1, 1};
+  const int J5[5] = {0, 1, 2, 1, 2};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int i = I5[k], j = J5[k];
+    const T L = lo[k];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      lD[i][m] += xi * L * Q[m][j];
+      lQ[m][j] += xi * L * Dm[i][m];
+      lQ[i][m] += xi * L * Dm[m][j];
+      lD[m][j] += xi * L * Q[i][m];
+      lO[i][m] += L * Q[m][j];
+      lQ[m][j] += L * Om[i][m];
+      lQ[i][m] -= L * Om[m][j];
+      lO[m][j] -= L * Q[i][m];
+    }
+    lD[i][j] += c23 * L;
+    lcq += L * Q[i][j];
+    lQ[i][j] += cq * L;
+    if (i == j) lcdiag += L;
+  }
+  // cdiag = cq/3 - (2 xi/9) trD; cq = -2 xi tr(QW)
+  lcq += lcdiag / T(3);
+  const T ltrD = -(T(2) * xi / T(9)) * lcdiag;
+  const T ltrQW = -T(2) * xi * lcq;
+  T lW[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) lW[i][j] = T(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    lD[i][i] += ltrD;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      lQ[i][j] += W[j][i] * ltrQW;
+      lW[j][i] += Q[i][j] * ltrQW;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      lW[i][j] += T(0.5) * (lD[i][j] + lO[i][j]);
+      lW[j][i] += T(0.5) * (lD[i][j] - lO[i][j]);
+    }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) out[4 + 3 * a + b] += lW[a][b];
+  lq0[0] += lQ[0][0] - lQ[2][2];
+  lq0[1] += lQ[0][1] + lQ[1][0];
+  lq0[2] += lQ[0][2] + lQ[2][0];
+  lq0[3] += lQ[1][1] - lQ[2][2];
+  lq0[4] += lQ[1][2] + lQ[2][1];
+  // upwind advection of Q and the psi face fluxes
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int ip = 2 * a, im = 2 * a + 1;
+    const T up = u0[a] > T(0) ? u0[a] : T(0);
+    const T um = u0[a] < T(0) ? u0[a] : T(0);
+    T lup = T(0), lum = T(0);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const T ladv = -lo[k];
+      lup += (q0[k] - qfl[5 * im + k]) * ladv;
+      lum += (qfl[5 * ip + k] - q0[k]) * ladv;
+      lq0[k] += (up - um) * ladv;
+      out[18 + 5 * im + k] += -up * ladv;
+      out[18 + 5 * ip + k] += um * ladv;
+    }
+    T lu0 = (u0[a] > T(0) ? lup : T(0)) + (u0[a] < T(0) ? lum : T(0));
+    const T ubp = T(0.5) * (u0[a] + uf[ip]);
+    const T lJp = ldivJ;
+    if (ubp > T(0)) out[48] += ubp * lJp; else out[49 + ip] += ubp * lJp;
+    const T lubp = (ubp > T(0) ? p0 : pf[ip]) * lJp;
+    lu0 += T(0.5) * lubp;
+    out[58 + ip] += T(0.5) * lubp;
+    const T ubm = T(0.5) * (uf[im] + u0[a]);
+    const T lJm = -ldivJ;
+    if (ubm > T(0)) out[49 + im] += ubm * lJm; else out[48] += ubm * lJm;
+    const T lubm = (ubm > T(0) ? pf[im] : p0) * lJm;
+    out[58 + im] += T(0.5) * lubm;
+    lu0 += T(0.5) * lubm;
+    out[55 + a] += lu0;
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) out[13 + k] += lq0[k];
+}
+
 // ---------------------------------------------------------------- RK1
-template <typename T, bool SHIFT, int K>
+template <typename T, bool SHIFT>
 __global__ void __launch_bounds__(kAdjBlock) k_adj_update(AdjDesc<T> A) {
   const InstDesc<T>& I = A.I;
   const long long N = I.N;
@@ -158,39 +394,9 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_update(AdjDesc<T> A) {
   lo[5] = A.lp[s];
   for (int a = 0; a < 3; ++a) lo[6 + a] = A.lu[a * N + s];
   for (int i = 0; i < 19; ++i) lo[9 + i] = A.lg[i * N + s];
-  const Coef<Dual<T, K>> cd = dual_coef<T, K>(I.c);
-  for (int j0 = 0; j0 < 88; j0 += K) {
-    using D = Dual<T, K>;
-    D v[88];
-    for (int j = 0; j < 88; ++j) {
-      v[j] = D(in[j]);
-      if (j >= j0 && j < j0 + K) v[j].d[j - j0] = T(1);
-    }
-    D F[3], lapmu, Wg[3][3], q0[5], qf[6][5], p0, pf[6], u0[3], uf[6], Hs[5], g[19];
-    for (int a = 0; a < 3; ++a) F[a] = v[a];
-    lapmu = v[3];
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) Wg[a][b] = v[4 + 3 * a + b];
-    for (int k = 0; k < 5; ++k) q0[k] = v[13 + k];
-    for (int f = 0; f < 6; ++f)
-      for (int k = 0; k < 5; ++k) qf[f][k] = v[18 + 5 * f + k];
-    p0 = v[48];
-    for (int f = 0; f < 6; ++f) pf[f] = v[49 + f];
-    for (int a = 0; a < 3; ++a) u0[a] = v[55 + a];
-    for (int f = 0; f < 6; ++f) uf[f] = v[58 + f];
-    for (int k = 0; k < 5; ++k) Hs[k] = v[64 + k];
-    for (int i = 0; i < 19; ++i) g[i] = v[69 + i];
-    D qn[5], pn, u[3];
-    update_math<D, SHIFT>(cd, F, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hs, g, qn, pn, u);
-    for (int k = 0; k < K && j0 + k < 88; ++k) {
-      T acc2 = T(0);
-      for (int c = 0; c < 5; ++c) acc2 += lo[c] * qn[c].d[k];
-      acc2 += lo[5] * pn.d[k];
-      for (int a = 0; a < 3; ++a) acc2 += lo[6 + a] * u[a].d[k];
-      for (int i = 0; i < 19; ++i) acc2 += lo[9 + i] * g[i].d[k];
-      A.A[(j0 + k) * N + s] = acc2;
-    }
-  }
+  T ci[88];
+  update_math_vjp<T, SHIFT>(I.c, in, lo, ci);
+  for (int j = 0; j < 88; ++j) A.A[j * N + s] = ci[j];
 }
 
 // ---------------------------------------------------------------- RK2
@@ -474,7 +680,7 @@ cudaError_t LaunchAdj<T, SHIFT>::reverse_step(const AdjDescHost<T>& h, cudaStrea
   A.pgrad = h.pgrad;
   const unsigned nb = (unsigned)((h.I.N + kAdjBlock - 1) / kAdjBlock);
   constexpr int K = sizeof(T) == 4 ? 8 : 4;
-  k_adj_update<T, SHIFT, K><<<nb, kAdjBlock, 0, s>>>(A);
+  k_adj_update<T, SHIFT><<<nb, kAdjBlock, 0, s>>>(A);
   k_adj_spread<T><<<nb, kAdjBlock, 0, s>>>(A);
   k_adj_fields<T, K><<<nb, kAdjBlock, 0, s>>>(A);
   k_adj_gather<T><<<nb, kAdjBlock, 0, s>>>(A);
