@@ -9,94 +9,17 @@
 //   RK2 k_adj_spread : transposes of the stencils that fed update_math: div sigma -> sigma,
 //                      lap mu -> mu, grad u -> u, face reads -> Q/psi/u, the pull -> g*
 //   RK3 k_adj_fields : per site, VJP of local_fields (H, mu, sigma of Eqs. 2-5) with respect
-//                      to its 36 inputs (Q, psi and their stencils) and to zeta and q0
+//                      to its 36 inputs (Q, psi and their stencils) and to zeta and q0, by a
+//                      hand-written reverse sweep (local_fields_vjp)
 //   RK4 k_adj_gather : transposes of the Q/psi stencils (gradient, Laplacian, Hessian)
-// The VJP of local_fields runs the forward device function on dual numbers carrying K
-// tangents (forward mode, K input directions per pass), so it differentiates exactly the
-// arithmetic the step executes.  Stencil transposes use the negated offsets on the
+// The per-site reverse sweeps recompute the forward intermediates of the site and take
+// every branch (upwind sides) as the forward takes it.  Stencil transposes use the negated offsets on the
 // periodic lattice, so no site is written by two threads.
 #pragma once
 
 #include "lbcad_kernels.cuh"
 
 namespace lbcad {
-
-// ---------------------------------------------------------------- dual numbers
-template <typename S, int K>
-struct Dual {
-  S v;
-  S d[K];
-  __device__ __forceinline__ Dual() {}
-  __device__ __forceinline__ Dual(S x) : v(x) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) d[k] = S(0);
-  }
-};
-
-template <typename S, int K>
-__device__ __forceinline__ Dual<S, K> operator+(const Dual<S, K>& a, const Dual<S, K>& b) {
-  Dual<S, K> r;
-  r.v = a.v + b.v;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] + b.d[k];
-  return r;
-}
-template <typename S, int K>
-__device__ __forceinline__ Dual<S, K> operator-(const Dual<S, K>& a, const Dual<S, K>& b) {
-  Dual<S, K> r;
-  r.v = a.v - b.v;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] - b.d[k];
-  return r;
-}
-template <typename S, int K>
-__device__ __forceinline__ Dual<S, K> operator-(const Dual<S, K>& a) {
-  Dual<S, K> r;
-  r.v = -a.v;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = -a.d[k];
-  return r;
-}
-template <typename S, int K>
-__device__ __forceinline__ Dual<S, K> operator*(const Dual<S, K>& a, const Dual<S, K>& b) {
-  Dual<S, K> r;
-  r.v = a.v * b.v;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
-  return r;
-}
-template <typename S, int K>
-__device__ __forceinline__ Dual<S, K> operator/(const Dual<S, K>& a, const Dual<S, K>& b) {
-  Dual<S, K> r;
-  const S inv = S(1) / b.v;
-  r.v = a.v * inv;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * inv;
-  return r;
-}
-template <typename S, int K>
-__device__ __forceinline__ Dual<S, K>& operator+=(Dual<S, K>& a, const Dual<S, K>& b) {
-  a = a + b;
-  return a;
-}
-template <typename S, int K>
-__device__ __forceinline__ Dual<S, K>& operator-=(Dual<S, K>& a, const Dual<S, K>& b) {
-  a = a - b;
-  return a;
-}
-template <typename S, int K>
-__device__ __forceinline__ bool operator>(const Dual<S, K>& a, const Dual<S, K>& b) { return a.v > b.v; }
-template <typename S, int K>
-__device__ __forceinline__ bool operator<(const Dual<S, K>& a, const Dual<S, K>& b) { return a.v < b.v; }
-
-template <typename S, int K>
-__device__ __forceinline__ Coef<Dual<S, K>> dual_coef(const Coef<S>& c) {
-  Coef<Dual<S, K>> r;
-  r.tau_inv = c.tau_inv; r.guo = c.guo; r.rho0 = c.rho0;
-  r.A0 = c.A0; r.chi0 = c.chi0; r.chis = c.chis; r.K = c.K; r.q0 = c.q0; r.gammaQ = c.gammaQ; r.xi = c.xi;
-  r.a = c.a; r.b = c.b; r.kphi = c.kphi; r.M = c.M; r.W = c.W; r.zeta = c.zeta;
-  return r;
-}
 
 // Buffers of one reverse step (all [component][site]).
 template <typename T>
@@ -353,6 +276,358 @@ __device__ __forceinline__ void update_math_vjp(const Coef<T>& c, const T in[88]
   for (int k = 0; k < 5; ++k) out[13 + k] += lq0[k];
 }
 
+// ---------------------------------------------------------------- reverse mode of local_fields
+// Vector-Jacobian product of local_fields at one site by a hand-written reverse sweep: in =
+// the 36 inputs (q0 0-4, psi 5, dq 6-20 as 6 + 5a + k, lapq 21-25, dp 26-28, lapp 29,
+// hp 30-35), lo = the cotangents of its outputs (H 0-4, mu 5, sigma 6-14), out = the
+// cotangents of the 36 inputs; lzeta and lq0 receive the derivatives with respect to the
+// parameters zeta and q0.  Full 3x3 cotangents of Q and dQ_a are accumulated entry by entry
+// as the forward reads them and folded onto the five stored components at the end.
+template <typename T>
+__device__ __forceinline__ void local_fields_vjp(const Coef<T>& c, const T in[36], const T lo[15], T out[36],
+                                                 T& lzeta, T& lq0) {
+  // ---- forward intermediates
+  const T* q = in;
+  const T psi = in[5];
+  T Q[3][3];
+  full3(q, Q);
+  T dQ[3][3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) full3(in + 6 + 5 * a, dQ[a]);
+  const T* dp = in + 26;
+  const T* hp = in + 30;
+  const T chi = c.chi0 + c.chis * (T(1) + psi);
+  T QQ[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      QQ[i][j] = Q[i][0] * Q[0][j] + Q[i][1] * Q[1][j] + Q[i][2] * Q[2][j];
+      QQ[j][i] = QQ[i][j];
+    }
+  const T trQ2 = QQ[0][0] + QQ[1][1] + QQ[2][2];
+  const T trQ3 = QQ[0][0] * Q[0][0] + QQ[1][1] * Q[1][1] + QQ[2][2] * Q[2][2] +
+                 T(2) * (QQ[0][1] * Q[0][1] + QQ[0][2] * Q[0][2] + QQ[1][2] * Q[1][2]);
+  T C[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    C[0][b] = dQ[1][2][b] - dQ[2][1][b];
+    C[1][b] = dQ[2][0][b] - dQ[0][2][b];
+    C[2][b] = dQ[0][1][b] - dQ[1][0][b];
+  }
+  T CC[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) CC[i][j] = C[i][j] + C[j][i];
+  const T g2 = dp[0] * dp[0] + dp[1] * dp[1] + dp[2] * dp[2];
+  const T Ac = c.A0 * chi;
+  const T Kq = T(2) * c.K * c.q0;
+  const T lin = -c.A0 * (T(1) - chi / T(3)) - Ac * trQ2 - Kq * T(2) * c.q0;
+  const T iso = (Ac * trQ2 - c.W * g2) / T(3);
+  const int I5[5] = {0, 0, 0, 1, 1};
+  const int J5[5] = {0, 1, 2, 1, 2};
+  T H[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int i = I5[k], j = J5[k];
+    T h = lin * Q[i][j] + Ac * QQ[i][j] + c.K * in[21 + k] - Kq * CC[i][j] - c.W * dp[i] * dp[j];
+    if (i == j) h -= iso;
+    H[k] = h;
+  }
+  T Hf[3][3];
+  full3(H, Hf);
+  const T Qh = Q[0][0] * hp[0] + Q[1][1] * hp[1] + Q[2][2] * hp[2] +
+               T(2) * (Q[0][1] * hp[3] + Q[0][2] * hp[4] + Q[1][2] * hp[5]);
+  T divQdp = T(0);
+#pragma unroll
+  for (int b = 0; b < 3; ++b) divQdp += (dQ[0][0][b] + dQ[1][1][b] + dQ[2][2][b]) * dp[b];
+  const T psi2 = psi * psi;
+  const T mu = psi * (c.b * psi2 - c.a) - c.kphi * in[29] +
+               c.A0 * c.chis * (trQ2 * (T(0.25) * trQ2 - T(1) / T(6)) - trQ3 / T(3)) - T(2) * c.W * (divQdp + Qh);
+  T Qdp[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Qdp[i] = Q[i][0] * dp[0] + Q[i][1] * dp[1] + Q[i][2] * dp[2];
+  const T QC = Q[0][0] * C[0][0] + Q[1][1] * C[1][1] + Q[2][2] * C[2][2] + Q[0][1] * CC[0][1] +
+               Q[0][2] * CC[0][2] + Q[1][2] * CC[1][2];
+  T QH[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) QH[i][j] = Q[i][0] * Hf[0][j] + Q[i][1] * Hf[1][j] + Q[i][2] * Hf[2][j];
+  const T phic = T(0.5) * (T(1) + psi);
+  const T trQH = QH[0][0] + QH[1][1] + QH[2][2];
+  const T cQ = T(2) * c.xi * trQH - c.zeta * phic;
+  const T cH = -T(2) * c.xi / T(3);
+  const T cP = T(1) - c.xi, cM = -(T(1) + c.xi);
+  T wv[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) wv[b] = c.kphi * dp[b] + T(2) * c.W * Qdp[b];
+  T v[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int g = (b + 1) % 3, m = (b + 2) % 3;
+      v[a][b] = dQ[a][g][0] * Q[0][m] + dQ[a][g][1] * Q[1][m] + dQ[a][g][2] * Q[2][m] -
+                (dQ[a][m][0] * Q[0][g] + dQ[a][m][1] * Q[1][g] + dQ[a][m][2] * Q[2][g]);
+    }
+
+  // ---- reverse sweep
+  T lQ[3][3], ldQ[3][3][3], lHf[3][3], lQH[3][3], lG[3][3], lCC[3][3], lC[3][3], lQQ[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      lQ[i][j] = lHf[i][j] = lQH[i][j] = lG[i][j] = lCC[i][j] = lC[i][j] = lQQ[i][j] = T(0);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) ldQ[a][i][j] = T(0);
+    }
+  T ldp[3] = {T(0), T(0), T(0)}, lwv[3] = {T(0), T(0), T(0)}, lQdp[3] = {T(0), T(0), T(0)};
+  T lpsi = T(0), lcQ = T(0), lcI = T(0), lKq = T(0), ltrQH = T(0), lP0 = T(0), lphic = T(0);
+  lzeta = T(0);
+  lq0 = T(0);
+  // sigma
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const T L = lo[6 + 3 * a + b];
+      lcQ += L * Q[a][b];
+      lQ[a][b] += cQ * L;
+      lQH[a][b] += cP * L;
+      lQH[b][a] += cM * L;
+      lHf[a][b] += cH * L;
+      lG[a][b] += -c.K * L;
+      lKq += -v[a][b] * L;
+      const T lv = -Kq * L;
+      ldp[a] += -wv[b] * L;
+      lwv[b] += -dp[a] * L;
+      if (a == b) lcI += L;
+      const int g = (b + 1) % 3, m = (b + 2) % 3;
+#pragma unroll
+      for (int n = 0; n < 3; ++n) {
+        ldQ[a][g][n] += lv * Q[n][m];
+        lQ[n][m] += lv * dQ[a][g][n];
+        ldQ[a][m][n] -= lv * Q[n][g];
+        lQ[n][g] -= lv * dQ[a][m][n];
+      }
+    }
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    ldp[b] += c.kphi * lwv[b];
+    lQdp[b] += T(2) * c.W * lwv[b];
+  }
+  // cQ = 2 xi trQH - zeta phic; cI = (2 xi/3) trQH - P0
+  ltrQH += T(2) * c.xi * lcQ + (T(2) * c.xi / T(3)) * lcI;
+  lzeta += -phic * lcQ;
+  lphic += -c.zeta * lcQ;
+  lP0 += -lcI;
+  lpsi += T(0.5) * lphic;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) lQH[i][i] += ltrQH;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        lQ[i][m] += lQH[i][j] * Hf[m][j];
+        lHf[m][j] += Q[i][m] * lQH[i][j];
+      }
+  // P0 = psi mu - fden
+  const T lmu = lo[5] + psi * lP0;
+  lpsi += mu * lP0;
+  const T lf = -lP0;
+  // fden
+  T lpsi2 = (T(0.5) * c.b * psi2 - T(0.5) * c.a) * lf;
+  T lg2 = T(0.5) * c.kphi * lf;
+  T lchi = c.A0 * (-(T(0.5) / T(3)) * trQ2 - trQ3 / T(3) + trQ2 * trQ2 / T(4)) * lf;
+  T ltrQ2 = c.A0 * (T(0.5) * (T(1) - chi / T(3)) + chi / T(2) * trQ2) * lf + Kq * c.q0 * lf;
+  T ltrQ3 = -c.A0 * chi / T(3) * lf;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) lG[a][a] += T(0.5) * c.K * lf;
+  lKq += QC * lf + c.q0 * trQ2 * lf;
+  const T lQC = Kq * lf;
+  lq0 += Kq * trQ2 * lf;
+  const T lanch = c.W * lf;
+  // anch = dp . Qdp; Qdp = Q dp
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    ldp[i] += Qdp[i] * lanch;
+    lQdp[i] += dp[i] * lanch;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      lQ[i][m] += lQdp[i] * dp[m];
+      ldp[m] += Q[i][m] * lQdp[i];
+    }
+  // QC
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    lQ[i][i] += C[i][i] * lQC;
+    lC[i][i] += Q[i][i] * lQC;
+  }
+  lQ[0][1] += CC[0][1] * lQC;
+  lCC[0][1] += Q[0][1] * lQC;
+  lQ[0][2] += CC[0][2] * lQC;
+  lCC[0][2] += Q[0][2] * lQC;
+  lQ[1][2] += CC[1][2] * lQC;
+  lCC[1][2] += Q[1][2] * lQC;
+  // mu
+  lpsi += (c.b * psi2 - c.a) * lmu;
+  lpsi2 += psi * c.b * lmu;
+  T llapp = -c.kphi * lmu;
+  ltrQ2 += c.A0 * c.chis * (T(0.5) * trQ2 - T(1) / T(6)) * lmu;
+  ltrQ3 += -c.A0 * c.chis / T(3) * lmu;
+  const T ldiv = -T(2) * c.W * lmu, lQh = -T(2) * c.W * lmu;
+  // Qh
+  T lhp[6];
+  lQ[0][0] += hp[0] * lQh;
+  lQ[1][1] += hp[1] * lQh;
+  lQ[2][2] += hp[2] * lQh;
+  lQ[0][1] += T(2) * hp[3] * lQh;
+  lQ[0][2] += T(2) * hp[4] * lQh;
+  lQ[1][2] += T(2) * hp[5] * lQh;
+  lhp[0] = Q[0][0] * lQh;
+  lhp[1] = Q[1][1] * lQh;
+  lhp[2] = Q[2][2] * lQh;
+  lhp[3] = T(2) * Q[0][1] * lQh;
+  lhp[4] = T(2) * Q[0][2] * lQh;
+  lhp[5] = T(2) * Q[1][2] * lQh;
+  // divQdp
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    ldQ[0][0][b] += dp[b] * ldiv;
+    ldQ[1][1][b] += dp[b] * ldiv;
+    ldQ[2][2][b] += dp[b] * ldiv;
+    ldp[b] += (dQ[0][0][b] + dQ[1][1][b] + dQ[2][2][b]) * ldiv;
+  }
+  lpsi += T(2) * psi * lpsi2;
+  // G (symmetric): the computed value s_ab serves G[a][b] and G[b][a]
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a; b < 3; ++b) {
+      const T ls = (a == b) ? lG[a][a] : lG[a][b] + lG[b][a];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+          const T w = (i == j) ? T(1) : T(2);
+          ldQ[a][i][j] += w * ls * dQ[b][i][j];
+          ldQ[b][i][j] += w * ls * dQ[a][i][j];
+        }
+    }
+  // H (outputs and the uses of Hf)
+  T lH[5];
+  lH[0] = lo[0] + lHf[0][0] - lHf[2][2];
+  lH[1] = lo[1] + lHf[0][1] + lHf[1][0];
+  lH[2] = lo[2] + lHf[0][2] + lHf[2][0];
+  lH[3] = lo[3] + lHf[1][1] - lHf[2][2];
+  lH[4] = lo[4] + lHf[1][2] + lHf[2][1];
+  T llin = T(0), lAc = T(0), liso = T(0), llapq[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int i = I5[k], j = J5[k];
+    const T L = lH[k];
+    llin += Q[i][j] * L;
+    lQ[i][j] += lin * L;
+    lAc += QQ[i][j] * L;
+    lQQ[i][j] += Ac * L;
+    llapq[k] = c.K * L;
+    lKq += -CC[i][j] * L;
+    lCC[i][j] += -Kq * L;
+    ldp[i] += -c.W * dp[j] * L;
+    ldp[j] += -c.W * dp[i] * L;
+    if (i == j) liso += -L;
+  }
+  // iso, lin, Kq, Ac, g2
+  lAc += trQ2 / T(3) * liso;
+  ltrQ2 += Ac / T(3) * liso;
+  lg2 += -c.W / T(3) * liso;
+  lchi += (c.A0 / T(3)) * llin;
+  lAc += -trQ2 * llin;
+  ltrQ2 += -Ac * llin;
+  lKq += -T(2) * c.q0 * llin;
+  lq0 += -T(2) * Kq * llin;
+  lq0 += T(2) * c.K * lKq;
+  lchi += c.A0 * lAc;
+#pragma unroll
+  for (int b = 0; b < 3; ++b) ldp[b] += T(2) * dp[b] * lg2;
+  // CC (symmetric value per unordered pair) and C
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      if (i == j) {
+        lC[i][i] += T(2) * lCC[i][i];
+      } else {
+        const T l = lCC[i][j] + lCC[j][i];
+        lC[i][j] += l;
+        lC[j][i] += l;
+      }
+    }
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    ldQ[1][2][b] += lC[0][b];
+    ldQ[2][1][b] -= lC[0][b];
+    ldQ[2][0][b] += lC[1][b];
+    ldQ[0][2][b] -= lC[1][b];
+    ldQ[0][1][b] += lC[2][b];
+    ldQ[1][0][b] -= lC[2][b];
+  }
+  // trQ3, trQ2, QQ
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    lQQ[i][i] += Q[i][i] * ltrQ3 + ltrQ2;
+    lQ[i][i] += QQ[i][i] * ltrQ3;
+  }
+  lQQ[0][1] += T(2) * Q[0][1] * ltrQ3;
+  lQ[0][1] += T(2) * QQ[0][1] * ltrQ3;
+  lQQ[0][2] += T(2) * Q[0][2] * ltrQ3;
+  lQ[0][2] += T(2) * QQ[0][2] * ltrQ3;
+  lQQ[1][2] += T(2) * Q[1][2] * ltrQ3;
+  lQ[1][2] += T(2) * QQ[1][2] * ltrQ3;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const T l = (i == j) ? lQQ[i][i] : lQQ[i][j] + lQQ[j][i];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        lQ[i][m] += l * Q[m][j];
+        lQ[m][j] += l * Q[i][m];
+      }
+    }
+  // chi = chi0 + chis (1 + psi)
+  lpsi += c.chis * lchi;
+  // fold the full-matrix cotangents onto the stored components (full3 transposed)
+  out[0] = lQ[0][0] - lQ[2][2];
+  out[1] = lQ[0][1] + lQ[1][0];
+  out[2] = lQ[0][2] + lQ[2][0];
+  out[3] = lQ[1][1] - lQ[2][2];
+  out[4] = lQ[1][2] + lQ[2][1];
+  out[5] = lpsi;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    out[6 + 5 * a + 0] = ldQ[a][0][0] - ldQ[a][2][2];
+    out[6 + 5 * a + 1] = ldQ[a][0][1] + ldQ[a][1][0];
+    out[6 + 5 * a + 2] = ldQ[a][0][2] + ldQ[a][2][0];
+    out[6 + 5 * a + 3] = ldQ[a][1][1] - ldQ[a][2][2];
+    out[6 + 5 * a + 4] = ldQ[a][1][2] + ldQ[a][2][1];
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) out[21 + k] = llapq[k];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) out[26 + b] = ldp[b];
+  out[29] = llapp;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) out[30 + k] = lhp[k];
+}
+
 // ---------------------------------------------------------------- RK1
 template <typename T, bool SHIFT>
 __global__ void __launch_bounds__(kAdjBlock) k_adj_update(AdjDesc<T> A) {
@@ -474,7 +749,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_spread(AdjDesc<T> A) {
 // ---------------------------------------------------------------- RK3
 // Inputs of local_fields, packed: q0 0-4, p0 5, dq 6-20 (a*5 + k), lapq 21-25, dp 26-28,
 // lapp 29, hp 30-35; two more tangent directions: zeta (36), q0 parameter (37).
-template <typename T, int K>
+template <typename T>
 __global__ void __launch_bounds__(kAdjBlock) k_adj_fields(AdjDesc<T> A) {
   const InstDesc<T>& I = A.I;
   const long long N = I.N;
@@ -506,38 +781,11 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_fields(AdjDesc<T> A) {
     for (int k = 0; k < 5; ++k) lo[k] = A.ls[(10 + k) * N + s];
     lo[5] = A.ls[9 * N + s];
     for (int k = 0; k < 9; ++k) lo[6 + k] = A.ls[k * N + s];
-    for (int j0 = 0; j0 < 38; j0 += K) {
-      using D = Dual<T, K>;
-      Coef<D> cd = dual_coef<T, K>(I.c);
-      if (36 >= j0 && 36 < j0 + K) cd.zeta.d[36 - j0] = T(1);
-      if (37 >= j0 && 37 < j0 + K) cd.q0.d[37 - j0] = T(1);
-      D v[36];
-      for (int j = 0; j < 36; ++j) {
-        v[j] = D(in[j]);
-        if (j >= j0 && j < j0 + K) v[j].d[j - j0] = T(1);
-      }
-      D q0[5], p0, dq[3][5], lapq[5], dp[3], lapp, hp[6];
-      for (int k = 0; k < 5; ++k) q0[k] = v[k];
-      p0 = v[5];
-      for (int a = 0; a < 3; ++a)
-        for (int k = 0; k < 5; ++k) dq[a][k] = v[6 + 5 * a + k];
-      for (int k = 0; k < 5; ++k) lapq[k] = v[21 + k];
-      for (int a = 0; a < 3; ++a) dp[a] = v[26 + a];
-      lapp = v[29];
-      for (int k = 0; k < 6; ++k) hp[k] = v[30 + k];
-      D H[5], mu, sig[9];
-      local_fields<D>(cd, q0, p0, dq, lapq, dp, lapp, hp, H, mu, sig);
-      for (int k = 0; k < K && j0 + k < 38; ++k) {
-        T acc2 = T(0);
-        for (int c = 0; c < 5; ++c) acc2 += lo[c] * H[c].d[k];
-        acc2 += lo[5] * mu.d[k];
-        for (int c = 0; c < 9; ++c) acc2 += lo[6 + c] * sig[c].d[k];
-        const int j = j0 + k;
-        if (j < 36) A.Bf[j * N + s] = acc2;
-        else if (j == 36) pz = (double)acc2;
-        else pq = (double)acc2;
-      }
-    }
+    T ci[36], lz, lq;
+    local_fields_vjp<T>(I.c, in, lo, ci, lz, lq);
+    for (int j = 0; j < 36; ++j) A.Bf[j * N + s] = ci[j];
+    pz = (double)lz;
+    pq = (double)lq;
   }
   // per-block FP64 sums of the parameter gradients (fixed order: deterministic)
   __shared__ double sh[2][kAdjBlock / 32];
@@ -679,10 +927,9 @@ cudaError_t LaunchAdj<T, SHIFT>::reverse_step(const AdjDescHost<T>& h, cudaStrea
   A.og = h.og; A.oq = h.oq; A.op = h.op; A.ou = h.ou;
   A.pgrad = h.pgrad;
   const unsigned nb = (unsigned)((h.I.N + kAdjBlock - 1) / kAdjBlock);
-  constexpr int K = sizeof(T) == 4 ? 8 : 4;
   k_adj_update<T, SHIFT><<<nb, kAdjBlock, 0, s>>>(A);
   k_adj_spread<T><<<nb, kAdjBlock, 0, s>>>(A);
-  k_adj_fields<T, K><<<nb, kAdjBlock, 0, s>>>(A);
+  k_adj_fields<T><<<nb, kAdjBlock, 0, s>>>(A);
   k_adj_gather<T><<<nb, kAdjBlock, 0, s>>>(A);
   return cudaGetLastError();
 }
