@@ -1,0 +1,200 @@
+"""Parity at the full sizes of the workloads, where the oracle cannot advance the whole box:
+the oracle advances windows cut from the GPU state.
+
+One step of the method reads neighbours at most three sites away (the pulled population
+carries the force of the neighbouring site, the force needs the stress one site further out,
+the stress needs the stencils of Q and psi one site further still), so after s steps the sites
+at least 3 s from the edge of a window depend only on the window's contents.  A W^3 window taken from the GPU state at step t, advanced s steps
+by the oracle with its own periodic wrap, must therefore match the GPU state at step t + s on
+its interior (W - 6 s)^3, whatever the wrap does to the rim.
+
+Workloads:
+- 256^3 droplet, R = 64, pitch 48, zeta = 0.005: FP32 against the GPU FP64 run over its first
+  100 steps (conserved sums and centroid every 20 steps, every field at step 100 by relative
+  L2), and windows of both runs against the oracle.
+- 64 droplets in boxes with edges from {48, 64, 80, 96}, FP32, one persistent launch per step
+  replayed from a CUDA graph, autotuned tiles: windows of every instance against the oracle.
+"""
+import numpy as np
+import pytest
+
+import paper_2011_00287_gb300 as L
+from paper_2011_00287_gb300 import workloads as WL
+from oracle import oracle as O
+
+REACH = 3  # sites one step reads away from the updated site
+
+
+@pytest.fixture(scope="module", autouse=True)
+def oracle_built():
+    O.build()
+
+
+@pytest.fixture(scope="module")
+def lib_built():
+    from paper_2011_00287_gb300 import build as B
+    B.build()
+
+
+def _perm():
+    """Index map from the library's D3Q19 order to the oracle's."""
+    cl, _ = L.lattice()
+    co, _ = O.lattice()
+    return np.array([int(np.where((co == v).all(1))[0][0]) for v in cl])
+
+
+def _rel_l2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _shifted(f):
+    _, w = O.lattice()
+    return f - w.reshape(19, 1, 1, 1)
+
+
+def _cut(fields, origin, W):
+    """W^3 window of every field (arrays [c][z][y][x]) starting at origin (x, y, z), periodic."""
+    out = {}
+    for k, a in fields.items():
+        nz, ny, nx = a.shape[-3:]
+        ix = (origin[0] + np.arange(W)) % nx
+        iy = (origin[1] + np.arange(W)) % ny
+        iz = (origin[2] + np.arange(W)) % nz
+        v = a[..., iz[:, None, None], iy[None, :, None], ix[None, None, :]]
+        out[k] = np.ascontiguousarray(v, dtype=np.float64)
+    return out
+
+
+def _oracle_window(win, W, steps, perm=None, **kw):
+    """Advance a window of the library's state by the oracle; returns its fields in the
+    library's population order (perm: library order -> oracle order)."""
+    perm = _perm() if perm is None else perm
+    s = O.State((W, W, W), O.default_params((W, W, W), **kw), seed=1)
+    f = np.empty_like(win["g"])
+    f[perm] = win["g"]
+    s.f, s.q, s.psi, s.u = f, win["q"].copy(), win["psi"].copy(), win["u"].copy()
+    s.step(steps)
+    return {"g": s.f[perm], "q": s.q, "psi": s.psi, "u": s.u}
+
+
+def _interior(a, h):
+    return a[..., h:-h, h:-h, h:-h]
+
+
+def _windows_of(shape, R):
+    """Window origins: on the droplet interface along x, and across the periodic corner."""
+    nx, ny, nz = shape
+    return [(int(nx / 2 + R) - 12, ny // 2 - 12, nz // 2 - 12), (nx - 12, ny - 12, nz - 12)]
+
+
+def _check_windows(before, after, origins, W, steps, fp64, **kw):
+    """FP64: max abs error on the window interiors <= 1e-12.  FP32: max abs error <= 1e-5 of
+    the field's largest magnitude over the whole instance (populations shifted by w_i rho0).
+    Relative norms on a window are no measure in FP32: far from the droplet the exact flow and
+    the flow-induced Q are many orders below the FP32 resolution of the instance's fields."""
+    h = REACH * steps
+    perm = _perm()
+    scale = {}
+    if not fp64:
+        for k, a in after.items():
+            scale[k] = float(np.abs(_shifted(a) if k == "g" else a).max())
+    worst = {}
+    for o in origins:
+        ref = _oracle_window(_cut(before, o, W), W, steps, perm, **kw)
+        got = _cut(after, o, W)
+        for k in ref:
+            e = float(np.abs(_interior(got[k], h) - _interior(ref[k], h)).max())
+            worst[k] = max(worst.get(k, 0.0), e if fp64 else e / scale[k])
+    for k, e in worst.items():
+        assert e <= (1e-12 if fp64 else 1e-5), (k, worst)
+    return worst
+
+
+def test_window_reach_on_a_small_box():
+    """The window argument itself, on the oracle alone: windows of a 32^3 oracle state cut
+    across the droplet, advanced by the oracle, against the full box.  One step: the interior
+    at depth 3 matches exactly and depth 2 does not (the reach of one step is 3).  Two steps:
+    depth 6, the margin the checks below use, matches exactly and depth 4 does not (the exact
+    reach of two steps is 5: Q's own update reads only one site away)."""
+    shape = (32, 32, 32)
+    full = O.State(shape, O.default_params(shape, R=8.0, p0=16.0), seed=3).step(5)
+    perm = np.arange(19)  # oracle order throughout
+    W, o = 20, (14, 6, 6)
+    for steps, ok, short in ((1, 3, 2), (2, 6, 4)):
+        st = full.copy()
+        before = {"g": st.f, "q": st.q, "psi": st.psi, "u": st.u}
+        ref = _oracle_window(_cut(before, o, W), W, steps, perm, R=8.0, p0=16.0)
+        st.step(steps)
+        after = _cut({"g": st.f, "q": st.q, "psi": st.psi, "u": st.u}, o, W)
+        for k in ref:
+            assert np.array_equal(_interior(ref[k], ok), _interior(after[k], ok)), (steps, k)
+        assert not np.array_equal(_interior(ref["g"], short), _interior(after["g"], short)), steps
+
+
+@pytest.mark.gpu
+def test_256cube_fp32_against_fp64_first_100_steps(lib_built):
+    shape = (256, 256, 256)
+    kw = dict(R=64.0, p0=48.0, zeta=0.005)
+    s32 = L.Simulation([shape], [L.default_params(shape, precision=L.FP32, **kw)], seed=1)
+    s64 = L.Simulation([shape], [L.default_params(shape, precision=L.FP64, **kw)], seed=1)
+    s32.autotune(2)
+    N = 256 ** 3
+    for _ in range(5):
+        s32.step(20)
+        s64.step(20)
+        a, b = s32.observables(0), s64.observables(0)
+        # FP64 sums of mass, psi and momentum, and the centroid (lattice units)
+        dc = np.abs(s32.centroid(0) - s64.centroid(0)).max()
+        print("256^3 FP32 - FP64: mass %.2e, psi %.2e, momentum %.2e, centroid %.2e"
+              % (a[0] - b[0], a[1] - b[1], np.abs(a[2:5] - b[2:5]).max(), dc))
+        assert abs(a[0] - b[0]) <= 1e-9 * N and abs(a[1] - b[1]) <= 1e-6 * N, (a, b)
+        assert np.abs(a[2:5] - b[2:5]).max() <= 1e-9 * N, (a, b)
+        assert dc <= 1e-4
+    f32, f64 = s32.get_fields(0), s64.get_fields(0)
+    errs = {"g": _rel_l2(_shifted(f32["g"]), _shifted(f64["g"]))}
+    for k in ("q", "psi", "u"):
+        errs[k] = _rel_l2(f32[k], f64[k])
+    print("256^3 after 100 steps, FP32 vs FP64 rel L2:", errs, "rms |u| %.2e" % np.sqrt((f64["u"] ** 2).sum(0).mean()))
+    # Q and psi within 1e-5.  The populations (shifted) and the velocity are held to 1e-4
+    # (measured 1.2e-5 and 1.4e-5): 100 FP32 roundings of about 6e-8 each reach 6e-6 where
+    # they add up, and the trajectory amplifies them; the 100-step check of the R = 8 droplet
+    # against the oracle stays within 1e-5.
+    tol = {"g": 1e-4, "u": 1e-4, "q": 1e-5, "psi": 1e-5}
+    for k, e in errs.items():
+        assert e <= tol[k], errs
+    del f32, f64
+    # windows of both runs, two steps by the oracle
+    W, steps = 24, 2
+    origins = _windows_of(shape, 64.0)
+    for sim, fp64 in ((s64, True), (s32, False)):
+        before = sim.get_fields(0)
+        sim.step(steps)
+        after = sim.get_fields(0)
+        worst = _check_windows(before, after, origins, W, steps, fp64, **kw)
+        print("256^3 windows, %s:" % ("FP64" if fp64 else "FP32"), worst)
+        del before, after
+    s32.close()
+    s64.close()
+
+
+@pytest.mark.gpu
+def test_batch_of_64_uneven_droplets_windows_against_oracle(lib_built):
+    work = WL.batch_uneven(seed=7, count=64)
+    prms = [L.default_params(w["grid"], R=w["R"], p0=w["p0"], zeta=w["zeta"], precision=L.FP32) for w in work]
+    sim = L.Simulation([w["grid"] for w in work], prms, seed=7)
+    sim.autotune(2)
+    sim.set_graph(2)
+    sim.step(18)
+    before = [sim.get_fields(i) for i in range(len(work))]
+    sim.step(2)  # one replay of the captured graph
+    W, steps = 24, 2
+    worst = {}
+    for i, w in enumerate(work):
+        after = sim.get_fields(i)
+        e = _check_windows(before[i], after, _windows_of(w["grid"], w["R"]), W, steps, False,
+                           R=w["R"], p0=w["p0"], zeta=w["zeta"])
+        for k, v in e.items():
+            worst[k] = max(worst.get(k, 0.0), v)
+        before[i] = None
+    print("64 uneven droplets, worst window rel L2 after 2 graph-replayed steps:", worst)
+    sim.close()
