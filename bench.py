@@ -249,7 +249,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--no-staged", action="store_true", help="skip the Heun / sync staged-path leg")
+    ap.add_argument("--no-staged", action="store_true",
+                    help="skip the Heun / sync, LB-variant and bulk legs")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg (64^3, 500 steps)")
     ap.add_argument("--workload", default="droplet", choices=["droplet", "batch64"],
                     help="droplet: the 128^3 benchmark line; batch64: 64 uneven droplets in one launch")
@@ -321,6 +322,26 @@ def main():
             sv.step(3)
             msv = time_steps(sv, torch, 20)
             staged[name] = {"mlups": N / (msv * 1e-3) / 1e6, "ms_per_step": msv, "kernels_per_step": launches}
+            sv.close()
+
+    # the other LB variants of Sec. 3 on the same workload: D3Q15 and the Eq. 9-11 form on the
+    # fused kernels (autotuned over their two tile shapes), each at a tau where it is stable
+    # on the droplet; the radius-2 stencils on the staged path
+    variants = None
+    if not args.no_staged:
+        variants = {}
+        for name, kw, steps in (("d3q15", dict(lattice=L.D3Q15, tau=1.0), 100),
+                                ("stress_eq", dict(lb_form=L.LB_STRESS_EQ, tau=1.5), 100),
+                                ("d3q15_stress_eq", dict(lattice=L.D3Q15, lb_form=L.LB_STRESS_EQ, tau=2.5), 50),
+                                ("r2_stencils", dict(stencil=L.STENCIL_R2), 20)):
+            sv = L.Simulation([(n, n, n)], [workload_params(L, n, L.FP32, **kw)], seed=1 + rank, device=local)
+            cfg = None
+            if name != "r2_stencils":
+                cfg, _ = sv.autotune(3)
+            sv.step(3)
+            msv = time_steps(sv, torch, steps)
+            variants[name] = {"mlups": N / (msv * 1e-3) / 1e6, "ms_per_step": msv, "tau": kw["tau"] if "tau" in kw else 1.0,
+                              "path": "staged" if cfg is None else "fused " + TILE_NAMES[cfg]}
             sv.close()
 
     # second workload: bulk active nematic (no droplet, psi = 1), same kernel and schedule
@@ -425,7 +446,7 @@ def main():
                            "l2": "state %.0f MB per step > 129 MB L2, no flush" % (224 * N / 1e6)},
                 "roofline": roofline, "roofline_issue": roofline_issue, "cpu_baseline": cpu, "e2e": e2e,
                 "tiles": {"chosen": TILE_NAMES[tile_cfg], "ms_per_cfg": dict(zip(TILE_NAMES, tile_ms))},
-                "gpu_launches": K, "clocks": csum, "fp64_gpu": fp64, "staged_fp32": staged, "bulk_fp32": bulk, "adjoint_fp32": adjoint,
+                "gpu_launches": K, "clocks": csum, "fp64_gpu": fp64, "staged_fp32": staged, "lb_variants_fp32": variants, "bulk_fp32": bulk, "adjoint_fp32": adjoint,
                 "speedup_fp32_vs_fp64": (value / world / fp64["mlups"]) if fp64 else None,
                 "observables_finite": finite}
         print(json.dumps(line))

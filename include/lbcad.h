@@ -168,25 +168,30 @@ int lbcad_step(lbcad_ctx* c, int64_t n);
 /* LBCAD_PATH_STAGED: per-site kernels in the order fields -> LB (force, pull, collision;
  * writes u of this step) -> order-parameter update, and for LBCAD_HEUN a second fields
  * pass at the predicted Q, psi and the corrector (Sec. 3).  The only path for LBCAD_HEUN,
- * LBCAD_SYNC, LBCAD_D3Q15, LBCAD_LB_STRESS_EQ or LBCAD_STENCIL_R2, selected at create; default contexts
- * may select it as a third cross-check (same per-site arithmetic as the other two).
- * Scratch: 15 values per site, 27 with LBCAD_HEUN.  Fused/two-kernel paths, tile shapes,
- * autotune and the adjoint return LBCAD_E_UNSUPPORTED on those contexts. */
+ * LBCAD_SYNC or LBCAD_STENCIL_R2, selected at create; other contexts may select it as a
+ * cross-check (same per-site arithmetic).  Scratch: 15 values per site, 27 with LBCAD_HEUN.
+ * Fused/two-kernel paths, tile shapes, autotune and the adjoint return LBCAD_E_UNSUPPORTED
+ * on those contexts.  LBCAD_D3Q15 and LBCAD_LB_STRESS_EQ run on the fused path (tile shapes
+ * 0 and 3 only) and the staged path; the two-kernel path and the adjoint return
+ * LBCAD_E_UNSUPPORTED for them. */
 #define LBCAD_PATH_STAGED 2
 int lbcad_set_path(lbcad_ctx* c, int32_t path);
 
 /* Picks the fastest tile shape of the fused step for this context by timing each
  * candidate over `reps` launches that recompute the step from the current state into
  * the next-state buffers (the simulation does not advance; results are unchanged, only
- * speed).  Writes the chosen index to *chosen and, if ms_per_cfg is given, the measured
+ * speed), in three rounds that interleave the candidates; a candidate's time is its best
+ * round.  Writes the chosen index to *chosen and, if ms_per_cfg is given, the measured
  * milliseconds per launch of up to ncfg candidates (-1 for a shape that does not fit).
  * Candidates: 0 = 32x8 tiles (default), 1 = 32x16, 2 = 64x8, 3 and 4 = 32x8 software-pipelined
  * (sigma of plane k+1 on 8 or 6 warps while the other 8 or 10 warps output plane k-1, in
  * one phase), 5 and 6 = 32x6 software-pipelined (9 or 10 sigma warps, one round per
- * plane); 1-6 are FP32 only. */
+ * plane); 1-6 are FP32 only.  With LBCAD_D3Q15 or LBCAD_LB_STRESS_EQ only 0 and 3 are
+ * candidates (-1 for the others). */
 int lbcad_autotune(lbcad_ctx* c, int32_t reps, int32_t* chosen, float* ms_per_cfg, int32_t ncfg);
 
-/* Selects tile shape `cfg` of the fused step explicitly (same candidates as above).
+/* Selects tile shape `cfg` of the fused step explicitly (same candidates as above;
+ * LBCAD_E_UNSUPPORTED for a shape the context's velocity set and LB form do not come in).
  * The arithmetic per site does not depend on the tile shape: results are identical. */
 int lbcad_set_tiles(lbcad_ctx* c, int32_t cfg);
 
@@ -227,8 +232,8 @@ int lbcad_set_state(lbcad_ctx* c, int32_t inst, const void* src, size_t bytes, i
  * Runs the forward from the current state (the context advances by nsteps, as with
  * lbcad_step), storing a checkpoint every ckpt_every steps; then, segment by segment in
  * reverse, replays the segment's states and applies the vector-Jacobian product of each
- * step (per-site Jacobians by forward-mode dual numbers through the step's own
- * arithmetic).  Writes dJ/dzeta and dJ/dq0 (accumulated in FP64; q0 enters through H and
+ * step (per-site vector-Jacobian products by hand-written reverse sweeps through the
+ * step's own arithmetic).  Writes dJ/dzeta and dJ/dq0 (accumulated in FP64; q0 enters through H and
  * sigma, the initial Q held fixed), dJ/dQ(t0) for the five stored Q components
  * ([5][z][y][x], host FP64, may be NULL) and J itself.  Device memory grows by
  * (ceil(nsteps/ckpt_every) + ckpt_every + 2) states plus 154 values per site, owned by the

@@ -15,6 +15,12 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblbcad.so")
 UNITS = ["lbcad_runtime.cu", "lbcad_f32.cu", "lbcad_f64.cu", "lbcad_noalloc.cu", "lbcad_adj_f32.cu",
          "lbcad_adj_f64.cu"]
+# Units with FP32 kernels flush FP32 subnormals to zero.  Subnormal values (below 1.2e-38)
+# appear where the first disturbances spread into the quiescent fluid around the droplet and
+# slow the FP32 arithmetic: the 128^3 step took 0.306 ms over its first 50 steps and 0.240
+# ms later, against 0.234 ms throughout when flushed.  They lie some 30 orders of magnitude
+# below the FP32 resolution of every field.  (-ftz leaves FP64 arithmetic alone.)
+FTZ_UNITS = {"lbcad_f32.cu", "lbcad_noalloc.cu", "lbcad_adj_f32.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -34,7 +40,7 @@ def up_to_date() -> bool:
     if not os.path.exists(LIB):
         return False
     t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(s) <= t for s in _sources())
+    return all(os.path.getmtime(s) <= t for s in _sources() + [os.path.abspath(__file__)])
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -49,7 +55,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_one(u):
         src = os.path.join(CSRC, u)
         obj = os.path.join(OBJ, u.replace(".cu", ".o"))
-        r = subprocess.run([cc, *flags, "-c", src, "-o", obj], capture_output=True, text=True)
+        extra = ["-ftz=true"] if u in FTZ_UNITS else []
+        r = subprocess.run([cc, *flags, *extra, "-c", src, "-o", obj], capture_output=True, text=True)
         with open(obj + ".log", "w") as fh:
             fh.write(r.stdout + r.stderr)
         if r.returncode != 0:

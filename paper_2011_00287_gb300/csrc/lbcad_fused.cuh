@@ -20,6 +20,8 @@
 // launch covers every instance of a batch.
 #pragma once
 
+#include <type_traits>
+
 #include "lbcad_kernels.cuh"
 
 namespace lbcad {
@@ -131,12 +133,79 @@ __device__ __forceinline__ void store_sigma(T* plane, int k, const T sig[9], T m
   }
 }
 
+// Component c (= 3a + b) of the stress at an offset, through an accessor of stress pairs.
+template <typename T, class A>
+__device__ __forceinline__ T pair_comp(const A& acc, int c, int cx, int cy, int cz) {
+  const Vec2<T> v = acc.spair(sig_pair(c), cx, cy, cz);
+  return sig_lane(c) ? v.y : v.x;
+}
+
+// The antisymmetric part sigma^A = (sigma - sigma^T)/2 through an accessor of stress pairs
+// (the force of the Eq. 9-11 form); pair 4 holds sigma^A_zz = 0 and no mu.
+template <typename T, class A>
+struct AntiPairAcc {
+  A a;
+  __device__ __forceinline__ T anti(int c, int cx, int cy, int cz) const {
+    const int r = c / 3, k = c - 3 * r;
+    if (r == k) return T(0);
+    return T(0.5) * (pair_comp<T>(a, c, cx, cy, cz) - pair_comp<T>(a, 3 * k + r, cx, cy, cz));
+  }
+  __device__ __forceinline__ Vec2<T> spair(int j, int cx, int cy, int cz) const {
+    if (j == 4) return Vec2<T>{T(0), T(0)};
+    return Vec2<T>{anti(pair_c0(j), cx, cy, cz), anti(pair_c1(j), cx, cy, cz)};
+  }
+};
+
+// The output work of one site (a3 - a5) from the shared-memory tiles: the force, the
+// stencils of a4, the pull of the populations of velocity set V, the order-parameter update
+// and the collision; stores g, Q, psi and u.  FORM 0: F = div sigma, BGK + Guo (Eqs. 6-8).
+// FORM 1: FA = div sigma^A and the equilibrium carrying sigma^S (Eqs. 9-11).  zo, pyo, pxo:
+// offs(zo, pyo, pxo) fills the global offsets of the planes z-1, z, z+1, the rows y-1, y, y+1
+// and the columns x-1, x, x+1, and hs(H) the molecular field of the site; both are called
+// late (after the stencils, after the pulls), so that their values do not hold registers
+// through the earlier work.
+template <typename T, bool SHIFT, class V, int FORM, class A, class Offs, class HS>
+__device__ __forceinline__ void output_site(const InstDesc<T>& I, const Coef<T>& cf, const A& acc, const Offs& offs,
+                                            const HS& hs) {
+  const long long N = I.N;
+  T F[3], lapmu, Wg[3][3], q0[5], qf[6][5], p0, pf[6], u0[3], uf[6];
+  if constexpr (FORM == 0) gather_force<T>(acc, F);
+  else gather_force<T>(AntiPairAcc<T, A>{acc}, F);
+  gather_op<T>(acc, lapmu, Wg, q0, qf, p0, pf, u0, uf);
+  long long zo[3];
+  int pyo[3], pxo[3];
+  offs(zo, pyo, pxo);
+  T g[V::Q];
+#pragma unroll
+  for (int i = 0; i < V::Q; ++i)
+    g[i] = ld(I.g_in + i * N + zo[1 - V::c(i, 2)] + pyo[1 - V::c(i, 1)] + pxo[1 - V::c(i, 0)]);
+  T Hs[5], qn[5], pn, u[3];
+  hs(Hs);
+  op_update<T, false>(cf, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hs, qn, pn);
+  if constexpr (FORM == 0) {
+    lb_collide<T, SHIFT, V>(cf, F, g, u);
+  } else {
+    T sg[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) sg[c] = pair_comp<T>(acc, c, 0, 0, 0);
+    lb_collide_stress<T, SHIFT, V>(cf, F, sg, g, u);
+  }
+  const long long s = zo[1] + pyo[1] + pxo[1];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) I.q_out[k * N + s] = qn[k];
+  I.psi_out[s] = pn;
+#pragma unroll
+  for (int i = 0; i < V::Q; ++i) I.g_out[i * N + s] = g[i];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) I.u_out[a * N + s] = u[a];
+}
+
 // Ring slots of plane p (p >= -2).
 __device__ __forceinline__ int qslot(int p) { return (p + 10) % 5; }
 __device__ __forceinline__ int sslot(int p) { return (p + 9) % 3; }
 __device__ __forceinline__ int uslot(int p) { return (p + 8) % 4; }
 
-template <typename T, bool SHIFT, int TX, int TY>
+template <typename T, bool SHIFT, int TX, int TY, class V, int FORM>
 __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 2 : 1)
     k_step_fused(const InstDesc<T>* __restrict__ D, const FusedTile* __restrict__ tiles, int ntiles,
                  long long total) {
@@ -187,7 +256,6 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
     const T* __restrict__ qin = I.q_in;
     const T* __restrict__ pin = I.psi_in;
     const T* __restrict__ uin = I.u_in;
-    const T* __restrict__ gin = I.g_in;
 
     __syncthreads();  // the previous segment is done with the shared tiles
     for (int k = tid; k < QW; k += NT) xmap[k] = wrapmod(tl.x0 + k - 2, nx);
@@ -309,29 +377,22 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
           acc.spl[j] = sS + sslot(z - 1 + j) * G::SSLOT;
           acc.upl[j] = sU + uslot(z - 1 + j) * G::USLOT;
         }
-        T F[3], lapmu, Wg[3][3], q0[5], qf[6][5], p0, pf[6], u0[3], uf[6];
-        gather_update<T>(acc, F, lapmu, Wg, q0, qf, p0, pf, u0, uf);
-        const long long zo[3] = {(long long)wrap_plane(z - 1, nz) * plane, (long long)z * plane,
-                                 (long long)wrap_plane(z + 1, nz) * plane};
-        // in-plane offsets of this thread's output site and its x, y neighbours (pull)
-        const int pxo[3] = {xmap[tx + 1], xmap[tx + 2], xmap[tx + 3]};
-        const int pyo[3] = {ymap[ty + 1], ymap[ty + 2], ymap[ty + 3]};
-        T g[19];
+        // offsets of this thread's output site and its neighbours (pull)
+        auto offs = [&](long long zo[3], int pyo[3], int pxo[3]) {
+          zo[0] = (long long)wrap_plane(z - 1, nz) * plane;
+          zo[1] = (long long)z * plane;
+          zo[2] = (long long)wrap_plane(z + 1, nz) * plane;
 #pragma unroll
-        for (int i = 0; i < 19; ++i) {
-          const int cx = lat_c(i, 0), cy = lat_c(i, 1), cz = lat_c(i, 2);
-          g[i] = ld(gin + i * N + zo[1 - cz] + pyo[1 - cy] + pxo[1 - cx]);
-        }
-        T qn[5], pn, u[3];
-        update_math<T, SHIFT>(cf, F, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hc, g, qn, pn, u);
-        const long long s = zo[1] + pyo[1] + pxo[1];
+          for (int j = 0; j < 3; ++j) {
+            pyo[j] = ymap[ty + 1 + j];
+            pxo[j] = xmap[tx + 1 + j];
+          }
+        };
+        auto hs = [&](T H[5]) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) I.q_out[k * N + s] = qn[k];
-        I.psi_out[s] = pn;
-#pragma unroll
-        for (int i = 0; i < 19; ++i) I.g_out[i * N + s] = g[i];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) I.u_out[a * N + s] = u[a];
+          for (int c = 0; c < 5; ++c) H[c] = Hc[c];
+        };
+        output_site<T, SHIFT, V, FORM>(I, cf, acc, offs, hs);
       }
 #pragma unroll
       for (int k = 0; k < 5; ++k) Hc[k] = Hn[k];
@@ -357,14 +418,6 @@ struct PipeGeom {
   static constexpr int IP = TX * TY;
   static constexpr int NQS = 6, NSS = 4, NHS = 3, NUS = 4;
   static_assert(QP <= NT && SP <= NT && SP <= 2 * NS && NO >= IP, "site counts per thread");
-  // sigma rounds: NFULL full rounds of NS sites, then the RLAST remaining sites on NWL
-  // warps of LL lanes, NWL a multiple of 4 where possible so that the four schedulers of
-  // the SM each get the same share of the last round
-  static constexpr int NFULL = SP / NS, RLAST = SP - NFULL * NS;
-  static constexpr int NWL0 = ((RLAST + 31) / 32 + 3) / 4 * 4;
-  static constexpr int NWL = NWL0 < NS / 32 ? NWL0 : NS / 32;
-  static constexpr int LL = RLAST > 0 ? (RLAST + NWL - 1) / NWL : 0;
-  static_assert(LL <= 32 && NWL * LL >= RLAST, "last sigma round");
   template <typename T>
   static constexpr size_t bytes() {
     return ((size_t)NQS * 6 * QP + (size_t)NSS * 10 * SP + (size_t)NHS * 5 * IP + (size_t)NUS * 3 * SP) * sizeof(T) +
@@ -388,7 +441,7 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
   if constexpr (sizeof(T) == 4) cp_async4(dst, src); else cp_async8(dst, src);
 }
 
-template <typename T, bool SHIFT, int TY, int NS>
+template <typename T, bool SHIFT, int TY, int NS, class V, int FORM>
 __global__ void __launch_bounds__(512, 1)
     k_step_pipe(const InstDesc<T>* __restrict__ D, const FusedTile* __restrict__ tiles, int ntiles, long long total) {
   using G = PipeGeom<TY, NS>;
@@ -428,7 +481,6 @@ __global__ void __launch_bounds__(512, 1)
     const T* __restrict__ qin = I.q_in;
     const T* __restrict__ pin = I.psi_in;
     const T* __restrict__ uin = I.u_in;
-    const T* __restrict__ gin = I.g_in;
 
     __syncthreads();
     for (int k = tid; k < QW; k += G::NT) xmap[k] = wrapmod(tl.x0 + k - 2, nx);
@@ -493,8 +545,8 @@ __global__ void __launch_bounds__(512, 1)
       } else if (k - 1 >= zb) {
         // output of plane z = k-1
         const int z = k - 1;
-        const long long zo[3] = {(long long)wrap_plane(z - 1, nz) * plane, (long long)z * plane,
-                                 (long long)wrap_plane(z + 1, nz) * plane};
+        const long long zo3[3] = {(long long)wrap_plane(z - 1, nz) * plane, (long long)z * plane,
+                                  (long long)wrap_plane(z + 1, nz) * plane};
         const int site = tid - G::NS;
         const int tx = site % TX, ty = site / TX;
         if (site < G::IP && tl.x0 + tx < nx && tl.y0 + ty < ny) {
@@ -507,29 +559,22 @@ __global__ void __launch_bounds__(512, 1)
             acc.spl[j] = sS + s4(z - 1 + j) * SSLOT;
             acc.upl[j] = sU + s4(z - 1 + j) * USLOT;
           }
-          T F[3], lapmu, Wg[3][3], q0[5], qf[6][5], p0, pf[6], u0[3], uf[6];
-          gather_update<T>(acc, F, lapmu, Wg, q0, qf, p0, pf, u0, uf);
-          const int pxo[3] = {xmap[tx + 1], xmap[tx + 2], xmap[tx + 3]};
-          const int pyo[3] = {ymap[ty + 1], ymap[ty + 2], ymap[ty + 3]};
-          T g[19];
-#pragma unroll
-          for (int i = 0; i < 19; ++i) {
-            const int cx = lat_c(i, 0), cy = lat_c(i, 1), cz = lat_c(i, 2);
-            g[i] = ld(gin + i * N + zo[1 - cz] + pyo[1 - cy] + pxo[1 - cx]);
-          }
-          T Hs[5];
+          T Hs[5];  // read before the stencils: measured faster here than a late read
 #pragma unroll
           for (int c = 0; c < 5; ++c) Hs[c] = sH[h3(z) * HSLOT + c * G::IP + site];
-          T qn[5], pn, u[3];
-          update_math<T, SHIFT>(cf, F, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hs, g, qn, pn, u);
-          const long long s = zo[1] + pyo[1] + pxo[1];
+          auto hs = [&](T H[5]) {
 #pragma unroll
-          for (int c = 0; c < 5; ++c) I.q_out[c * N + s] = qn[c];
-          I.psi_out[s] = pn;
+            for (int c = 0; c < 5; ++c) H[c] = Hs[c];
+          };
+          auto offs = [&](long long zo[3], int pyo[3], int pxo[3]) {
 #pragma unroll
-          for (int i = 0; i < 19; ++i) I.g_out[i * N + s] = g[i];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) I.u_out[a * N + s] = u[a];
+            for (int j = 0; j < 3; ++j) {
+              zo[j] = zo3[j];
+              pyo[j] = ymap[ty + 1 + j];
+              pxo[j] = xmap[tx + 1 + j];
+            }
+          };
+          output_site<T, SHIFT, V, FORM>(I, cf, acc, offs, hs);
         }
       }
       cp_async_commit_wait_all();
@@ -538,18 +583,18 @@ __global__ void __launch_bounds__(512, 1)
   }
 }
 
-template <typename T, bool SHIFT, int TX, int TY>
+template <typename T, bool SHIFT, int TX, int TY, class V, int FORM>
 cudaError_t launch_cfg(const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles, long long total, int grid,
                        cudaStream_t s) {
   using G = FusedGeom<T, TX, TY>;
-  k_step_fused<T, SHIFT, TX, TY><<<grid, G::NT, G::bytes, s>>>(d_desc, tiles, ntiles, total);
+  k_step_fused<T, SHIFT, TX, TY, V, FORM><<<grid, G::NT, G::bytes, s>>>(d_desc, tiles, ntiles, total);
   return cudaGetLastError();
 }
 
-template <typename T, bool SHIFT, int TX, int TY>
+template <typename T, bool SHIFT, int TX, int TY, class V, int FORM>
 cudaError_t prepare_cfg(FusedCfg* cfg) {
   using G = FusedGeom<T, TX, TY>;
-  auto k = k_step_fused<T, SHIFT, TX, TY>;
+  auto k = k_step_fused<T, SHIFT, TX, TY, V, FORM>;
   cfg->tx = TX;
   cfg->ty = TY;
   cfg->threads = G::NT;
@@ -560,16 +605,18 @@ cudaError_t prepare_cfg(FusedCfg* cfg) {
 }
 
 // Tile shapes offered to the autotuner: 32x8 (two blocks per SM in FP32), 32x16 and
-// 64x8 (one block per SM, fewer redundant halo sites).  FP64 only fits 32x8.
+// 64x8 (one block per SM, fewer redundant halo sites), and the pipelined schedules.  FP64
+// only fits 32x8.  The D3Q15 and Eq. 9-11 variants come in 32x8 and the pipelined 32x8
+// schedule with 8 + 8 warps.
 template <typename T, bool SHIFT>
 int LaunchFused<T, SHIFT>::num_configs() {
   return sizeof(T) == 4 ? 7 : 1;
 }
 
-template <typename T, bool SHIFT, int TY, int NS>
+template <typename T, bool SHIFT, int TY, int NS, class V, int FORM>
 cudaError_t prepare_pipe(FusedCfg* cfg) {
   using G = PipeGeom<TY, NS>;
-  auto k = k_step_pipe<T, SHIFT, TY, NS>;
+  auto k = k_step_pipe<T, SHIFT, TY, NS, V, FORM>;
   cfg->tx = G::TX;
   cfg->ty = G::TY;
   cfg->threads = G::NT;
@@ -579,40 +626,71 @@ cudaError_t prepare_pipe(FusedCfg* cfg) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cfg->blocks_per_sm, k, G::NT, cfg->smem);
 }
 
-template <typename T, bool SHIFT, int TY, int NS>
+template <typename T, bool SHIFT, int TY, int NS, class V, int FORM>
 cudaError_t launch_pipe(const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles, long long total, int grid,
                         cudaStream_t s) {
   using G = PipeGeom<TY, NS>;
-  k_step_pipe<T, SHIFT, TY, NS><<<grid, G::NT, G::template bytes<T>(), s>>>(d_desc, tiles, ntiles, total);
+  k_step_pipe<T, SHIFT, TY, NS, V, FORM><<<grid, G::NT, G::template bytes<T>(), s>>>(d_desc, tiles, ntiles, total);
   return cudaGetLastError();
 }
 
-template <typename T, bool SHIFT>
-cudaError_t LaunchFused<T, SHIFT>::prepare(int cfg_index, FusedCfg* cfg) {
-  if constexpr (sizeof(T) == 4) {
-    if (cfg_index == 1) return prepare_cfg<T, SHIFT, 32, 16>(cfg);
-    if (cfg_index == 2) return prepare_cfg<T, SHIFT, 64, 8>(cfg);
-    if (cfg_index == 3) return prepare_pipe<T, SHIFT, 8, 256>(cfg);
-    if (cfg_index == 4) return prepare_pipe<T, SHIFT, 8, 192>(cfg);
-    if (cfg_index == 5) return prepare_pipe<T, SHIFT, 6, 288>(cfg);
-    if (cfg_index == 6) return prepare_pipe<T, SHIFT, 6, 320>(cfg);
+// One variant (velocity set V, LB form FORM): cfg_index -> tile shape.
+template <typename T, bool SHIFT, class V, int FORM>
+struct FusedVariant {
+  static constexpr bool ALL = std::is_same<V, VelD3Q19>::value && FORM == 0;
+  static cudaError_t prepare(int k, FusedCfg* cfg) {
+    if constexpr (sizeof(T) == 4) {
+      if constexpr (ALL) {
+        if (k == 1) return prepare_cfg<T, SHIFT, 32, 16, V, FORM>(cfg);
+        if (k == 2) return prepare_cfg<T, SHIFT, 64, 8, V, FORM>(cfg);
+        if (k == 4) return prepare_pipe<T, SHIFT, 8, 192, V, FORM>(cfg);
+        if (k == 5) return prepare_pipe<T, SHIFT, 6, 288, V, FORM>(cfg);
+        if (k == 6) return prepare_pipe<T, SHIFT, 6, 320, V, FORM>(cfg);
+      }
+      if (k == 3) return prepare_pipe<T, SHIFT, 8, 256, V, FORM>(cfg);
+    }
+    if (k == 0) return prepare_cfg<T, SHIFT, 32, 8, V, FORM>(cfg);
+    return k >= 0 && k < LaunchFused<T, SHIFT>::num_configs() ? cudaErrorNotSupported : cudaErrorInvalidValue;
   }
-  if (cfg_index == 0) return prepare_cfg<T, SHIFT, 32, 8>(cfg);
+  static cudaError_t step(int k, const InstDesc<T>* d, const FusedTile* t, int nt, long long total, int grid,
+                          cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+      if constexpr (ALL) {
+        if (k == 1) return launch_cfg<T, SHIFT, 32, 16, V, FORM>(d, t, nt, total, grid, s);
+        if (k == 2) return launch_cfg<T, SHIFT, 64, 8, V, FORM>(d, t, nt, total, grid, s);
+        if (k == 4) return launch_pipe<T, SHIFT, 8, 192, V, FORM>(d, t, nt, total, grid, s);
+        if (k == 5) return launch_pipe<T, SHIFT, 6, 288, V, FORM>(d, t, nt, total, grid, s);
+        if (k == 6) return launch_pipe<T, SHIFT, 6, 320, V, FORM>(d, t, nt, total, grid, s);
+      }
+      if (k == 3) return launch_pipe<T, SHIFT, 8, 256, V, FORM>(d, t, nt, total, grid, s);
+    }
+    if (k == 0) return launch_cfg<T, SHIFT, 32, 8, V, FORM>(d, t, nt, total, grid, s);
+    return cudaErrorInvalidValue;
+  }
+};
+
+// variant = (velocity set D3Q15 ? 1 : 0) + 2 * (Eq. 9-11 form ? 1 : 0)
+template <typename T, bool SHIFT>
+cudaError_t LaunchFused<T, SHIFT>::prepare(int variant, int cfg_index, FusedCfg* cfg) {
+  switch (variant) {
+    case 0: return FusedVariant<T, SHIFT, VelD3Q19, 0>::prepare(cfg_index, cfg);
+    case 1: return FusedVariant<T, SHIFT, VelD3Q15, 0>::prepare(cfg_index, cfg);
+    case 2: return FusedVariant<T, SHIFT, VelD3Q19, 1>::prepare(cfg_index, cfg);
+    case 3: return FusedVariant<T, SHIFT, VelD3Q15, 1>::prepare(cfg_index, cfg);
+  }
   return cudaErrorInvalidValue;
 }
 
 template <typename T, bool SHIFT>
-cudaError_t LaunchFused<T, SHIFT>::step(int cfg_index, const InstDesc<T>* d_desc, const FusedTile* tiles,
-                                        int ntiles, long long total, int grid, cudaStream_t s) {
-  if constexpr (sizeof(T) == 4) {
-    if (cfg_index == 1) return launch_cfg<T, SHIFT, 32, 16>(d_desc, tiles, ntiles, total, grid, s);
-    if (cfg_index == 2) return launch_cfg<T, SHIFT, 64, 8>(d_desc, tiles, ntiles, total, grid, s);
-    if (cfg_index == 3) return launch_pipe<T, SHIFT, 8, 256>(d_desc, tiles, ntiles, total, grid, s);
-    if (cfg_index == 4) return launch_pipe<T, SHIFT, 8, 192>(d_desc, tiles, ntiles, total, grid, s);
-    if (cfg_index == 5) return launch_pipe<T, SHIFT, 6, 288>(d_desc, tiles, ntiles, total, grid, s);
-    if (cfg_index == 6) return launch_pipe<T, SHIFT, 6, 320>(d_desc, tiles, ntiles, total, grid, s);
+cudaError_t LaunchFused<T, SHIFT>::step(int variant, int cfg_index, const InstDesc<T>* d_desc,
+                                        const FusedTile* tiles, int ntiles, long long total, int grid,
+                                        cudaStream_t s) {
+  switch (variant) {
+    case 0: return FusedVariant<T, SHIFT, VelD3Q19, 0>::step(cfg_index, d_desc, tiles, ntiles, total, grid, s);
+    case 1: return FusedVariant<T, SHIFT, VelD3Q15, 0>::step(cfg_index, d_desc, tiles, ntiles, total, grid, s);
+    case 2: return FusedVariant<T, SHIFT, VelD3Q19, 1>::step(cfg_index, d_desc, tiles, ntiles, total, grid, s);
+    case 3: return FusedVariant<T, SHIFT, VelD3Q15, 1>::step(cfg_index, d_desc, tiles, ntiles, total, grid, s);
   }
-  if (cfg_index == 0) return launch_cfg<T, SHIFT, 32, 8>(d_desc, tiles, ntiles, total, grid, s);
   return cudaErrorInvalidValue;
 }
 

@@ -111,13 +111,15 @@ struct FusedCfg {
   size_t smem = 0;
 };
 
-// The fused one-kernel step (lbcad_fused.cuh), in several tile shapes.
+// The fused one-kernel step (lbcad_fused.cuh), in several tile shapes, for each variant
+// of the LB part: variant = (D3Q15 ? 1 : 0) + 2 * (Eq. 9-11 form ? 1 : 0).  prepare returns
+// cudaErrorNotSupported for a tile shape the variant does not come in.
 template <typename T, bool SHIFT>
 struct LaunchFused {
   static int num_configs();
-  static cudaError_t prepare(int cfg_index, FusedCfg* cfg);
-  static cudaError_t step(int cfg_index, const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles,
-                          long long total, int grid, cudaStream_t s);
+  static cudaError_t prepare(int variant, int cfg_index, FusedCfg* cfg);
+  static cudaError_t step(int variant, int cfg_index, const InstDesc<T>* d_desc, const FusedTile* tiles,
+                          int ntiles, long long total, int grid, cudaStream_t s);
 };
 
 // Buffers of one reverse step of the adjoint (lbcad_adjoint.cuh).

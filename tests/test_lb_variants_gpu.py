@@ -1,5 +1,5 @@
 """The D3Q15 velocity set and the stress-in-equilibrium LB form (Eqs. 9-11) on the GPU
-staged path against the FP64 oracle, through the C ABI.
+fused path (their default) and the staged path against the FP64 oracle, through the C ABI.
 
 Tolerances: FP64 within 1e-12 max abs per field after 10 steps; FP32 within 1e-5 relative L2
 per field after 100 steps for D3Q15 with the body force, 1e-4 for the stress-in-equilibrium form
@@ -75,15 +75,18 @@ def test_velocity_set_tables_match_the_oracle():
         assert np.array_equal(cl, co[perm]) and np.array_equal(wl, wo[perm])
 
 
+@pytest.mark.parametrize("path", ["fused", "staged"])
 @pytest.mark.parametrize("name", list(VARIANTS))
 @pytest.mark.parametrize("shape,kw", [
     ((32, 32, 32), KW0),
     ((21, 13, 10), dict(R=4.0, p0=8.0, zeta=0.01, W=0.05)),
     ((4, 5, 6), dict(R=2.0, p0=6.0)),
 ])
-def test_fp64_parity_10_steps(shape, kw, name):
+def test_fp64_parity_10_steps(shape, kw, name, path):
     var = VARIANTS[name]
     sim = L.Simulation([shape], [_lib_params(shape, L.FP64, **kw, **_lib_kw(var))], seed=2)
+    if path == "staged":
+        sim.set_path(L.lbcad.PATH_STAGED)
     got0 = sim.get_fields(0)
     ref = _oracle(shape, seed=2, **kw, **var)
     assert np.array_equal(got0["g"], ref.f[_perm(var["lattice"])])
@@ -103,6 +106,48 @@ def test_fp32_parity_100_steps(name):
     ref = _oracle(shape, seed=1, **KW0, tau=tau, **var).step(n)
     print(name, "fp32 rel L2 after %d steps:" % n, _compare(sim.get_fields(0), ref, var["lattice"], False,
                                                            FP32_TOL[name]))
+
+
+@pytest.mark.parametrize("name", list(VARIANTS))
+@pytest.mark.parametrize("prec", [L.FP32, L.FP64])
+def test_fused_shapes_and_staged_path_agree(name, prec):
+    """Both fused tile shapes of a variant give identical results (the per-site arithmetic
+    does not depend on the shape), and the staged path, a different kernel split of the same
+    per-site functions, agrees to rounding (after 20 steps, within a tenth of the variant's
+    100-step FP32 parity bound)."""
+    var = VARIANTS[name]
+    shape = (40, 18, 12)
+    kw = dict(R=5.0, p0=8.0, zeta=0.01, tau=TAU_STABLE[name])
+    sims = [L.Simulation([shape], [_lib_params(shape, prec, **kw, **_lib_kw(var))], seed=3) for _ in range(3)]
+    if prec == L.FP32:
+        sims[1].set_tiles(3)
+    sims[2].set_path(L.lbcad.PATH_STAGED)
+    for s_ in sims:
+        s_.step(20)
+    f = [s_.get_fields(0) for s_ in sims]
+    _, w = O.lattice(var["lattice"])
+    wq = w[_perm(var["lattice"])].reshape(-1, 1, 1, 1)
+    for k in f[0]:
+        assert np.array_equal(f[0][k], f[1][k]), k
+        if prec == L.FP64:
+            assert np.abs(f[0][k] - f[2][k]).max() <= 1e-13, k
+        else:
+            x, y = (f[0][k] - wq, f[2][k] - wq) if k == "g" else (f[0][k], f[2][k])
+            # the staged split rounds differently; a tenth of the 100-step parity bound
+            assert _rel_l2(x, y) <= FP32_TOL[name] / 10, k
+
+
+def test_variant_contexts_refuse_what_covers_the_default_lb_only():
+    shape = (8, 8, 8)
+    for var in VARIANTS.values():
+        sim = L.Simulation([shape], [_lib_params(shape, L.FP32, **_lib_kw(var))], seed=1)
+        for call in (lambda: sim.set_path(L.lbcad.PATH_TWO_KERNEL), lambda: sim.set_tiles(1),
+                     lambda: sim.set_tiles(6), lambda: sim.adjoint(2, 1)):
+            with pytest.raises(L.LbcadError):
+                call()
+        cfg, ms = sim.autotune(1)
+        assert cfg in (0, 3) and all(m < 0 for i, m in enumerate(ms) if i not in (0, 3))
+        sim.step(2)
 
 
 def test_all_options_together_match_the_oracle():
