@@ -166,6 +166,7 @@ def cpu_oracle_rate(n, budget_s=12.0, max_steps=None):
     steps, t0 = 0, time.perf_counter()
     while True:
         s.step(1)
+        s.observables()  # a6 of every step, as the GPU step forms them
         steps += 1
         el = time.perf_counter() - t0
         if el >= budget_s or (max_steps and steps >= max_steps):
@@ -246,6 +247,8 @@ def main():
     ap.add_argument("--size", type=int, default=128)
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--tiles", type=int, default=None,
+                    help="fixed fused tile shape (index into the autotuner's candidates) instead of autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -281,11 +284,18 @@ def main():
     K, W = args.steps, args.warmup
     # replicas: each rank advances its own copy of the workload (weak scaling)
     sim = L.Simulation([(n, n, n)], [workload_params(L, n, L.FP32)], seed=1 + rank, device=local)
-    tile_cfg, tile_ms = sim.autotune(5)
+    if args.tiles is None:
+        tile_cfg, tile_ms = sim.autotune(5)
+    else:  # a fixed tile shape (profiling runs): no autotuning launches
+        sim.set_tiles(args.tiles)
+        tile_cfg, tile_ms = args.tiles, [None] * len(TILE_NAMES)
     sim.step(W)
     sim.sync()
     if dist:
         dist.barrier()
+    # every timed step is the whole hot path: stencils, fields, stress and force, the order-
+    # parameter update, the LB collision and streaming, and the FP64 conserved and centroid
+    # sums of the new state (fused into the same kernel; the library default)
     with ClockSampler(local) as clk:
         ms = time_steps(sim, torch, K)
     if dist:
@@ -293,6 +303,15 @@ def main():
     obs = sim.observables(0)
     finite = all(math.isfinite(v) for v in obs)
     value = whole_job_mlups(N, world, ms)
+    # the same step kernel without the sums (for runs that read observables rarely; each
+    # read then costs a separate pass)
+    sim.set_observe(False)
+    sim.step(3)
+    ms_nosums = time_steps(sim, torch, min(K, 1000))
+    sim.set_observe(True)
+    sim.step(1)
+    without_sums = {"mlups": whole_job_mlups(N, world, ms_nosums), "ms_per_step": ms_nosums,
+                    "note": "same step kernel without the fused FP64 sums (lbcad_set_observe(0))"}
 
     # plain FP64 GPU path on the same workload
     fp64 = None
@@ -410,7 +429,8 @@ def main():
     traffic_site = committed_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (traffic_site * N) if traffic_site else None,
-                "kernel": "k_step_fused (one launch = one whole hybrid step)", "algorithmic_bytes_per_site": 200,
+                "kernel": "k_step_pipe (one launch = one whole hybrid step, a6 sums included)",
+                "algorithmic_bytes_per_site": 200,
                 "peak_kind": peak_kind,
                 # the design floor also moves u in and out (224 B per site)
                 "design_bytes_per_site": 224, "design_frac": 224 * N / (ms * 1e-3) / 1e9 / peak,
@@ -443,10 +463,11 @@ def main():
                 "config": {"workload": "active cholesteric droplet 128^3, R=32, pitch 32, zeta=0.005, FP32 "
                                        "shifted populations" if n == 128 else "droplet %d^3" % n,
                            "box": [n, n, n], "parallelism": "replicas" if world > 1 else "single",
-                           "l2": "state %.0f MB per step > 129 MB L2, no flush" % (224 * N / 1e6)},
+                           "l2": "state %.0f MB per step > 129 MB L2, no flush" % (224 * N / 1e6),
+                           "a6": "FP64 mass, psi, momentum and centroid sums of every step, fused"},
                 "roofline": roofline, "roofline_issue": roofline_issue, "cpu_baseline": cpu, "e2e": e2e,
                 "tiles": {"chosen": TILE_NAMES[tile_cfg], "ms_per_cfg": dict(zip(TILE_NAMES, tile_ms))},
-                "gpu_launches": K, "clocks": csum, "fp64_gpu": fp64, "staged_fp32": staged, "lb_variants_fp32": variants, "bulk_fp32": bulk, "adjoint_fp32": adjoint,
+                "gpu_launches": K, "clocks": csum, "step_without_sums": without_sums, "fp64_gpu": fp64, "staged_fp32": staged, "lb_variants_fp32": variants, "bulk_fp32": bulk, "adjoint_fp32": adjoint,
                 "speedup_fp32_vs_fp64": (value / world / fp64["mlups"]) if fp64 else None,
                 "observables_finite": finite}
         print(json.dumps(line))

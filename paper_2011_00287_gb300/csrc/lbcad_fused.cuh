@@ -35,7 +35,14 @@ struct FusedGeom {
   // rings: Q/psi planes z-1 .. z+3, sigma/mu planes z-1 .. z+1, u planes z-1 .. z+2
   static constexpr int NQS = 5, NSS = 3, NUS = 4;
   static constexpr size_t elems = (size_t)NQS * QSLOT + (size_t)NSS * SSLOT + (size_t)NUS * USLOT;
-  static constexpr size_t bytes = elems * sizeof(T) + (QW + QH) * sizeof(int);
+  static constexpr int NW = NT / 32;  // warps adding to the a6 sums
+  // a6 (kernels with the sums): per-warp accumulators [NW][12][2] in T, then the segment's 12
+  // FP64 values
+  static constexpr size_t obs_off = (elems * sizeof(T) + (QW + QH) * sizeof(int) + 15) / 16 * 16;
+  static constexpr size_t seg_off = obs_off + (size_t)NW * 24 * sizeof(T);
+  static constexpr size_t bytes_plain = elems * sizeof(T) + (QW + QH) * sizeof(int);
+  static constexpr size_t bytes_obs = seg_off + 12 * sizeof(double);
+  static constexpr size_t bytes(bool obs) { return obs ? bytes_obs : bytes_plain; }
   static constexpr int NHALO = SP - NT;   // halo sites of the sigma phase (second round)
   static constexpr int NLOAD = NT - NHALO;  // threads free to prefetch during that round
   static_assert(NHALO > 0 && NHALO < NT, "halo sites must fit in one extra round");
@@ -95,6 +102,18 @@ __device__ __forceinline__ Vec2<T> lds2(const T* p) {
     return Vec2<T>{v.x, v.y};
   } else {
     const double2 v = *reinterpret_cast<const double2*>(p);
+    return Vec2<T>{v.x, v.y};
+  }
+}
+
+// An aligned pair from global memory through the read-only path.
+template <typename T>
+__device__ __forceinline__ Vec2<T> ldg2(const T* p) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return Vec2<T>{v.x, v.y};
+  } else {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
     return Vec2<T>{v.x, v.y};
   }
 }
@@ -160,35 +179,36 @@ struct AntiPairAcc {
 // stencils of a4, the pull of the populations of velocity set V, the order-parameter update
 // and the collision; stores g, Q, psi and u.  FORM 0: F = div sigma, BGK + Guo (Eqs. 6-8).
 // FORM 1: FA = div sigma^A and the equilibrium carrying sigma^S (Eqs. 9-11).  zo, pyo, pxo:
-// offs(zo, pyo, pxo) fills the global offsets of the planes z-1, z, z+1, the rows y-1, y, y+1
-// and the columns x-1, x, x+1, and hs(H) the molecular field of the site; both are called
-// late (after the stencils, after the pulls), so that their values do not hold registers
-// through the earlier work.
-template <typename T, bool SHIFT, class V, int FORM, class A, class Offs, class HS>
+// offs(zo, pyo, pxo, xyz) fills the global offsets of the planes z-1, z, z+1, the rows y-1, y,
+// y+1 and the columns x-1, x, x+1 and the site's coordinates, and hs(H) the molecular field of
+// the site; both are called late (after the stencils, after the pulls), so that their values
+// do not hold registers through the earlier work.  ob (OBS): the site's share of the a6 sums
+// of the new state (see FusedObs).
+template <typename T, bool SHIFT, class V, int FORM, bool OBS, class A, class Offs, class HS>
 __device__ __forceinline__ void output_site(const InstDesc<T>& I, const Coef<T>& cf, const A& acc, const Offs& offs,
-                                            const HS& hs) {
+                                            const HS& hs, T ob[12]) {
   const long long N = I.N;
   T F[3], lapmu, Wg[3][3], q0[5], qf[6][5], p0, pf[6], u0[3], uf[6];
   if constexpr (FORM == 0) gather_force<T>(acc, F);
   else gather_force<T>(AntiPairAcc<T, A>{acc}, F);
   gather_op<T>(acc, lapmu, Wg, q0, qf, p0, pf, u0, uf);
   long long zo[3];
-  int pyo[3], pxo[3];
-  offs(zo, pyo, pxo);
+  int pyo[3], pxo[3], xyz[3];
+  offs(zo, pyo, pxo, xyz);
   T g[V::Q];
 #pragma unroll
   for (int i = 0; i < V::Q; ++i)
     g[i] = ld(I.g_in + i * N + zo[1 - V::c(i, 2)] + pyo[1 - V::c(i, 1)] + pxo[1 - V::c(i, 0)]);
-  T Hs[5], qn[5], pn, u[3];
+  T Hs[5], qn[5], pn, u[3], mom[4];
   hs(Hs);
   op_update<T, false>(cf, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hs, qn, pn);
   if constexpr (FORM == 0) {
-    lb_collide<T, SHIFT, V>(cf, F, g, u);
+    lb_collide<T, SHIFT, V>(cf, F, g, u, OBS ? mom : nullptr);
   } else {
     T sg[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) sg[c] = pair_comp<T>(acc, c, 0, 0, 0);
-    lb_collide_stress<T, SHIFT, V>(cf, F, sg, g, u);
+    lb_collide_stress<T, SHIFT, V>(cf, F, sg, g, u, OBS ? mom : nullptr);
   }
   const long long s = zo[1] + pyo[1] + pxo[1];
 #pragma unroll
@@ -198,6 +218,128 @@ __device__ __forceinline__ void output_site(const InstDesc<T>& I, const Coef<T>&
   for (int i = 0; i < V::Q; ++i) I.g_out[i * N + s] = g[i];
 #pragma unroll
   for (int a = 0; a < 3; ++a) I.u_out[a * N + s] = u[a];
+  // a6: mass, psi and momentum of the new state, and phi_c with its centroid moments
+  if constexpr (OBS) {
+    const T pc = T(0.5) * (T(1) + pn);
+    ob[0] = mom[0];
+    ob[1] = pn;
+    ob[2] = mom[1];
+    ob[3] = mom[2];
+    ob[4] = mom[3];
+    ob[11] = pc;
+    const Vec2<T> tx = ldg2(I.trig + 2 * xyz[0]);
+    const Vec2<T> ty = ldg2(I.trig + 2 * (I.nx + xyz[1]));
+    const Vec2<T> tz = ldg2(I.trig + 2 * (I.nx + I.ny + xyz[2]));
+    ob[5] = pc * tx.x;
+    ob[6] = pc * ty.x;
+    ob[7] = pc * tz.x;
+    ob[8] = pc * tx.y;
+    ob[9] = pc * ty.y;
+    ob[10] = pc * tz.y;
+  }
+}
+
+// The a6 sums within a block.  Per plane they are added in the compute type T: FP64
+// arithmetic is slow on this part, and a few FP64 operations per plane on the critical path of
+// the step cost a third of its speed.  Each warp keeps Kahan-compensated sums (sum,
+// compensation) of the twelve values, so that summing over the planes of a segment loses
+// nothing to T's rounding; FP64 takes over at the end of the segment.
+
+// Butterfly sum of the twelve values across the warp (every lane receives the sums), then
+// lane k < 12 adds value k to the warp's accumulator acc_w[k] = (sum, compensation).
+template <typename T>
+__device__ __forceinline__ void obs_warp_add(T v[12], T* acc_w) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  }
+  const int lane = threadIdx.x & 31;
+  T mine = T(0);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) mine = lane == k ? v[k] : mine;
+  if (lane < 12) {
+    T* a = acc_w + 2 * lane;
+    const T y = mine - a[1];
+    const T t = a[0] + y;
+    a[1] = (t - a[0]) - y;
+    a[0] = t;
+  }
+}
+
+// The FP64 value k of a segment from nw warp accumulators acc[nw][12][2].
+template <typename T>
+__device__ __forceinline__ double obs_acc_value(const T* acc, int nw, int k) {
+  double v = 0.0;
+  for (int w = 0; w < nw; ++w) v += (double)acc[(w * 12 + k) * 2] - (double)acc[(w * 12 + k) * 2 + 1];
+  return v;
+}
+
+// End of a column segment (all threads, after a barrier): seg[12] (shared memory, written by
+// threads 0-11 before the barrier) goes to the segment's slot; the block that fills the last
+// slot of the instance then sums the instance's slots into ob.latest, each of the twelve
+// values over fixed strided subsets of the slots and then over the subsets in order, so the
+// result does not depend on which block finishes last.  red: shared scratch of at least
+// 12 * (blockDim.x / 12) doubles.  mass_shift = N rho0 with shifted populations.
+__device__ __forceinline__ void obs_segment_end(const FusedObs& ob, int slot, int inst, const double* seg,
+                                                double* red, double mass_shift) {
+  __shared__ int last;
+  const int tid = threadIdx.x;
+  if (tid < 12) {
+    ob.slots[slot * 12 + tid] = seg[tid];
+    __threadfence();
+  }
+  __syncthreads();
+  if (tid == 0) last = atomicAdd(&ob.cnt[inst], 1u) == (unsigned)(ob.nslot[inst] - 1);
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    const int per = blockDim.x / 12;
+    const int lo = ob.slot_lo[inst], hi = ob.slot_hi[inst];
+    if (tid < 12 * per) {
+      const int k = tid % 12, l = tid / 12;
+      double v = 0.0;
+      for (int sl = lo + l; sl < hi; sl += per)
+        if (ob.slot_inst[sl] == inst) v += __ldcg(ob.slots + sl * 12 + k);
+      red[l * 12 + k] = v;
+    }
+    __syncthreads();
+    if (tid < 12) {
+      double v = tid == 0 ? mass_shift : 0.0;
+      for (int l = 0; l < per; ++l) v += red[l * 12 + tid];
+      ob.latest[inst * 12 + tid] = v;
+    }
+    if (tid == 0) ob.cnt[inst] = 0u;
+  }
+  __syncthreads();
+}
+
+// Pipelined kernel: the a6 shares of an output plane (sh[IP][12], site-major, left in shared
+// memory by the output warps) are added up in the next phase by the sigma threads, in the time
+// the sigma group otherwise waits at the plane barrier.  With NR = the largest multiple of 12
+// <= NS, sigma thread t < NR adds the elements t, t + NR, t + 2 NR, ... (all of value t % 12,
+// consecutive addresses across a warp) into its own Kahan accumulator acc[t] = (sum,
+// compensation): no shuffles and no atomics.
+template <typename T, class G>
+__device__ __forceinline__ void obs_sigma_reduce(const T* sh, T* acc) {
+  const int t = threadIdx.x;
+  if (t >= G::NR) return;
+  T v = T(0);
+#pragma unroll 4
+  for (int e = t; e < 12 * G::IP; e += G::NR) v += sh[e];
+  T* a = acc + 2 * t;
+  const T y = v - a[1];
+  const T s = a[0] + y;
+  a[1] = (s - a[0]) - y;
+  a[0] = s;
+}
+
+// The FP64 value k of a pipelined segment from the sigma threads' accumulators.
+template <typename T, class G>
+__device__ __forceinline__ double obs_sigma_value(const T* acc, int k) {
+  double v = 0.0;
+  for (int t = k; t < G::NR; t += 12) v += (double)acc[2 * t] - (double)acc[2 * t + 1];
+  return v;
 }
 
 // Ring slots of plane p (p >= -2).
@@ -205,10 +347,10 @@ __device__ __forceinline__ int qslot(int p) { return (p + 10) % 5; }
 __device__ __forceinline__ int sslot(int p) { return (p + 9) % 3; }
 __device__ __forceinline__ int uslot(int p) { return (p + 8) % 4; }
 
-template <typename T, bool SHIFT, int TX, int TY, class V, int FORM>
+template <typename T, bool SHIFT, int TX, int TY, class V, int FORM, bool OBS>
 __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 2 : 1)
     k_step_fused(const InstDesc<T>* __restrict__ D, const FusedTile* __restrict__ tiles, int ntiles,
-                 long long total) {
+                 long long total, FusedObs ob) {
   using G = FusedGeom<T, TX, TY>;
   constexpr int QW = G::QW, QP = G::QP, SW = G::SW, SH = G::SH, SP = G::SP, NT = G::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -217,6 +359,8 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
   T* sU = sS + G::NSS * G::SSLOT;
   int* xmap = reinterpret_cast<int*>(sU + G::NUS * G::USLOT);  // global x of Q-tile column
   int* ymap = xmap + QW;                                         // global y * nx of Q-tile row
+  T* oacc = reinterpret_cast<T*>(smem_raw + G::obs_off);                 // a6 sums per warp [NW][12][2]
+  double* oseg = reinterpret_cast<double*>(smem_raw + G::seg_off);       // a6 sums of the segment [12]
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
 
@@ -237,6 +381,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
   const long long begin = (total * blockIdx.x) / gridDim.x;
   const long long end = (total * (blockIdx.x + 1)) / gridDim.x;
   long long it = begin;
+  int seg = 0;  // ordinal of the column segment within this block (its a6 slot)
   while (it < end) {
     int lo = 0, hi = ntiles - 1;
     while (lo < hi) {
@@ -260,6 +405,8 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
     __syncthreads();  // the previous segment is done with the shared tiles
     for (int k = tid; k < QW; k += NT) xmap[k] = wrapmod(tl.x0 + k - 2, nx);
     for (int k = tid; k < G::QH; k += NT) ymap[k] = wrapmod(tl.y0 + k - 2, ny) * nx;
+    if constexpr (OBS)
+      for (int k = tid; k < G::NW * 24; k += NT) oacc[k] = T(0);
     __syncthreads();
 
     // planes are loaded by a fixed set of tile positions per thread: their in-plane
@@ -367,6 +514,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
       }
       if (tid >= G::NHALO) prefetch(z + 3, z + 2);
       __syncthreads();
+      T ob6[12] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
       if (z >= zb && tl.x0 + tx < nx && tl.y0 + ty < ny) {
         SmemUpdateAcc<T, QW, QP, SW, SP> acc;
         acc.qc = (ty + 2) * QW + (tx + 2);
@@ -378,7 +526,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
           acc.upl[j] = sU + uslot(z - 1 + j) * G::USLOT;
         }
         // offsets of this thread's output site and its neighbours (pull)
-        auto offs = [&](long long zo[3], int pyo[3], int pxo[3]) {
+        auto offs = [&](long long zo[3], int pyo[3], int pxo[3], int xyz[3]) {
           zo[0] = (long long)wrap_plane(z - 1, nz) * plane;
           zo[1] = (long long)z * plane;
           zo[2] = (long long)wrap_plane(z + 1, nz) * plane;
@@ -387,16 +535,29 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
             pyo[j] = ymap[ty + 1 + j];
             pxo[j] = xmap[tx + 1 + j];
           }
+          xyz[0] = tl.x0 + tx;
+          xyz[1] = tl.y0 + ty;
+          xyz[2] = z;
         };
         auto hs = [&](T H[5]) {
 #pragma unroll
           for (int c = 0; c < 5; ++c) H[c] = Hc[c];
         };
-        output_site<T, SHIFT, V, FORM>(I, cf, acc, offs, hs);
+        output_site<T, SHIFT, V, FORM, OBS>(I, cf, acc, offs, hs, ob6);
       }
+      if constexpr (OBS)
+        if (z >= zb) obs_warp_add<T>(ob6, oacc + (tid >> 5) * 24);
 #pragma unroll
       for (int k = 0; k < 5; ++k) Hc[k] = Hn[k];
     }
+    if constexpr (OBS) {
+      __syncthreads();
+      if (tid < 12) oseg[tid] = obs_acc_value<T>(oacc, G::NW, tid);
+      __syncthreads();
+      obs_segment_end(ob, blockIdx.x * ob.maxseg + seg, tl.inst, oseg, reinterpret_cast<double*>(smem_raw),
+                      SHIFT ? (double)cf.rho0 * (double)N : 0.0);
+    }
+    ++seg;
   }
 }
 
@@ -418,10 +579,29 @@ struct PipeGeom {
   static constexpr int IP = TX * TY;
   static constexpr int NQS = 6, NSS = 4, NHS = 3, NUS = 4;
   static_assert(QP <= NT && SP <= NT && SP <= 2 * NS && NO >= IP, "site counts per thread");
+  static_assert(NS % 32 == 0, "whole warps per group");
+  static constexpr int NR = NS / 12 * 12;  // sigma threads that add up the a6 shares
+  // a6: the output planes' shares [2][IP][12] (double-buffered by plane parity), the sigma
+  // threads' accumulators [NR][2] in T, then the segment's 12 FP64 values
   template <typename T>
-  static constexpr size_t bytes() {
-    return ((size_t)NQS * 6 * QP + (size_t)NSS * 10 * SP + (size_t)NHS * 5 * IP + (size_t)NUS * 3 * SP) * sizeof(T) +
-           (QW + QH) * sizeof(int);
+  __host__ __device__ static constexpr size_t obs_off() {
+    return (((size_t)NQS * 6 * QP + (size_t)NSS * 10 * SP + (size_t)NHS * 5 * IP + (size_t)NUS * 3 * SP) * sizeof(T) +
+            (QW + QH) * sizeof(int) + 15) / 16 * 16;
+  }
+  template <typename T>
+  __host__ __device__ static constexpr size_t acc_off() {
+    return obs_off<T>() + (size_t)2 * IP * 12 * sizeof(T);
+  }
+  template <typename T>
+  __host__ __device__ static constexpr size_t seg_off() {
+    return (acc_off<T>() + (size_t)NR * 2 * sizeof(T) + 7) / 8 * 8;
+  }
+  template <typename T>
+  __host__ __device__ static constexpr size_t bytes(bool obs) {
+    return obs ? seg_off<T>() + 12 * sizeof(double)
+               : ((size_t)NQS * 6 * QP + (size_t)NSS * 10 * SP + (size_t)NHS * 5 * IP + (size_t)NUS * 3 * SP) *
+                         sizeof(T) +
+                     (QW + QH) * sizeof(int);
   }
 };
 
@@ -441,9 +621,10 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
   if constexpr (sizeof(T) == 4) cp_async4(dst, src); else cp_async8(dst, src);
 }
 
-template <typename T, bool SHIFT, int TY, int NS, class V, int FORM>
+template <typename T, bool SHIFT, int TY, int NS, class V, int FORM, bool OBS>
 __global__ void __launch_bounds__(512, 1)
-    k_step_pipe(const InstDesc<T>* __restrict__ D, const FusedTile* __restrict__ tiles, int ntiles, long long total) {
+    k_step_pipe(const InstDesc<T>* __restrict__ D, const FusedTile* __restrict__ tiles, int ntiles, long long total,
+                FusedObs ob) {
   using G = PipeGeom<TY, NS>;
   constexpr int QW = G::QW, QP = G::QP, SW = G::SW, SP = G::SP, TX = G::TX;
   constexpr int QSLOT = 6 * QP, SSLOT = 10 * SP, HSLOT = 5 * G::IP, USLOT = 3 * SP;
@@ -454,6 +635,9 @@ __global__ void __launch_bounds__(512, 1)
   T* sU = sH + G::NHS * HSLOT;
   int* xmap = reinterpret_cast<int*>(sU + G::NUS * USLOT);
   int* ymap = xmap + QW;
+  T* oshare = reinterpret_cast<T*>(smem_raw + G::template obs_off<T>());  // a6 shares [2][IP][12]
+  T* oacc = reinterpret_cast<T*>(smem_raw + G::template acc_off<T>());    // sigma-thread sums [NR][2]
+  double* oseg = reinterpret_cast<double*>(smem_raw + G::template seg_off<T>());
   const int tid = threadIdx.x;
   auto q6 = [](int p) { return (p + 12) % 6; };
   auto s4 = [](int p) { return (p + 12) % 4; };
@@ -462,6 +646,7 @@ __global__ void __launch_bounds__(512, 1)
   const long long begin = (total * blockIdx.x) / gridDim.x;
   const long long end = (total * (blockIdx.x + 1)) / gridDim.x;
   long long it = begin;
+  int seg = 0;  // ordinal of the column segment within this block (its a6 slot)
   while (it < end) {
     int lo = 0, hi = ntiles - 1;
     while (lo < hi) {
@@ -485,6 +670,8 @@ __global__ void __launch_bounds__(512, 1)
     __syncthreads();
     for (int k = tid; k < QW; k += G::NT) xmap[k] = wrapmod(tl.x0 + k - 2, nx);
     for (int k = tid; k < G::QH; k += G::NT) ymap[k] = wrapmod(tl.y0 + k - 2, ny) * nx;
+    if constexpr (OBS)
+      for (int k = tid; k < G::NR * 2; k += G::NT) oacc[k] = T(0);
     __syncthreads();
     // this thread's load sites (at most one Q/psi site and one u site per plane)
     int qoff = 0, uoff = 0;
@@ -542,6 +729,9 @@ __global__ void __launch_bounds__(512, 1)
             for (int c = 0; c < 5; ++c) hd[c * G::IP] = H[c];
           }
         }
+        // a6: the shares of output plane k-2, left by the output warps in the previous phase
+        if constexpr (OBS)
+          if (k - 2 >= zb) obs_sigma_reduce<T, G>(oshare + ((k - 2) & 1) * G::IP * 12, oacc);
       } else if (k - 1 >= zb) {
         // output of plane z = k-1
         const int z = k - 1;
@@ -549,6 +739,7 @@ __global__ void __launch_bounds__(512, 1)
                                   (long long)wrap_plane(z + 1, nz) * plane};
         const int site = tid - G::NS;
         const int tx = site % TX, ty = site / TX;
+        T ob6[12] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
         if (site < G::IP && tl.x0 + tx < nx && tl.y0 + ty < ny) {
           SmemUpdateAcc<T, QW, QP, SW, SP> acc;
           acc.qc = (ty + 2) * QW + (tx + 2);
@@ -566,42 +757,71 @@ __global__ void __launch_bounds__(512, 1)
 #pragma unroll
             for (int c = 0; c < 5; ++c) H[c] = Hs[c];
           };
-          auto offs = [&](long long zo[3], int pyo[3], int pxo[3]) {
+          auto offs = [&](long long zo[3], int pyo[3], int pxo[3], int xyz[3]) {
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
               zo[j] = zo3[j];
               pyo[j] = ymap[ty + 1 + j];
               pxo[j] = xmap[tx + 1 + j];
             }
+            xyz[0] = tl.x0 + tx;
+            xyz[1] = tl.y0 + ty;
+            xyz[2] = z;
           };
-          output_site<T, SHIFT, V, FORM>(I, cf, acc, offs, hs);
+          output_site<T, SHIFT, V, FORM, OBS>(I, cf, acc, offs, hs, ob6);
+        }
+        if (OBS && site < G::IP) {
+          T* dst = oshare + (z & 1) * G::IP * 12 + site * 12;
+#pragma unroll
+          for (int c = 0; c < 12; c += 2) {
+            if constexpr (sizeof(T) == 4) *reinterpret_cast<float2*>(dst + c) = make_float2(ob6[c], ob6[c + 1]);
+            else *reinterpret_cast<double2*>(dst + c) = make_double2(ob6[c], ob6[c + 1]);
+          }
         }
       }
       cp_async_commit_wait_all();
       __syncthreads();
     }
+    if constexpr (OBS) {
+      // the last output plane (ze - 1) has not been added up yet
+      if (ze - 1 >= zb) obs_sigma_reduce<T, G>(oshare + ((ze - 1) & 1) * G::IP * 12, oacc);
+      __syncthreads();
+      if (tid < 12) oseg[tid] = obs_sigma_value<T, G>(oacc, tid);
+      __syncthreads();
+      obs_segment_end(ob, blockIdx.x * ob.maxseg + seg, tl.inst, oseg, reinterpret_cast<double*>(smem_raw),
+                      SHIFT ? (double)cf.rho0 * (double)N : 0.0);
+    }
+    ++seg;
   }
 }
 
 template <typename T, bool SHIFT, int TX, int TY, class V, int FORM>
 cudaError_t launch_cfg(const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles, long long total, int grid,
-                       cudaStream_t s) {
+                       const FusedObs& ob, bool obs, cudaStream_t s) {
   using G = FusedGeom<T, TX, TY>;
-  k_step_fused<T, SHIFT, TX, TY, V, FORM><<<grid, G::NT, G::bytes, s>>>(d_desc, tiles, ntiles, total);
+  if (obs)
+    k_step_fused<T, SHIFT, TX, TY, V, FORM, true><<<grid, G::NT, G::bytes(true), s>>>(d_desc, tiles, ntiles, total, ob);
+  else
+    k_step_fused<T, SHIFT, TX, TY, V, FORM, false><<<grid, G::NT, G::bytes(false), s>>>(d_desc, tiles, ntiles, total,
+                                                                                        ob);
   return cudaGetLastError();
 }
 
+// Both kernels of a tile shape (with and without the a6 sums); the launch resources are those
+// of the one with the sums (more shared memory), so that both run on the same grid.
 template <typename T, bool SHIFT, int TX, int TY, class V, int FORM>
 cudaError_t prepare_cfg(FusedCfg* cfg) {
   using G = FusedGeom<T, TX, TY>;
-  auto k = k_step_fused<T, SHIFT, TX, TY, V, FORM>;
+  auto k0 = k_step_fused<T, SHIFT, TX, TY, V, FORM, false>;
+  auto k1 = k_step_fused<T, SHIFT, TX, TY, V, FORM, true>;
   cfg->tx = TX;
   cfg->ty = TY;
   cfg->threads = G::NT;
-  cfg->smem = G::bytes;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::bytes);
+  cfg->smem = G::bytes(true);
+  cudaError_t e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::bytes(false));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::bytes(true));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cfg->blocks_per_sm, k, G::NT, G::bytes);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cfg->blocks_per_sm, k1, G::NT, G::bytes(true));
 }
 
 // Tile shapes offered to the autotuner: 32x8 (two blocks per SM in FP32), 32x16 and
@@ -616,21 +836,29 @@ int LaunchFused<T, SHIFT>::num_configs() {
 template <typename T, bool SHIFT, int TY, int NS, class V, int FORM>
 cudaError_t prepare_pipe(FusedCfg* cfg) {
   using G = PipeGeom<TY, NS>;
-  auto k = k_step_pipe<T, SHIFT, TY, NS, V, FORM>;
+  auto k0 = k_step_pipe<T, SHIFT, TY, NS, V, FORM, false>;
+  auto k1 = k_step_pipe<T, SHIFT, TY, NS, V, FORM, true>;
   cfg->tx = G::TX;
   cfg->ty = G::TY;
   cfg->threads = G::NT;
-  cfg->smem = G::template bytes<T>();
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg->smem);
+  cfg->smem = G::template bytes<T>(true);
+  cudaError_t e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::template bytes<T>(false));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::template bytes<T>(true));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cfg->blocks_per_sm, k, G::NT, cfg->smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cfg->blocks_per_sm, k1, G::NT, cfg->smem);
 }
 
 template <typename T, bool SHIFT, int TY, int NS, class V, int FORM>
 cudaError_t launch_pipe(const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles, long long total, int grid,
-                        cudaStream_t s) {
+                        const FusedObs& ob, bool obs, cudaStream_t s) {
   using G = PipeGeom<TY, NS>;
-  k_step_pipe<T, SHIFT, TY, NS, V, FORM><<<grid, G::NT, G::template bytes<T>(), s>>>(d_desc, tiles, ntiles, total);
+  if (obs)
+    k_step_pipe<T, SHIFT, TY, NS, V, FORM, true><<<grid, G::NT, G::template bytes<T>(true), s>>>(d_desc, tiles, ntiles,
+                                                                                                 total, ob);
+  else
+    k_step_pipe<T, SHIFT, TY, NS, V, FORM, false><<<grid, G::NT, G::template bytes<T>(false), s>>>(d_desc, tiles, ntiles,
+                                                                                                   total, ob);
   return cudaGetLastError();
 }
 
@@ -653,18 +881,18 @@ struct FusedVariant {
     return k >= 0 && k < LaunchFused<T, SHIFT>::num_configs() ? cudaErrorNotSupported : cudaErrorInvalidValue;
   }
   static cudaError_t step(int k, const InstDesc<T>* d, const FusedTile* t, int nt, long long total, int grid,
-                          cudaStream_t s) {
+                          const FusedObs& ob, bool obs, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
       if constexpr (ALL) {
-        if (k == 1) return launch_cfg<T, SHIFT, 32, 16, V, FORM>(d, t, nt, total, grid, s);
-        if (k == 2) return launch_cfg<T, SHIFT, 64, 8, V, FORM>(d, t, nt, total, grid, s);
-        if (k == 4) return launch_pipe<T, SHIFT, 8, 192, V, FORM>(d, t, nt, total, grid, s);
-        if (k == 5) return launch_pipe<T, SHIFT, 6, 288, V, FORM>(d, t, nt, total, grid, s);
-        if (k == 6) return launch_pipe<T, SHIFT, 6, 320, V, FORM>(d, t, nt, total, grid, s);
+        if (k == 1) return launch_cfg<T, SHIFT, 32, 16, V, FORM>(d, t, nt, total, grid, ob, obs, s);
+        if (k == 2) return launch_cfg<T, SHIFT, 64, 8, V, FORM>(d, t, nt, total, grid, ob, obs, s);
+        if (k == 4) return launch_pipe<T, SHIFT, 8, 192, V, FORM>(d, t, nt, total, grid, ob, obs, s);
+        if (k == 5) return launch_pipe<T, SHIFT, 6, 288, V, FORM>(d, t, nt, total, grid, ob, obs, s);
+        if (k == 6) return launch_pipe<T, SHIFT, 6, 320, V, FORM>(d, t, nt, total, grid, ob, obs, s);
       }
-      if (k == 3) return launch_pipe<T, SHIFT, 8, 256, V, FORM>(d, t, nt, total, grid, s);
+      if (k == 3) return launch_pipe<T, SHIFT, 8, 256, V, FORM>(d, t, nt, total, grid, ob, obs, s);
     }
-    if (k == 0) return launch_cfg<T, SHIFT, 32, 8, V, FORM>(d, t, nt, total, grid, s);
+    if (k == 0) return launch_cfg<T, SHIFT, 32, 8, V, FORM>(d, t, nt, total, grid, ob, obs, s);
     return cudaErrorInvalidValue;
   }
 };
@@ -684,12 +912,12 @@ cudaError_t LaunchFused<T, SHIFT>::prepare(int variant, int cfg_index, FusedCfg*
 template <typename T, bool SHIFT>
 cudaError_t LaunchFused<T, SHIFT>::step(int variant, int cfg_index, const InstDesc<T>* d_desc,
                                         const FusedTile* tiles, int ntiles, long long total, int grid,
-                                        cudaStream_t s) {
+                                        const FusedObs& ob, bool obs, cudaStream_t s) {
   switch (variant) {
-    case 0: return FusedVariant<T, SHIFT, VelD3Q19, 0>::step(cfg_index, d_desc, tiles, ntiles, total, grid, s);
-    case 1: return FusedVariant<T, SHIFT, VelD3Q15, 0>::step(cfg_index, d_desc, tiles, ntiles, total, grid, s);
-    case 2: return FusedVariant<T, SHIFT, VelD3Q19, 1>::step(cfg_index, d_desc, tiles, ntiles, total, grid, s);
-    case 3: return FusedVariant<T, SHIFT, VelD3Q15, 1>::step(cfg_index, d_desc, tiles, ntiles, total, grid, s);
+    case 0: return FusedVariant<T, SHIFT, VelD3Q19, 0>::step(cfg_index, d_desc, tiles, ntiles, total, grid, ob, obs, s);
+    case 1: return FusedVariant<T, SHIFT, VelD3Q15, 0>::step(cfg_index, d_desc, tiles, ntiles, total, grid, ob, obs, s);
+    case 2: return FusedVariant<T, SHIFT, VelD3Q19, 1>::step(cfg_index, d_desc, tiles, ntiles, total, grid, ob, obs, s);
+    case 3: return FusedVariant<T, SHIFT, VelD3Q15, 1>::step(cfg_index, d_desc, tiles, ntiles, total, grid, ob, obs, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -76,6 +76,7 @@ struct InstDesc {
   T* H;            // scratch: molecular field [5][N]
   T* rq;           // staged path, Heun: right-hand side R(Q, psi) at t [6][N] (Q 5, psi 1)
   T* qp;           // staged path, Heun: predicted Q, psi [6][N]
+  const T* trig;   // (cos, sin) of 2 pi x/nx, 2 pi y/ny, 2 pi z/nz: [nx + ny + nz][2] (centroid sums)
   Coef<T> c;
 };
 
@@ -111,6 +112,23 @@ struct FusedCfg {
   size_t smem = 0;
 };
 
+// The FP64 conserved and centroid sums of the fused step (a6).  Each column segment a block
+// works on has a slot of 12 partial sums (block b, segment j of the block: slot b * maxseg + j);
+// slot_inst[slot] is its instance (-1: unused).  The block that fills the last slot of an
+// instance (cnt counts them; the kernel resets it) sums the instance's slots, in slot order,
+// into latest[inst][12]: mass, sum psi, momentum (3), sum phi_c cos (3), sum phi_c sin (3),
+// sum phi_c.
+struct FusedObs {
+  double* slots;
+  const int* slot_inst;
+  const int* nslot;    // [ninst] slots of each instance
+  const int* slot_lo;  // [ninst] first slot of each instance
+  const int* slot_hi;  // [ninst] one past its last slot
+  unsigned* cnt;       // [ninst]
+  double* latest;      // [ninst][12]
+  int maxseg;
+};
+
 // The fused one-kernel step (lbcad_fused.cuh), in several tile shapes, for each variant
 // of the LB part: variant = (D3Q15 ? 1 : 0) + 2 * (Eq. 9-11 form ? 1 : 0).  prepare returns
 // cudaErrorNotSupported for a tile shape the variant does not come in.
@@ -118,8 +136,9 @@ template <typename T, bool SHIFT>
 struct LaunchFused {
   static int num_configs();
   static cudaError_t prepare(int variant, int cfg_index, FusedCfg* cfg);
+  // obs: the kernel that also forms the a6 sums of the new state (FusedObs)
   static cudaError_t step(int variant, int cfg_index, const InstDesc<T>* d_desc, const FusedTile* tiles,
-                          int ntiles, long long total, int grid, cudaStream_t s);
+                          int ntiles, long long total, int grid, const FusedObs& ob, bool obs, cudaStream_t s);
 };
 
 // Buffers of one reverse step of the adjoint (lbcad_adjoint.cuh).
@@ -150,5 +169,6 @@ void set_thread_error(const char* msg);
 constexpr int kStepBlock = 256;
 constexpr int kObsBlock = 256;
 constexpr int kObsMaxBlocks = 1024;
+constexpr int kObsRowsPerBlock = 32;  // x rows per block of the separate a6 pass (4 per warp)
 
 }  // namespace lbcad

@@ -539,8 +539,10 @@ __device__ __forceinline__ void op_update(const Coef<T>& c, T lapmu, const T Wg[
 // a5 at one site: moments of the pulled populations g and the force F, then BGK + Guo
 // collision (Eqs. 6-8); g is overwritten with the post-collision values, u = velocity.
 // The equilibrium and forcing terms of opposite velocities c and -c share their even part.
+// mom (optional): the site's share of the conserved sums of the new state, mom[0] = mass
+// (minus rho0 when SHIFT) and mom[1..3] = post-collision momentum j + F.
 template <typename T, bool SHIFT, class V = VelD3Q19>
-__device__ __forceinline__ void lb_collide(const Coef<T>& c, const T F[3], T g[V::Q], T u[3]) {
+__device__ __forceinline__ void lb_collide(const Coef<T>& c, const T F[3], T g[V::Q], T u[3], T* mom = nullptr) {
   // moments from opposite pairs
   T m0 = g[0];
   T j[3] = {T(0), T(0), T(0)};
@@ -556,6 +558,11 @@ __device__ __forceinline__ void lb_collide(const Coef<T>& c, const T F[3], T g[V
   const T rinv = T(1) / rho;
 #pragma unroll
   for (int a = 0; a < 3; ++a) u[a] = (j[a] + T(0.5) * F[a]) * rinv;
+  if (mom) {
+    mom[0] = m0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) mom[1 + a] = j[a] + F[a];
+  }
   const T u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const T uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
   // equilibrium w rho (1 + 3 cu + 4.5 cu^2 - 1.5 u^2) (shifted: minus w rho0) and Guo
@@ -593,7 +600,7 @@ __device__ __forceinline__ void lb_collide(const Coef<T>& c, const T F[3], T g[V
 // stress at the site (9, row-major).  Opposite velocities share the even part of f_eq.
 template <typename T, bool SHIFT, class V>
 __device__ __forceinline__ void lb_collide_stress(const Coef<T>& c, const T FA[3], const T sig[9], T g[V::Q],
-                                                  T u[3]) {
+                                                  T u[3], T* mom = nullptr) {
   T m0 = g[0];
   T j[3] = {T(0), T(0), T(0)};
 #pragma unroll
@@ -608,6 +615,11 @@ __device__ __forceinline__ void lb_collide_stress(const Coef<T>& c, const T FA[3
   const T rinv = T(1) / rho;
 #pragma unroll
   for (int a = 0; a < 3; ++a) u[a] = j[a] * rinv;
+  if (mom) {  // as in lb_collide: the forcing adds FA to the momentum (Eq. 10)
+    mom[0] = m0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) mom[1 + a] = j[a] + FA[a];
+  }
   // Pi = rho u u - sigma^S (symmetric: xx, yy, zz, xy, xz, yz)
   const T Pxx = rho * u[0] * u[0] - sig[0], Pyy = rho * u[1] * u[1] - sig[4], Pzz = rho * u[2] * u[2] - sig[8];
   const T Pxy = rho * u[0] * u[1] - T(0.5) * (sig[1] + sig[3]);
@@ -1077,48 +1089,59 @@ __global__ void k_set_fields(InstDesc<T> I, long long oG, long long oU, long lon
 }
 
 // ---------------------------------------------------------------- FP64 reductions
-// 12 sums per instance (see lbcad_obs).  Fixed-order block reduction with warp shuffles
-// into partial[block][12]; k_obs_final sums the partials in block order.
+// a6 as a separate pass (state set from outside, or a path without the fused sums): FP64
+// mass, sum psi, momentum (3), sum phi_c cos (3), sum phi_c sin (3) and sum phi_c of the
+// populations stored at each site (streaming only permutes them, so the sums equal those of
+// the pulled populations).  Each warp takes whole x rows (no index division per site); a lane
+// adds its sites of a row in T, then into FP64; cos and sin come from the instance's tables.
+// k_obs_partial writes partial[block][12]; k_obs_final sums them in a fixed order.
 template <typename T, bool SHIFT, class V>
 __global__ void __launch_bounds__(kObsBlock) k_obs_partial(InstDesc<T> I, double* __restrict__ partial) {
   double acc[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = 0.0;
+  const int nx = I.nx, ny = I.ny;
   const long long N = I.N;
-  const double two_pi = 6.283185307179586476925286766559;
-  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N; s += (long long)gridDim.x * blockDim.x) {
-    const int nx = I.nx, ny = I.ny, nz = I.nz;
-    const int x = (int)(s % nx);
-    const long long t = s / nx;
-    const int y = (int)(t % ny);
-    const int z = (int)(t / ny);
-    const Nbr nb = make_nbr(x, y, z, nx, ny, nz);
-#pragma unroll
-    for (int i = 0; i < V::Q; ++i) {
-      const long long src = nb.off(-V::c(i, 0), -V::c(i, 1), -V::c(i, 2));
-      double fi = (double)I.g_in[i * N + src];
-      if (SHIFT) fi += V::w(i) * (double)I.c.rho0;
-      acc[0] += fi;
-      if (V::c(i, 0)) acc[2] += V::c(i, 0) * fi;
-      if (V::c(i, 1)) acc[3] += V::c(i, 1) * fi;
-      if (V::c(i, 2)) acc[4] += V::c(i, 2) * fi;
-    }
-    const double p = (double)I.psi_in[s];
-    acc[1] += p;
-    const double pc = 0.5 * (1.0 + p);
-    const int r[3] = {x, y, z};
-    const int L[3] = {nx, ny, nz};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      double sn, cs;
-      sincos(two_pi * (double)r[a] / (double)L[a], &sn, &cs);
-      acc[5 + a] += pc * cs;
-      acc[8 + a] += pc * sn;
-    }
-    acc[11] += pc;
-  }
-  __shared__ double sh[kObsBlock / 32][12];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int WPB = kObsBlock / 32;
+  const int rows = ny * I.nz;
+  for (int r = blockIdx.x * WPB + wid; r < rows; r += gridDim.x * WPB) {
+    const int y = r % ny, z = r / ny;
+    const long long base = (long long)r * nx;
+    T m = T(0), j0 = T(0), j1 = T(0), j2 = T(0), ps = T(0), pc = T(0), pcc = T(0), pcs = T(0);
+    for (int x = lane; x < nx; x += 32) {
+      const long long st = base + x;
+#pragma unroll
+      for (int i = 0; i < V::Q; ++i) {
+        const T f = __ldg(I.g_in + i * N + st);
+        m += f;
+        if (V::c(i, 0)) j0 += V::c(i, 0) > 0 ? f : -f;
+        if (V::c(i, 1)) j1 += V::c(i, 1) > 0 ? f : -f;
+        if (V::c(i, 2)) j2 += V::c(i, 2) > 0 ? f : -f;
+      }
+      const T p = __ldg(I.psi_in + st);
+      ps += p;
+      const T h = T(0.5) * (T(1) + p);
+      pc += h;
+      pcc += h * __ldg(I.trig + 2 * x);
+      pcs += h * __ldg(I.trig + 2 * x + 1);
+    }
+    acc[0] += (double)m;
+    acc[1] += (double)ps;
+    acc[2] += (double)j0;
+    acc[3] += (double)j1;
+    acc[4] += (double)j2;
+    acc[5] += (double)pcc;
+    acc[8] += (double)pcs;
+    const double dpc = (double)pc;
+    acc[6] += dpc * (double)__ldg(I.trig + 2 * (nx + y));
+    acc[9] += dpc * (double)__ldg(I.trig + 2 * (nx + y) + 1);
+    acc[7] += dpc * (double)__ldg(I.trig + 2 * (nx + ny + z));
+    acc[10] += dpc * (double)__ldg(I.trig + 2 * (nx + ny + z) + 1);
+    acc[11] += dpc;
+  }
+  if (SHIFT && blockIdx.x == 0 && threadIdx.x == 0) acc[0] += (double)N * (double)I.c.rho0;
+  __shared__ double sh[WPB][12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     double v = acc[k];
@@ -1129,16 +1152,25 @@ __global__ void __launch_bounds__(kObsBlock) k_obs_partial(InstDesc<T> I, double
   __syncthreads();
   if (threadIdx.x < 12) {
     double v = 0.0;
-    for (int w = 0; w < kObsBlock / 32; ++w) v += sh[w][threadIdx.x];
+    for (int w = 0; w < WPB; ++w) v += sh[w][threadIdx.x];
     partial[blockIdx.x * 12 + threadIdx.x] = v;
   }
 }
 
-static __global__ void k_obs_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
+// Sums partial[nblocks][12] into out[12]: thread (l, k) adds blocks l, l + 32, ... of value k,
+// then the 32 subtotals of each value are added in order.
+static __global__ void __launch_bounds__(384) k_obs_final(const double* __restrict__ partial, int nblocks,
+                                                          double* __restrict__ out) {
+  __shared__ double red[32][12];
+  const int k = threadIdx.x % 12, l = threadIdx.x / 12;
+  double v = 0.0;
+  for (int b = l; b < nblocks; b += 32) v += partial[b * 12 + k];
+  red[l][k] = v;
+  __syncthreads();
   if (threadIdx.x < 12) {
-    double v = 0.0;
-    for (int b = 0; b < nblocks; ++b) v += partial[b * 12 + threadIdx.x];
-    out[threadIdx.x] = v;
+    double t = 0.0;
+    for (int q = 0; q < 32; ++q) t += red[q][threadIdx.x];
+    out[threadIdx.x] = t;
   }
 }
 
@@ -1227,7 +1259,7 @@ cudaError_t Launch<T, SHIFT>::observables(const InstDesc<T>& I, double* partial,
   else k_obs_partial<T, SHIFT, VelD3Q19><<<nblocks, kObsBlock, 0, s>>>(I, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_obs_final<<<1, 32, 0, s>>>(partial, nblocks, out);
+  k_obs_final<<<1, 384, 0, s>>>(partial, nblocks, out);
   return cudaGetLastError();
 }
 

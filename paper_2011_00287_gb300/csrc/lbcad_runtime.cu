@@ -33,6 +33,7 @@ struct Inst {
   void* H = nullptr;
   void* rq = nullptr;  // Heun: right-hand side at t (6 per site)
   void* qp = nullptr;  // Heun: predicted Q, psi (6 per site)
+  void* trig = nullptr;  // (cos, sin) of 2 pi x/nx, 2 pi y/ny, 2 pi z/nz for the centroid sums
   long long blk0 = 0, nblk = 0;
 };
 
@@ -85,6 +86,17 @@ struct lbcad_ctx {
   int fused_grid = 0;
   int cfg_index = 0;
   FusedCfg cfg;
+  // a6 sums of the fused step (see FusedObs): slots per (block, segment), per-instance
+  // bookkeeping, and the sums of the latest state; obs_valid while they describe the state
+  double* obs_slots = nullptr;
+  size_t obs_slots_cap = 0;
+  int* obs_map = nullptr;  // slot_inst [nslots], then nslot, slot_lo, slot_hi [ninst each]
+  size_t obs_map_cap = 0;
+  unsigned* obs_cnt = nullptr;
+  double* obs_latest = nullptr;
+  int obs_maxseg = 0;
+  bool observe = true;     // fused steps form the a6 sums (lbcad_set_observe)
+  bool obs_valid = false;
   void* adj_lam = nullptr;  // cotangent of the initial state of the last lbcad_adjoint
   std::string err;
   size_t elem() const { return prec == LBCAD_FP64 ? sizeof(double) : sizeof(float); }
@@ -190,6 +202,7 @@ InstDesc<T> make_desc(const Inst& I, int parity) {
   d.u_in = (const T*)I.ub[a]; d.u_out = (T*)I.ub[b];
   d.sig = (T*)I.sig; d.mu = (T*)I.mu; d.H = (T*)I.H;
   d.rq = (T*)I.rq; d.qp = (T*)I.qp;
+  d.trig = (const T*)I.trig;
   d.c = coefs<T>(I.p);
   return d;
 }
@@ -330,7 +343,32 @@ int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint
       I.ub[par] = dev_alloc(c, 3 * I.N * es);
       if (!I.gb[par] || !I.qb[par] || !I.pb[par] || !I.ub[par]) return bail(LBCAD_E_OOM, "device allocation failed");
     }
+    const int L = I.g.nx + I.g.ny + I.g.nz;
+    I.trig = dev_alloc(c, 2 * (size_t)L * es);
+    if (!I.trig) return bail(LBCAD_E_OOM, "device allocation failed");
+    std::vector<double> tr(2 * (size_t)L);
+    const int len[3] = {I.g.nx, I.g.ny, I.g.nz};
+    for (int a = 0, k = 0; a < 3; ++a)
+      for (int x = 0; x < len[a]; ++x, ++k) {
+        const double ph = 2.0 * M_PI * (double)x / (double)len[a];
+        tr[2 * k] = std::cos(ph);
+        tr[2 * k + 1] = std::sin(ph);
+      }
+    cudaError_t te;
+    std::vector<float> tf(tr.begin(), tr.end());
+    if (c->prec == LBCAD_FP64)
+      te = cudaMemcpyAsync(I.trig, tr.data(), tr.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    else
+      te = cudaMemcpyAsync(I.trig, tf.data(), tf.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    if (te == cudaSuccess) te = cudaStreamSynchronize(c->stream);
+    if (te != cudaSuccess) return bail(LBCAD_E_CUDA, std::string("trig table upload: ") + cudaGetErrorString(te));
   }
+  c->obs_cnt = (unsigned*)dev_alloc(c, n * sizeof(unsigned));
+  c->obs_latest = (double*)dev_alloc(c, (size_t)n * 12 * sizeof(double));
+  if (!c->obs_cnt || !c->obs_latest) return bail(LBCAD_E_OOM, "device allocation failed");
+  if (cudaMemsetAsync(c->obs_cnt, 0, n * sizeof(unsigned), c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return bail(LBCAD_E_CUDA, "a6 counter initialisation failed");
   c->total_blocks = blk;
   if (blk >= (1LL << 31)) return bail(LBCAD_E_INVALID_ARG, "too many blocks for one launch");
   const size_t dsz = (c->prec == LBCAD_FP64 ? sizeof(InstDesc<double>) : sizeof(InstDesc<float>)) * n;
@@ -425,6 +463,54 @@ int prepare_fused(lbcad_ctx* c, int cfg_index) {
   CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
   long long grid = (long long)sms * cfg.blocks_per_sm;
   if (grid > start) grid = start;
+  // the column segments of each block, split exactly as the kernels split them: slot
+  // (block, segment) -> instance, and each instance's slot count and range
+  const int ninst = (int)c->inst.size();
+  std::vector<std::vector<int>> seg_inst(grid);
+  int maxseg = 1;
+  for (long long b = 0; b < grid; ++b) {
+    const long long begin = (start * b) / grid, end = (start * (b + 1)) / grid;
+    for (long long it = begin; it < end;) {
+      int lo = 0, hi = (int)t.size() - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t[mid].start <= it) lo = mid; else hi = mid - 1;
+      }
+      const long long seg_end = std::min(end, t[lo].start + t[lo].nz);
+      seg_inst[b].push_back(t[lo].inst);
+      it = seg_end;
+    }
+    maxseg = std::max(maxseg, (int)seg_inst[b].size());
+  }
+  const size_t nslots = (size_t)grid * maxseg;
+  std::vector<int> map(nslots + 3 * (size_t)ninst, -1);
+  int* nslot = map.data() + nslots;
+  int* slot_lo = nslot + ninst;
+  int* slot_hi = slot_lo + ninst;
+  for (int i = 0; i < ninst; ++i) nslot[i] = 0;
+  for (long long b = 0; b < grid; ++b)
+    for (size_t j = 0; j < seg_inst[b].size(); ++j) {
+      const int sl = (int)(b * maxseg + j), i = seg_inst[b][j];
+      map[sl] = i;
+      if (nslot[i]++ == 0) slot_lo[i] = sl;
+      slot_hi[i] = sl + 1;
+    }
+  for (int i = 0; i < ninst; ++i)
+    if (nslot[i] == 0) return fail(c, LBCAD_E_INVALID_ARG, "an instance has no fused work");
+  if (nslots * 12 > c->obs_slots_cap) {
+    c->obs_slots = (double*)dev_alloc(c, nslots * 12 * sizeof(double));
+    if (!c->obs_slots) return fail(c, LBCAD_E_OOM, "a6 slot allocation failed");
+    c->obs_slots_cap = nslots * 12;
+  }
+  if (map.size() > c->obs_map_cap) {
+    c->obs_map = (int*)dev_alloc(c, map.size() * sizeof(int));
+    if (!c->obs_map) return fail(c, LBCAD_E_OOM, "a6 slot map allocation failed");
+    c->obs_map_cap = map.size();
+  }
+  CK(c, cudaMemcpyAsync(c->obs_map, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->obs_maxseg = maxseg;
+  c->obs_valid = false;
   c->ntiles = (int)t.size();
   c->fused_total = start;
   c->fused_grid = (int)grid;
@@ -435,11 +521,22 @@ int prepare_fused(lbcad_ctx* c, int cfg_index) {
 
 cudaError_t launch_fused(lbcad_ctx* c, int par) {
   const int v = c->fused_variant();
+  const int ninst = (int)c->inst.size();
+  const size_t nslots = (size_t)c->fused_grid * c->obs_maxseg;
+  FusedObs ob;
+  ob.slots = c->obs_slots;
+  ob.slot_inst = c->obs_map;
+  ob.nslot = c->obs_map + nslots;
+  ob.slot_lo = ob.nslot + ninst;
+  ob.slot_hi = ob.slot_lo + ninst;
+  ob.cnt = c->obs_cnt;
+  ob.latest = c->obs_latest;
+  ob.maxseg = c->obs_maxseg;
   if (c->prec == LBCAD_FP64)
     return LaunchFused<double, false>::step(v, c->cfg_index, (const InstDesc<double>*)c->desc[par], c->tiles,
-                                            c->ntiles, c->fused_total, c->fused_grid, c->stream);
+                                            c->ntiles, c->fused_total, c->fused_grid, ob, c->observe, c->stream);
   return LaunchFused<float, true>::step(v, c->cfg_index, (const InstDesc<float>*)c->desc[par], c->tiles, c->ntiles,
-                                        c->fused_total, c->fused_grid, c->stream);
+                                        c->fused_total, c->fused_grid, ob, c->observe, c->stream);
 }
 
 void drop_graph(lbcad_ctx* c) {
@@ -543,6 +640,7 @@ int lbcad_set_path(lbcad_ctx* c, int32_t path) {
     if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
     if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
     c->path = path;
+    c->obs_valid = false;
   }
   return LBCAD_OK;
 }
@@ -609,6 +707,16 @@ int lbcad_set_tiles(lbcad_ctx* c, int32_t cfg) {
   return LBCAD_OK;
 }
 
+int lbcad_set_observe(lbcad_ctx* c, int32_t on) {
+  if (!c || (on != 0 && on != 1)) return LBCAD_E_INVALID_ARG;
+  if (c->observe != (on == 1)) {
+    c->observe = on == 1;
+    drop_graph(c);
+    c->obs_valid = false;
+  }
+  return LBCAD_OK;
+}
+
 int lbcad_set_graph(lbcad_ctx* c, int32_t steps_per_graph) {
   if (!c || steps_per_graph < 0) return LBCAD_E_INVALID_ARG;
   DeviceGuard dg(c->device);
@@ -646,7 +754,10 @@ int lbcad_step(lbcad_ctx* c, int64_t n) {
       left -= c->graph_steps;
     }
   }
-  return launch_steps(c, left);
+  int r = launch_steps(c, left);
+  // after a fused step the a6 sums of the new state are in obs_latest
+  if (r == LBCAD_OK && n > 0) c->obs_valid = c->path == LBCAD_PATH_FUSED && c->observe;
+  return r;
 }
 
 int lbcad_get_fields(lbcad_ctx* c, int32_t inst, uint32_t mask, void* dst, size_t bytes, int32_t dst_is_device) {
@@ -699,6 +810,7 @@ int lbcad_set_fields(lbcad_ctx* c, int32_t inst, uint32_t mask, const void* src,
     e = Launch<float, true>::set_fields(desc_now<float>(c, inst), mask, from, (float*)I.gb[par], (float*)I.qb[par],
                                         (float*)I.pb[par], (float*)I.ub[par], c->stream);
   if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("set_fields: ") + cudaGetErrorString(e));
+  c->obs_valid = false;
   CK(c, cudaStreamSynchronize(c->stream));
   return LBCAD_OK;
 }
@@ -732,6 +844,7 @@ int copy_state(lbcad_ctx* c, int inst, void* ext, size_t bytes, bool ext_is_devi
     else CK(c, cudaMemcpyAsync(parts[k], e, sizes[k], kind, c->stream));
     off += sizes[k];
   }
+  if (!to_ext) c->obs_valid = false;
   CK(c, cudaStreamSynchronize(c->stream));
   return LBCAD_OK;
 }
@@ -751,17 +864,21 @@ int lbcad_observables(lbcad_ctx* c, int32_t inst, lbcad_obs* out) {
   if (!c || !out) return LBCAD_E_INVALID_ARG;
   if (inst < 0 || inst >= (int)c->inst.size()) return fail(c, LBCAD_E_INVALID_ARG, "instance out of range");
   DeviceGuard dg(c->device);
-  const long long N = c->inst[inst].N;
-  long long nb = (N + kObsBlock - 1) / kObsBlock;
-  if (nb > kObsMaxBlocks) nb = kObsMaxBlocks;
-  cudaError_t e = (c->prec == LBCAD_FP64)
-                      ? Launch<double, false>::observables(desc_now<double>(c, inst), c->obs_partial, (int)nb,
-                                                           c->obs_out, c->stream)
-                      : Launch<float, true>::observables(desc_now<float>(c, inst), c->obs_partial, (int)nb,
-                                                         c->obs_out, c->stream);
-  if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("observables: ") + cudaGetErrorString(e));
+  const double* src = c->obs_latest + 12 * (size_t)inst;  // summed by the fused step
+  if (!c->obs_valid) {  // another path, or the state was set: a separate reduction pass
+    const Inst& I = c->inst[inst];
+    long long nb = ((long long)I.g.ny * I.g.nz + kObsRowsPerBlock - 1) / kObsRowsPerBlock;
+    if (nb > kObsMaxBlocks) nb = kObsMaxBlocks;
+    cudaError_t e = (c->prec == LBCAD_FP64)
+                        ? Launch<double, false>::observables(desc_now<double>(c, inst), c->obs_partial, (int)nb,
+                                                             c->obs_out, c->stream)
+                        : Launch<float, true>::observables(desc_now<float>(c, inst), c->obs_partial, (int)nb,
+                                                           c->obs_out, c->stream);
+    if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("observables: ") + cudaGetErrorString(e));
+    src = c->obs_out;
+  }
   double h[12];
-  CK(c, cudaMemcpyAsync(h, c->obs_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(h, src, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   out->mass = h[0];
   out->sum_psi = h[1];
@@ -938,8 +1055,10 @@ int lbcad_adjoint(lbcad_ctx* c, int64_t nsteps, int32_t ckpt_every, double* dJ_d
   if (nsteps < 1 || ckpt_every < 1) return fail(c, LBCAD_E_INVALID_ARG, "need nsteps >= 1 and ckpt_every >= 1");
   DeviceGuard dg(c->device);
   const int k = (int)std::min<int64_t>(ckpt_every, nsteps);
-  return c->prec == LBCAD_FP64 ? adjoint_impl<double, false>(c, nsteps, k, dJ_dzeta, dJ_dq0, dJ_dQ0, J)
-                               : adjoint_impl<float, true>(c, nsteps, k, dJ_dzeta, dJ_dq0, dJ_dQ0, J);
+  const int r = c->prec == LBCAD_FP64 ? adjoint_impl<double, false>(c, nsteps, k, dJ_dzeta, dJ_dq0, dJ_dQ0, J)
+                                      : adjoint_impl<float, true>(c, nsteps, k, dJ_dzeta, dJ_dq0, dJ_dQ0, J);
+  c->obs_valid = false;  // the replays reuse the fused step
+  return r;
 }
 
 int lbcad_adjoint_fields(lbcad_ctx* c, uint32_t mask, void* dst, size_t bytes) {

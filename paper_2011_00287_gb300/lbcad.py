@@ -85,6 +85,7 @@ _SIGS = {
                                           _P(ctypes.c_void_p)]),
     "lbcad_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "lbcad_set_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "lbcad_set_observe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "lbcad_set_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "lbcad_set_tiles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "lbcad_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _P(ctypes.c_int32), _P(ctypes.c_float),
@@ -294,6 +295,11 @@ class Simulation:
 
     def set_tiles(self, cfg: int):
         _check(library().lbcad_set_tiles(self.ctx, int(cfg)), self.ctx)
+
+    def set_observe(self, on: bool):
+        """Whether fused steps also form the FP64 mass, psi, momentum and centroid sums of
+        the state they write (default on); off, observables() runs a separate pass."""
+        _check(library().lbcad_set_observe(self.ctx, 1 if on else 0), self.ctx)
 
     def set_graph(self, steps_per_graph: int):
         _check(library().lbcad_set_graph(self.ctx, int(steps_per_graph)), self.ctx)
