@@ -178,23 +178,23 @@ struct AntiPairAcc {
 // The output work of one site (a3 - a5) from the shared-memory tiles: the force, the
 // stencils of a4, the pull of the populations of velocity set V, the order-parameter update
 // and the collision; stores g, Q, psi and u.  FORM 0: F = div sigma, BGK + Guo (Eqs. 6-8).
-// FORM 1: FA = div sigma^A and the equilibrium carrying sigma^S (Eqs. 9-11).  zo, pyo, pxo:
-// offs(zo, pyo, pxo, xyz) fills the global offsets of the planes z-1, z, z+1, the rows y-1, y,
-// y+1 and the columns x-1, x, x+1 and the site's coordinates, and hs(H) the molecular field of
-// the site; both are called late (after the stencils, after the pulls), so that their values
-// do not hold registers through the earlier work.  ob (OBS): the site's share of the a6 sums
-// of the new state (see FusedObs).
-template <typename T, bool SHIFT, class V, int FORM, bool OBS, class A, class Offs, class HS>
+// FORM 1: FA = div sigma^A and the equilibrium carrying sigma^S (Eqs. 9-11).
+// offs(zo, pyo, pxo) fills the global offsets of the planes z-1, z, z+1, the rows y-1, y, y+1
+// and the columns x-1, x, x+1, and hs(H) the molecular field of the site; both are called
+// late (after the stencils, after the pulls), so that their values do not hold registers
+// through the earlier work.  ob (OBS): the site's share of the a6 sums of the new state (see
+// FusedObs); trg(tx, ty, tz) gives (cos, sin) of 2 pi x/nx, 2 pi y/ny and 2 pi z/nz of the site.
+template <typename T, bool SHIFT, class V, int FORM, bool OBS, class A, class Offs, class HS, class TR>
 __device__ __forceinline__ void output_site(const InstDesc<T>& I, const Coef<T>& cf, const A& acc, const Offs& offs,
-                                            const HS& hs, T ob[12]) {
+                                            const HS& hs, const TR& trg, T ob[12]) {
   const long long N = I.N;
   T F[3], lapmu, Wg[3][3], q0[5], qf[6][5], p0, pf[6], u0[3], uf[6];
   if constexpr (FORM == 0) gather_force<T>(acc, F);
   else gather_force<T>(AntiPairAcc<T, A>{acc}, F);
   gather_op<T>(acc, lapmu, Wg, q0, qf, p0, pf, u0, uf);
   long long zo[3];
-  int pyo[3], pxo[3], xyz[3];
-  offs(zo, pyo, pxo, xyz);
+  int pyo[3], pxo[3];
+  offs(zo, pyo, pxo);
   T g[V::Q];
 #pragma unroll
   for (int i = 0; i < V::Q; ++i)
@@ -227,9 +227,8 @@ __device__ __forceinline__ void output_site(const InstDesc<T>& I, const Coef<T>&
     ob[3] = mom[2];
     ob[4] = mom[3];
     ob[11] = pc;
-    const Vec2<T> tx = ldg2(I.trig + 2 * xyz[0]);
-    const Vec2<T> ty = ldg2(I.trig + 2 * (I.nx + xyz[1]));
-    const Vec2<T> tz = ldg2(I.trig + 2 * (I.nx + I.ny + xyz[2]));
+    Vec2<T> tx, ty, tz;
+    trg(tx, ty, tz);
     ob[5] = pc * tx.x;
     ob[6] = pc * ty.x;
     ob[7] = pc * tz.x;
@@ -526,7 +525,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
           acc.upl[j] = sU + uslot(z - 1 + j) * G::USLOT;
         }
         // offsets of this thread's output site and its neighbours (pull)
-        auto offs = [&](long long zo[3], int pyo[3], int pxo[3], int xyz[3]) {
+        auto offs = [&](long long zo[3], int pyo[3], int pxo[3]) {
           zo[0] = (long long)wrap_plane(z - 1, nz) * plane;
           zo[1] = (long long)z * plane;
           zo[2] = (long long)wrap_plane(z + 1, nz) * plane;
@@ -535,15 +534,17 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
             pyo[j] = ymap[ty + 1 + j];
             pxo[j] = xmap[tx + 1 + j];
           }
-          xyz[0] = tl.x0 + tx;
-          xyz[1] = tl.y0 + ty;
-          xyz[2] = z;
         };
         auto hs = [&](T H[5]) {
 #pragma unroll
           for (int c = 0; c < 5; ++c) H[c] = Hc[c];
         };
-        output_site<T, SHIFT, V, FORM, OBS>(I, cf, acc, offs, hs, ob6);
+        auto trg = [&](Vec2<T>& ctx, Vec2<T>& cty, Vec2<T>& ctz) {
+          ctx = ldg2(I.trig + 2 * (tl.x0 + tx));
+          cty = ldg2(I.trig + 2 * (nx + tl.y0 + ty));
+          ctz = ldg2(I.trig + 2 * (nx + ny + z));
+        };
+        output_site<T, SHIFT, V, FORM, OBS>(I, cf, acc, offs, hs, trg, ob6);
       }
       if constexpr (OBS)
         if (z >= zb) obs_warp_add<T>(ob6, oacc + (tid >> 5) * 24);
@@ -582,7 +583,8 @@ struct PipeGeom {
   static_assert(NS % 32 == 0, "whole warps per group");
   static constexpr int NR = NS / 12 * 12;  // sigma threads that add up the a6 shares
   // a6: the output planes' shares [2][IP][12] (double-buffered by plane parity), the sigma
-  // threads' accumulators [NR][2] in T, then the segment's 12 FP64 values
+  // threads' accumulators [NR][2] in T, the tile's (cos, sin) of x and y [TX + TY][2], then
+  // the segment's 12 FP64 values
   template <typename T>
   __host__ __device__ static constexpr size_t obs_off() {
     return (((size_t)NQS * 6 * QP + (size_t)NSS * 10 * SP + (size_t)NHS * 5 * IP + (size_t)NUS * 3 * SP) * sizeof(T) +
@@ -593,8 +595,12 @@ struct PipeGeom {
     return obs_off<T>() + (size_t)2 * IP * 12 * sizeof(T);
   }
   template <typename T>
+  __host__ __device__ static constexpr size_t trig_off() {
+    return acc_off<T>() + (size_t)NR * 2 * sizeof(T);
+  }
+  template <typename T>
   __host__ __device__ static constexpr size_t seg_off() {
-    return (acc_off<T>() + (size_t)NR * 2 * sizeof(T) + 7) / 8 * 8;
+    return (trig_off<T>() + (size_t)(TX + TY) * 2 * sizeof(T) + 7) / 8 * 8;
   }
   template <typename T>
   __host__ __device__ static constexpr size_t bytes(bool obs) {
@@ -637,6 +643,8 @@ __global__ void __launch_bounds__(512, 1)
   int* ymap = xmap + QW;
   T* oshare = reinterpret_cast<T*>(smem_raw + G::template obs_off<T>());  // a6 shares [2][IP][12]
   T* oacc = reinterpret_cast<T*>(smem_raw + G::template acc_off<T>());    // sigma-thread sums [NR][2]
+  T* xt = reinterpret_cast<T*>(smem_raw + G::template trig_off<T>());     // (cos, sin) of the tile's x
+  T* yt = xt + 2 * TX;                                                     // ... and y
   double* oseg = reinterpret_cast<double*>(smem_raw + G::template seg_off<T>());
   const int tid = threadIdx.x;
   auto q6 = [](int p) { return (p + 12) % 6; };
@@ -670,8 +678,13 @@ __global__ void __launch_bounds__(512, 1)
     __syncthreads();
     for (int k = tid; k < QW; k += G::NT) xmap[k] = wrapmod(tl.x0 + k - 2, nx);
     for (int k = tid; k < G::QH; k += G::NT) ymap[k] = wrapmod(tl.y0 + k - 2, ny) * nx;
-    if constexpr (OBS)
+    if constexpr (OBS) {
       for (int k = tid; k < G::NR * 2; k += G::NT) oacc[k] = T(0);
+      for (int k = tid; k < 2 * (TX + G::TY); k += G::NT) {  // column k/2 < TX, else row k/2 - TX
+        const int e = k >> 1, c = k & 1;
+        xt[k] = e < TX ? I.trig[2 * ((tl.x0 + e) % nx) + c] : I.trig[2 * (nx + (tl.y0 + e - TX) % ny) + c];
+      }
+    }
     __syncthreads();
     // this thread's load sites (at most one Q/psi site and one u site per plane)
     int qoff = 0, uoff = 0;
@@ -737,6 +750,10 @@ __global__ void __launch_bounds__(512, 1)
         const int z = k - 1;
         const long long zo3[3] = {(long long)wrap_plane(z - 1, nz) * plane, (long long)z * plane,
                                   (long long)wrap_plane(z + 1, nz) * plane};
+        // cos, sin of the plane for the a6 centroid sums, read early: its latency hides
+        // behind the stencils
+        Vec2<T> tz = v2(T(0), T(0));
+        if constexpr (OBS) tz = ldg2(I.trig + 2 * (nx + ny + z));
         const int site = tid - G::NS;
         const int tx = site % TX, ty = site / TX;
         T ob6[12] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
@@ -757,18 +774,20 @@ __global__ void __launch_bounds__(512, 1)
 #pragma unroll
             for (int c = 0; c < 5; ++c) H[c] = Hs[c];
           };
-          auto offs = [&](long long zo[3], int pyo[3], int pxo[3], int xyz[3]) {
+          auto offs = [&](long long zo[3], int pyo[3], int pxo[3]) {
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
               zo[j] = zo3[j];
               pyo[j] = ymap[ty + 1 + j];
               pxo[j] = xmap[tx + 1 + j];
             }
-            xyz[0] = tl.x0 + tx;
-            xyz[1] = tl.y0 + ty;
-            xyz[2] = z;
           };
-          output_site<T, SHIFT, V, FORM, OBS>(I, cf, acc, offs, hs, ob6);
+          auto trg = [&](Vec2<T>& ctx, Vec2<T>& cty, Vec2<T>& ctz) {
+            ctx = lds2(xt + 2 * tx);
+            cty = lds2(yt + 2 * ty);
+            ctz = tz;
+          };
+          output_site<T, SHIFT, V, FORM, OBS>(I, cf, acc, offs, hs, trg, ob6);
         }
         if (OBS && site < G::IP) {
           T* dst = oshare + (z & 1) * G::IP * 12 + site * 12;
