@@ -314,15 +314,15 @@ __device__ __forceinline__ void obs_segment_end(const FusedObs& ob, int slot, in
 }
 
 // Pipelined kernel: the a6 shares of an output plane (sh[IP][12], site-major, left in shared
-// memory by the output warps) are added up in the next phase by the sigma threads, in the time
-// the sigma group otherwise waits at the plane barrier.  With NR = the largest multiple of 12
-// <= NS, sigma thread t < NR adds the elements t, t + NR, t + 2 NR, ... (all of value t % 12,
-// consecutive addresses across a warp) into its own Kahan accumulator acc[t] = (sum,
-// compensation): no shuffles and no atomics.
+// memory by the output warps) are added up in the next phase by the sigma threads that have no
+// site in the last sigma round, while the others finish it: threads R0 .. R0 + NR - 1 (G::R0,
+// G::NR, NR a multiple of 12).  Thread t = tid - R0 adds the elements t, t + NR, t + 2 NR, ...
+// (all of value t % 12, consecutive addresses across a warp) into its own Kahan accumulator
+// acc[t] = (sum, compensation): no shuffles and no atomics.
 template <typename T, class G>
 __device__ __forceinline__ void obs_sigma_reduce(const T* sh, T* acc) {
-  const int t = threadIdx.x;
-  if (t >= G::NR) return;
+  const int t = (int)threadIdx.x - G::R0;
+  if (t < 0 || t >= G::NR) return;
   T v = T(0);
 #pragma unroll 4
   for (int e = t; e < 12 * G::IP; e += G::NR) v += sh[e];
@@ -581,7 +581,12 @@ struct PipeGeom {
   static constexpr int NQS = 6, NSS = 4, NHS = 3, NUS = 4;
   static_assert(QP <= NT && SP <= NT && SP <= 2 * NS && NO >= IP, "site counts per thread");
   static_assert(NS % 32 == 0, "whole warps per group");
-  static constexpr int NR = NS / 12 * 12;  // sigma threads that add up the a6 shares
+  // a6 reducers: the sigma threads from R0 on, which have no site in the last sigma round
+  // (R0 rounded up to a warp where that leaves at least 12 threads)
+  static constexpr int RL = SP - (SP - 1) / NS * NS;  // sites of the last sigma round
+  static constexpr int R0 = ((RL + 31) / 32 * 32 < NS - 12) ? (RL + 31) / 32 * 32 : NS - 12;
+  static constexpr int NR = (NS - R0) / 12 * 12;
+  static_assert(NR >= 12, "a6 reducer threads");
   // a6: the output planes' shares [2][IP][12] (double-buffered by plane parity), the sigma
   // threads' accumulators [NR][2] in T, the tile's (cos, sin) of x and y [TX + TY][2], then
   // the segment's 12 FP64 values
