@@ -199,7 +199,7 @@ int lbcad_set_tiles(lbcad_ctx* c, int32_t cfg);
  * psi, momentum and centroid sums of the state it writes (per-site shares, per-block sums in
  * shared memory, per-segment FP64 partials, and a last-block sum per instance), and
  * lbcad_observables after such a step only copies them.  on = 0 runs the step kernels without
- * the sums (about 10% faster on the 128^3 workload); lbcad_observables then runs a separate
+ * the sums (about 5% faster on the 128^3 workload); lbcad_observables then runs a separate
  * reduction pass over the state.  Either way the state is the same.  Drops a captured graph. */
 int lbcad_set_observe(lbcad_ctx* c, int32_t on);
 
