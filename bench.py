@@ -253,7 +253,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-staged", action="store_true",
-                    help="skip the Heun / sync, LB-variant and bulk legs")
+                    help="skip the sync / Heun, LB-variant and bulk legs")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg (64^3, 500 steps)")
     ap.add_argument("--workload", default="droplet", choices=["droplet", "batch64"],
                     help="droplet: the 128^3 benchmark line; batch64: 64 uneven droplets in one launch")
@@ -331,16 +331,24 @@ def main():
                                     "fp64_pipe_active_pct", "lbcad_step_fp64_128cube.md")}
         s64.close()
 
-    # the staged path (Sec. 3 predictor-corrector and sync coupling) on the same workload
+    # Sec. 3's sync coupling and predictor-corrector on the same workload: Euler + sync on the
+    # fused path (the LB half in the fused kernel, then the order-parameter kernel) and on the
+    # staged path; Heun + sync on the staged path
     staged = None
     if not args.no_staged:
         staged = {}
-        for name, integ, coup, launches in (("euler_sync", L.EULER, L.SYNC, 3), ("heun_sync", L.HEUN, L.SYNC, 5)):
+        for name, integ, coup, path, launches in (
+                ("euler_sync", L.EULER, L.SYNC, "fused LB half + order-parameter kernel", 2),
+                ("euler_sync_staged", L.EULER, L.SYNC, "staged", 3),
+                ("heun_sync", L.HEUN, L.SYNC, "staged", 5)):
             sv = L.Simulation([(n, n, n)], [workload_params(L, n, L.FP32, integrator=integ, coupling=coup)],
                               seed=1 + rank, device=local)
+            if path == "staged":
+                sv.set_path(L.lbcad.PATH_STAGED)
             sv.step(3)
             msv = time_steps(sv, torch, 20)
-            staged[name] = {"mlups": N / (msv * 1e-3) / 1e6, "ms_per_step": msv, "kernels_per_step": launches}
+            staged[name] = {"mlups": N / (msv * 1e-3) / 1e6, "ms_per_step": msv, "kernels_per_step": launches,
+                            "path": path}
             sv.close()
 
     # the other LB variants of Sec. 3 on the same workload: D3Q15 and the Eq. 9-11 form on the
@@ -467,7 +475,7 @@ def main():
                            "a6": "FP64 mass, psi, momentum and centroid sums of every step, fused"},
                 "roofline": roofline, "roofline_issue": roofline_issue, "cpu_baseline": cpu, "e2e": e2e,
                 "tiles": {"chosen": TILE_NAMES[tile_cfg], "ms_per_cfg": dict(zip(TILE_NAMES, tile_ms))},
-                "gpu_launches": K, "clocks": csum, "step_without_sums": without_sums, "fp64_gpu": fp64, "staged_fp32": staged, "lb_variants_fp32": variants, "bulk_fp32": bulk, "adjoint_fp32": adjoint,
+                "gpu_launches": K, "clocks": csum, "step_without_sums": without_sums, "fp64_gpu": fp64, "integrators_fp32": staged, "lb_variants_fp32": variants, "bulk_fp32": bulk, "adjoint_fp32": adjoint,
                 "speedup_fp32_vs_fp64": (value / world / fp64["mlups"]) if fp64 else None,
                 "observables_finite": finite}
         print(json.dumps(line))

@@ -184,10 +184,45 @@ struct AntiPairAcc {
 // late (after the stencils, after the pulls), so that their values do not hold registers
 // through the earlier work.  ob (OBS): the site's share of the a6 sums of the new state (see
 // FusedObs); trg(tx, ty, tz) gives (cos, sin) of 2 pi x/nx, 2 pi y/ny and 2 pi z/nz of the site.
-template <typename T, bool SHIFT, class V, int FORM, bool OBS, class A, class Offs, class HS, class TR>
+template <typename T, bool SHIFT, class V, int FORM, int MODE, class A, class Offs, class HS, class TR>
 __device__ __forceinline__ void output_site(const InstDesc<T>& I, const Coef<T>& cf, const A& acc, const Offs& offs,
                                             const HS& hs, const TR& trg, T ob[12]) {
+  constexpr bool OBS = MODE == kFusedSums;
   const long long N = I.N;
+  if constexpr (MODE == kFusedLbOnly) {
+    // sync coupling, first half: force, pull and collision (u of this step), and H and mu of
+    // the site into the scratch that the order-parameter kernel reads
+    T F[3];
+    if constexpr (FORM == 0) gather_force<T>(acc, F);
+    else gather_force<T>(AntiPairAcc<T, A>{acc}, F);
+    long long zo[3];
+    int pyo[3], pxo[3];
+    offs(zo, pyo, pxo);
+    T g[V::Q];
+#pragma unroll
+    for (int i = 0; i < V::Q; ++i)
+      g[i] = ld(I.g_in + i * N + zo[1 - V::c(i, 2)] + pyo[1 - V::c(i, 1)] + pxo[1 - V::c(i, 0)]);
+    T u[3];
+    if constexpr (FORM == 0) {
+      lb_collide<T, SHIFT, V>(cf, F, g, u);
+    } else {
+      T sg[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) sg[c] = pair_comp<T>(acc, c, 0, 0, 0);
+      lb_collide_stress<T, SHIFT, V>(cf, F, sg, g, u);
+    }
+    const long long s = zo[1] + pyo[1] + pxo[1];
+#pragma unroll
+    for (int i = 0; i < V::Q; ++i) I.g_out[i * N + s] = g[i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) I.u_out[a * N + s] = u[a];
+    T Hs[5];
+    hs(Hs);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) I.H[k * N + s] = Hs[k];
+    I.mu[s] = acc.spair(4, 0, 0, 0).y;
+    return;
+  }
   T F[3], lapmu, Wg[3][3], q0[5], qf[6][5], p0, pf[6], u0[3], uf[6];
   if constexpr (FORM == 0) gather_force<T>(acc, F);
   else gather_force<T>(AntiPairAcc<T, A>{acc}, F);
@@ -346,10 +381,11 @@ __device__ __forceinline__ int qslot(int p) { return (p + 10) % 5; }
 __device__ __forceinline__ int sslot(int p) { return (p + 9) % 3; }
 __device__ __forceinline__ int uslot(int p) { return (p + 8) % 4; }
 
-template <typename T, bool SHIFT, int TX, int TY, class V, int FORM, bool OBS>
+template <typename T, bool SHIFT, int TX, int TY, class V, int FORM, int MODE>
 __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 2 : 1)
     k_step_fused(const InstDesc<T>* __restrict__ D, const FusedTile* __restrict__ tiles, int ntiles,
                  long long total, FusedObs ob) {
+  constexpr bool OBS = MODE == kFusedSums;
   using G = FusedGeom<T, TX, TY>;
   constexpr int QW = G::QW, QP = G::QP, SW = G::SW, SH = G::SH, SP = G::SP, NT = G::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -544,7 +580,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
           cty = ldg2(I.trig + 2 * (nx + tl.y0 + ty));
           ctz = ldg2(I.trig + 2 * (nx + ny + z));
         };
-        output_site<T, SHIFT, V, FORM, OBS>(I, cf, acc, offs, hs, trg, ob6);
+        output_site<T, SHIFT, V, FORM, MODE>(I, cf, acc, offs, hs, trg, ob6);
       }
       if constexpr (OBS)
         if (z >= zb) obs_warp_add<T>(ob6, oacc + (tid >> 5) * 24);
@@ -632,10 +668,11 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
   if constexpr (sizeof(T) == 4) cp_async4(dst, src); else cp_async8(dst, src);
 }
 
-template <typename T, bool SHIFT, int TY, int NS, class V, int FORM, bool OBS>
+template <typename T, bool SHIFT, int TY, int NS, class V, int FORM, int MODE>
 __global__ void __launch_bounds__(512, 1)
     k_step_pipe(const InstDesc<T>* __restrict__ D, const FusedTile* __restrict__ tiles, int ntiles, long long total,
                 FusedObs ob) {
+  constexpr bool OBS = MODE == kFusedSums;
   using G = PipeGeom<TY, NS>;
   constexpr int QW = G::QW, QP = G::QP, SW = G::SW, SP = G::SP, TX = G::TX;
   constexpr int QSLOT = 6 * QP, SSLOT = 10 * SP, HSLOT = 5 * G::IP, USLOT = 3 * SP;
@@ -792,7 +829,7 @@ __global__ void __launch_bounds__(512, 1)
             cty = lds2(yt + 2 * ty);
             ctz = tz;
           };
-          output_site<T, SHIFT, V, FORM, OBS>(I, cf, acc, offs, hs, trg, ob6);
+          output_site<T, SHIFT, V, FORM, MODE>(I, cf, acc, offs, hs, trg, ob6);
         }
         if (OBS && site < G::IP) {
           T* dst = oshare + (z & 1) * G::IP * 12 + site * 12;
@@ -824,26 +861,30 @@ cudaError_t launch_cfg(const InstDesc<T>* d_desc, const FusedTile* tiles, int nt
                        const FusedObs& ob, bool obs, cudaStream_t s) {
   using G = FusedGeom<T, TX, TY>;
   if (obs)
-    k_step_fused<T, SHIFT, TX, TY, V, FORM, true><<<grid, G::NT, G::bytes(true), s>>>(d_desc, tiles, ntiles, total, ob);
+    k_step_fused<T, SHIFT, TX, TY, V, FORM, kFusedSums><<<grid, G::NT, G::bytes(true), s>>>(d_desc, tiles, ntiles,
+                                                                                            total, ob);
   else
-    k_step_fused<T, SHIFT, TX, TY, V, FORM, false><<<grid, G::NT, G::bytes(false), s>>>(d_desc, tiles, ntiles, total,
-                                                                                        ob);
+    k_step_fused<T, SHIFT, TX, TY, V, FORM, kFusedPlain><<<grid, G::NT, G::bytes(false), s>>>(d_desc, tiles, ntiles,
+                                                                                              total, ob);
   return cudaGetLastError();
 }
 
 // Both kernels of a tile shape (with and without the a6 sums); the launch resources are those
 // of the one with the sums (more shared memory), so that both run on the same grid.
-template <typename T, bool SHIFT, int TX, int TY, class V, int FORM>
+template <typename T, bool SHIFT, int TX, int TY, class V, int FORM, bool LB = false>
 cudaError_t prepare_cfg(FusedCfg* cfg) {
   using G = FusedGeom<T, TX, TY>;
-  auto k0 = k_step_fused<T, SHIFT, TX, TY, V, FORM, false>;
-  auto k1 = k_step_fused<T, SHIFT, TX, TY, V, FORM, true>;
+  auto k0 = k_step_fused<T, SHIFT, TX, TY, V, FORM, kFusedPlain>;
+  auto k1 = k_step_fused<T, SHIFT, TX, TY, V, FORM, kFusedSums>;
+  auto k2 = k_step_fused<T, SHIFT, TX, TY, V, FORM, kFusedLbOnly>;
   cfg->tx = TX;
   cfg->ty = TY;
   cfg->threads = G::NT;
   cfg->smem = G::bytes(true);
   cudaError_t e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::bytes(false));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::bytes(true));
+  if (e == cudaSuccess && LB)
+    e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::bytes(false));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cfg->blocks_per_sm, k1, G::NT, G::bytes(true));
 }
@@ -857,11 +898,12 @@ int LaunchFused<T, SHIFT>::num_configs() {
   return sizeof(T) == 4 ? 7 : 1;
 }
 
-template <typename T, bool SHIFT, int TY, int NS, class V, int FORM>
+template <typename T, bool SHIFT, int TY, int NS, class V, int FORM, bool LB = false>
 cudaError_t prepare_pipe(FusedCfg* cfg) {
   using G = PipeGeom<TY, NS>;
-  auto k0 = k_step_pipe<T, SHIFT, TY, NS, V, FORM, false>;
-  auto k1 = k_step_pipe<T, SHIFT, TY, NS, V, FORM, true>;
+  auto k0 = k_step_pipe<T, SHIFT, TY, NS, V, FORM, kFusedPlain>;
+  auto k1 = k_step_pipe<T, SHIFT, TY, NS, V, FORM, kFusedSums>;
+  auto k2 = k_step_pipe<T, SHIFT, TY, NS, V, FORM, kFusedLbOnly>;
   cfg->tx = G::TX;
   cfg->ty = G::TY;
   cfg->threads = G::NT;
@@ -869,6 +911,8 @@ cudaError_t prepare_pipe(FusedCfg* cfg) {
   cudaError_t e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::template bytes<T>(false));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::template bytes<T>(true));
+  if (e == cudaSuccess && LB)
+    e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::template bytes<T>(false));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cfg->blocks_per_sm, k1, G::NT, cfg->smem);
 }
@@ -878,11 +922,11 @@ cudaError_t launch_pipe(const InstDesc<T>* d_desc, const FusedTile* tiles, int n
                         const FusedObs& ob, bool obs, cudaStream_t s) {
   using G = PipeGeom<TY, NS>;
   if (obs)
-    k_step_pipe<T, SHIFT, TY, NS, V, FORM, true><<<grid, G::NT, G::template bytes<T>(true), s>>>(d_desc, tiles, ntiles,
-                                                                                                 total, ob);
+    k_step_pipe<T, SHIFT, TY, NS, V, FORM, kFusedSums><<<grid, G::NT, G::template bytes<T>(true), s>>>(
+        d_desc, tiles, ntiles, total, ob);
   else
-    k_step_pipe<T, SHIFT, TY, NS, V, FORM, false><<<grid, G::NT, G::template bytes<T>(false), s>>>(d_desc, tiles, ntiles,
-                                                                                                   total, ob);
+    k_step_pipe<T, SHIFT, TY, NS, V, FORM, kFusedPlain><<<grid, G::NT, G::template bytes<T>(false), s>>>(
+        d_desc, tiles, ntiles, total, ob);
   return cudaGetLastError();
 }
 
@@ -899,10 +943,23 @@ struct FusedVariant {
         if (k == 5) return prepare_pipe<T, SHIFT, 6, 288, V, FORM>(cfg);
         if (k == 6) return prepare_pipe<T, SHIFT, 6, 320, V, FORM>(cfg);
       }
-      if (k == 3) return prepare_pipe<T, SHIFT, 8, 256, V, FORM>(cfg);
+      if (k == 3) return prepare_pipe<T, SHIFT, 8, 256, V, FORM, true>(cfg);
     }
-    if (k == 0) return prepare_cfg<T, SHIFT, 32, 8, V, FORM>(cfg);
+    if (k == 0) return prepare_cfg<T, SHIFT, 32, 8, V, FORM, sizeof(T) == 8>(cfg);
     return k >= 0 && k < LaunchFused<T, SHIFT>::num_configs() ? cudaErrorNotSupported : cudaErrorInvalidValue;
+  }
+  // the first half of a sync-coupled step: FP32 on the pipelined 32x8 schedule, FP64 on 32x8
+  static cudaError_t step_lb(const InstDesc<T>* d, const FusedTile* t, int nt, long long total, int grid,
+                             const FusedObs& ob, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+      using G = PipeGeom<8, 256>;
+      k_step_pipe<T, SHIFT, 8, 256, V, FORM, kFusedLbOnly><<<grid, G::NT, G::template bytes<T>(false), s>>>(
+          d, t, nt, total, ob);
+    } else {
+      using G = FusedGeom<T, 32, 8>;
+      k_step_fused<T, SHIFT, 32, 8, V, FORM, kFusedLbOnly><<<grid, G::NT, G::bytes(false), s>>>(d, t, nt, total, ob);
+    }
+    return cudaGetLastError();
   }
   static cudaError_t step(int k, const InstDesc<T>* d, const FusedTile* t, int nt, long long total, int grid,
                           const FusedObs& ob, bool obs, cudaStream_t s) {
@@ -929,6 +986,23 @@ cudaError_t LaunchFused<T, SHIFT>::prepare(int variant, int cfg_index, FusedCfg*
     case 1: return FusedVariant<T, SHIFT, VelD3Q15, 0>::prepare(cfg_index, cfg);
     case 2: return FusedVariant<T, SHIFT, VelD3Q19, 1>::prepare(cfg_index, cfg);
     case 3: return FusedVariant<T, SHIFT, VelD3Q15, 1>::prepare(cfg_index, cfg);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, bool SHIFT>
+int LaunchFused<T, SHIFT>::sync_config() {
+  return sizeof(T) == 4 ? 3 : 0;
+}
+
+template <typename T, bool SHIFT>
+cudaError_t LaunchFused<T, SHIFT>::step_lb(int variant, const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles,
+                                           long long total, int grid, const FusedObs& ob, cudaStream_t s) {
+  switch (variant) {
+    case 0: return FusedVariant<T, SHIFT, VelD3Q19, 0>::step_lb(d_desc, tiles, ntiles, total, grid, ob, s);
+    case 1: return FusedVariant<T, SHIFT, VelD3Q15, 0>::step_lb(d_desc, tiles, ntiles, total, grid, ob, s);
+    case 2: return FusedVariant<T, SHIFT, VelD3Q19, 1>::step_lb(d_desc, tiles, ntiles, total, grid, ob, s);
+    case 3: return FusedVariant<T, SHIFT, VelD3Q15, 1>::step_lb(d_desc, tiles, ntiles, total, grid, ob, s);
   }
   return cudaErrorInvalidValue;
 }

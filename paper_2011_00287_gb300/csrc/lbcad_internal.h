@@ -93,6 +93,9 @@ struct Launch {
   // stencil: 0 = isotropic D3Q19 finite differences, 1 = fourth-order radius-2 differences.
   static cudaError_t staged(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, bool heun,
                             bool sync, int vel, int form, int stencil, cudaStream_t s);
+  // The order-parameter update with the velocity of this step (u_out) and H, mu from the
+  // scratch: the second half of a sync-coupled step after LaunchFused::step_lb.
+  static cudaError_t op_sync(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, cudaStream_t s);
   static cudaError_t get_fields(const InstDesc<T>& I, uint32_t mask, double* dst, cudaStream_t s);
   static cudaError_t set_fields(const InstDesc<T>& I, uint32_t mask, const double* src, T* g_target,
                                 T* q_target, T* psi_target, T* u_target, cudaStream_t s);
@@ -111,6 +114,10 @@ struct FusedCfg {
   int tx = 0, ty = 0, threads = 0, blocks_per_sm = 0;
   size_t smem = 0;
 };
+
+// What a fused step kernel does: the whole step (kFusedPlain), the whole step and the a6 sums
+// (kFusedSums), or the LB half of a sync-coupled step (kFusedLbOnly).
+constexpr int kFusedPlain = 0, kFusedSums = 1, kFusedLbOnly = 2;
 
 // The FP64 conserved and centroid sums of the fused step (a6).  Each column segment a block
 // works on has a slot of 12 partial sums (block b, segment j of the block: slot b * maxseg + j);
@@ -139,6 +146,11 @@ struct LaunchFused {
   // obs: the kernel that also forms the a6 sums of the new state (FusedObs)
   static cudaError_t step(int variant, int cfg_index, const InstDesc<T>* d_desc, const FusedTile* tiles,
                           int ntiles, long long total, int grid, const FusedObs& ob, bool obs, cudaStream_t s);
+  // Sync coupling: the first half of the step (force, pull, collision, u of this step; H and mu
+  // of every site into the scratch), on tile shape sync_config(); Launch::op_sync finishes it.
+  static int sync_config();
+  static cudaError_t step_lb(int variant, const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles,
+                             long long total, int grid, const FusedObs& ob, cudaStream_t s);
 };
 
 // Buffers of one reverse step of the adjoint (lbcad_adjoint.cuh).

@@ -100,10 +100,11 @@ struct lbcad_ctx {
   void* adj_lam = nullptr;  // cotangent of the initial state of the last lbcad_adjoint
   std::string err;
   size_t elem() const { return prec == LBCAD_FP64 ? sizeof(double) : sizeof(float); }
-  // Heun, sync and the radius-2 stencils run on the staged path only
-  bool staged_only() const {
-    return integrator != LBCAD_EULER || coupling != LBCAD_LAGGED || stencil != LBCAD_STENCIL_ISO;
-  }
+  // Heun and the radius-2 stencils run on the staged path only
+  bool staged_only() const { return integrator != LBCAD_EULER || stencil != LBCAD_STENCIL_ISO; }
+  // Euler with sync coupling on the fused path: the LB half in the fused kernel on a fixed tile
+  // shape, then the order-parameter kernel
+  bool sync_split() const { return !staged_only() && coupling == LBCAD_SYNC; }
   // D3Q19 with the body force: the two-kernel path and the adjoint cover this LB only
   bool default_lb() const { return vel == LBCAD_D3Q19 && lb_form == LBCAD_LB_BODY_FORCE; }
   // variant of the fused kernels (see LaunchFused)
@@ -269,6 +270,7 @@ int upload_init(lbcad_ctx* c, Inst& I, uint64_t seed, int idx) {
 int upload_descs(lbcad_ctx* c);
 int prepare_fused(lbcad_ctx* c, int cfg_index);
 int ensure_scratch(lbcad_ctx* c);
+cudaError_t launch_fused_lb(lbcad_ctx* c, int par);
 
 int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint64_t seed, lbcad_ctx** out) {
   g_create_err.clear();
@@ -380,11 +382,14 @@ int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint
   c->obs_out = (double*)dev_alloc(c, 12 * sizeof(double));
   if (!c->obs_partial || !c->obs_out) return bail(LBCAD_E_OOM, "device allocation failed");
   if (upload_descs(c) != LBCAD_OK) return bail(LBCAD_E_CUDA, "");
-  if ((code = prepare_fused(c, 0)) != LBCAD_OK) return bail(code, "");
-  if (c->staged_only()) {
+  const int cfg0 = !c->sync_split() ? 0
+                   : (c->prec == LBCAD_FP64 ? LaunchFused<double, false>::sync_config()
+                                            : LaunchFused<float, true>::sync_config());
+  if ((code = prepare_fused(c, cfg0)) != LBCAD_OK) return bail(code, "");
+  if (c->staged_only() || c->sync_split()) {
     if ((code = ensure_scratch(c)) != LBCAD_OK) return bail(code, "");
-    c->path = LBCAD_PATH_STAGED;
   }
+  if (c->staged_only()) c->path = LBCAD_PATH_STAGED;
   for (int i = 0; i < n; ++i) {
     code = (c->prec == LBCAD_FP64) ? upload_init<double>(c, c->inst[i], seed, i)
                                    : upload_init<float>(c, c->inst[i], seed, i);
@@ -539,6 +544,16 @@ cudaError_t launch_fused(lbcad_ctx* c, int par) {
                                         c->fused_total, c->fused_grid, ob, c->observe, c->stream);
 }
 
+cudaError_t launch_fused_lb(lbcad_ctx* c, int par) {
+  const int v = c->fused_variant();
+  FusedObs ob{};  // the LB half forms no sums
+  if (c->prec == LBCAD_FP64)
+    return LaunchFused<double, false>::step_lb(v, (const InstDesc<double>*)c->desc[par], c->tiles, c->ntiles,
+                                               c->fused_total, c->fused_grid, ob, c->stream);
+  return LaunchFused<float, true>::step_lb(v, (const InstDesc<float>*)c->desc[par], c->tiles, c->ntiles,
+                                           c->fused_total, c->fused_grid, ob, c->stream);
+}
+
 void drop_graph(lbcad_ctx* c) {
   if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
   if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
@@ -549,7 +564,15 @@ int launch_steps(lbcad_ctx* c, int64_t n) {
     const int par = (int)(c->step & 1);
     cudaError_t e;
     const bool heun = c->integrator == LBCAD_HEUN, sync = c->coupling == LBCAD_SYNC;
-    if (c->path == LBCAD_PATH_FUSED) {
+    if (c->path == LBCAD_PATH_FUSED && c->sync_split()) {
+      e = launch_fused_lb(c, par);
+      if (e == cudaSuccess)
+        e = (c->prec == LBCAD_FP64)
+                ? Launch<double, false>::op_sync((const InstDesc<double>*)c->desc[par], (int)c->inst.size(),
+                                                 c->total_blocks, kStepBlock, c->stream)
+                : Launch<float, true>::op_sync((const InstDesc<float>*)c->desc[par], (int)c->inst.size(),
+                                               c->total_blocks, kStepBlock, c->stream);
+    } else if (c->path == LBCAD_PATH_FUSED) {
       e = launch_fused(c, par);
     } else if (c->path == LBCAD_PATH_STAGED) {
       e = (c->prec == LBCAD_FP64)
@@ -628,9 +651,9 @@ int lbcad_set_path(lbcad_ctx* c, int32_t path) {
   if (path != LBCAD_PATH_FUSED && path != LBCAD_PATH_TWO_KERNEL && path != LBCAD_PATH_STAGED)
     return fail(c, LBCAD_E_INVALID_ARG, "unknown path");
   if (path != LBCAD_PATH_STAGED && c->staged_only())
-    return fail(c, LBCAD_E_UNSUPPORTED, "Heun, sync or radius-2 contexts run on the staged path only");
-  if (path == LBCAD_PATH_TWO_KERNEL && !c->default_lb())
-    return fail(c, LBCAD_E_UNSUPPORTED, "the two-kernel path covers D3Q19 with the body force only");
+    return fail(c, LBCAD_E_UNSUPPORTED, "Heun or radius-2 contexts run on the staged path only");
+  if (path == LBCAD_PATH_TWO_KERNEL && (!c->default_lb() || c->coupling != LBCAD_LAGGED))
+    return fail(c, LBCAD_E_UNSUPPORTED, "the two-kernel path covers lagged D3Q19 with the body force only");
   DeviceGuard dg(c->device);
   if (path != LBCAD_PATH_FUSED) {
     int r = ensure_scratch(c);
@@ -648,6 +671,7 @@ int lbcad_set_path(lbcad_ctx* c, int32_t path) {
 int lbcad_autotune(lbcad_ctx* c, int32_t reps, int32_t* chosen, float* ms_per_cfg, int32_t ncfg) {
   if (!c || reps < 1) return LBCAD_E_INVALID_ARG;
   if (c->staged_only()) return fail(c, LBCAD_E_UNSUPPORTED, "tile shapes belong to the fused path (Euler, lagged)");
+  if (c->sync_split()) return fail(c, LBCAD_E_UNSUPPORTED, "sync coupling runs on one fixed fused tile shape");
   DeviceGuard dg(c->device);
   const int n = (c->prec == LBCAD_FP64) ? LaunchFused<double, false>::num_configs()
                                         : LaunchFused<float, true>::num_configs();
@@ -697,6 +721,7 @@ int lbcad_autotune(lbcad_ctx* c, int32_t reps, int32_t* chosen, float* ms_per_cf
 int lbcad_set_tiles(lbcad_ctx* c, int32_t cfg) {
   if (!c) return LBCAD_E_INVALID_ARG;
   if (c->staged_only()) return fail(c, LBCAD_E_UNSUPPORTED, "tile shapes belong to the fused path (Euler, lagged)");
+  if (c->sync_split()) return fail(c, LBCAD_E_UNSUPPORTED, "sync coupling runs on one fixed fused tile shape");
   DeviceGuard dg(c->device);
   const int n = (c->prec == LBCAD_FP64) ? LaunchFused<double, false>::num_configs()
                                         : LaunchFused<float, true>::num_configs();
@@ -756,7 +781,7 @@ int lbcad_step(lbcad_ctx* c, int64_t n) {
   }
   int r = launch_steps(c, left);
   // after a fused step the a6 sums of the new state are in obs_latest
-  if (r == LBCAD_OK && n > 0) c->obs_valid = c->path == LBCAD_PATH_FUSED && c->observe;
+  if (r == LBCAD_OK && n > 0) c->obs_valid = c->path == LBCAD_PATH_FUSED && c->observe && !c->sync_split();
   return r;
 }
 
@@ -1050,7 +1075,7 @@ int lbcad_adjoint(lbcad_ctx* c, int64_t nsteps, int32_t ckpt_every, double* dJ_d
                   double* dJ_dQ0, double* J) {
   if (!c) return LBCAD_E_INVALID_ARG;
   if (c->inst.size() != 1) return fail(c, LBCAD_E_UNSUPPORTED, "the adjoint runs on single-instance contexts");
-  if (c->staged_only() || !c->default_lb())
+  if (c->staged_only() || c->coupling != LBCAD_LAGGED || !c->default_lb())
     return fail(c, LBCAD_E_UNSUPPORTED, "the adjoint differentiates the Euler, lagged step of D3Q19 with the body force");
   if (nsteps < 1 || ckpt_every < 1) return fail(c, LBCAD_E_INVALID_ARG, "need nsteps >= 1 and ckpt_every >= 1");
   DeviceGuard dg(c->device);

@@ -27,14 +27,19 @@ def built():
     O.build()
 
 
+@pytest.mark.parametrize("path", ["default", "staged"])
 @pytest.mark.parametrize("var", VARIANTS, ids=["heun-lagged", "euler-sync", "heun-sync"])
 @pytest.mark.parametrize("shape,kw", [
     ((32, 32, 32), KW0),
     ((21, 13, 10), dict(R=4.0, p0=8.0, zeta=0.01, W=0.05)),
     ((4, 5, 6), dict(R=2.0, p0=6.0)),
 ])
-def test_fp64_parity_10_steps(shape, kw, var):
+def test_fp64_parity_10_steps(shape, kw, var, path):
+    """Heun runs on the staged path; Euler with sync coupling by default on the fused path
+    (the LB half in the fused kernel, then the order-parameter kernel), or staged."""
     sim = L.Simulation([shape], [_lib_params(shape, L.FP64, **kw, **var)], seed=2)
+    if path == "staged":
+        sim.set_path(L.lbcad.PATH_STAGED)
     sim.step(10)
     ref = _oracle(shape, seed=2, **kw, **var).step(10)
     _compare_fp64(sim.get_fields(0), ref)
@@ -79,6 +84,41 @@ def test_staged_euler_lagged_agrees_with_fused(prec):
         else:
             x, y = (_shifted(fa[k]), _shifted(fb[k])) if k == "g" else (fa[k], fb[k])
             assert _rel_l2(x, y) <= 1e-6, k
+
+
+@pytest.mark.parametrize("prec", [L.FP32, L.FP64])
+def test_sync_split_agrees_with_the_staged_path(prec):
+    """Euler with sync coupling: the fused split (default) and the staged path evaluate the
+    same per-site functions in a different kernel split; agreement to rounding, also for a
+    batch of uneven instances replayed from a graph."""
+    shapes = [(40, 18, 12), (16, 12, 10)]
+    kws = [dict(R=5.0, p0=8.0, zeta=0.01), dict(R=3.0, p0=8.0, zeta=0.004)]
+    prm = [_lib_params(s_, prec, **k, coupling=L.SYNC) for s_, k in zip(shapes, kws)]
+    a = L.Simulation(shapes, prm, seed=3)
+    b = L.Simulation(shapes, prm, seed=3)
+    b.set_path(L.lbcad.PATH_STAGED)
+    a.set_graph(4)
+    a.step(20)
+    b.step(20)
+    for i in range(len(shapes)):
+        fa, fb = a.get_fields(i), b.get_fields(i)
+        for k in fa:
+            if prec == L.FP64:
+                assert np.abs(fa[k] - fb[k]).max() <= 1e-13, (i, k)
+            else:
+                x, y = (_shifted(fa[k]), _shifted(fb[k])) if k == "g" else (fa[k], fb[k])
+                assert _rel_l2(x, y) <= 1e-6, (i, k)
+
+
+def test_sync_split_refuses_tile_choices_and_the_adjoint():
+    shape = (8, 8, 8)
+    sim = L.Simulation([shape], [_lib_params(shape, L.FP32, coupling=L.SYNC)], seed=1)
+    for call in (lambda: sim.set_tiles(0), lambda: sim.autotune(1), lambda: sim.adjoint(2, 1),
+                 lambda: sim.set_path(L.lbcad.PATH_TWO_KERNEL)):
+        with pytest.raises(L.LbcadError):
+            call()
+    sim.step(2)
+    assert np.isfinite(sim.observables(0)).all()
 
 
 def test_batch_heun_sync_instances_match_oracle():
