@@ -331,16 +331,16 @@ def main():
                                     "fp64_pipe_active_pct", "lbcad_step_fp64_128cube.md")}
         s64.close()
 
-    # Sec. 3's sync coupling and predictor-corrector on the same workload: Euler + sync on the
-    # fused path (the LB half in the fused kernel, then the order-parameter kernel) and on the
-    # staged path; Heun + sync on the staged path
+    # Sec. 3's sync coupling and predictor-corrector on the same workload, on the fused split
+    # (the LB half in the fused kernel, then the order-parameter kernels) and on the staged path
     staged = None
     if not args.no_staged:
         staged = {}
         for name, integ, coup, path, launches in (
                 ("euler_sync", L.EULER, L.SYNC, "fused LB half + order-parameter kernel", 2),
                 ("euler_sync_staged", L.EULER, L.SYNC, "staged", 3),
-                ("heun_sync", L.HEUN, L.SYNC, "staged", 5)):
+                ("heun_sync", L.HEUN, L.SYNC, "fused LB half + predictor, fields, corrector", 4),
+                ("heun_sync_staged", L.HEUN, L.SYNC, "staged", 5)):
             sv = L.Simulation([(n, n, n)], [workload_params(L, n, L.FP32, integrator=integ, coupling=coup)],
                               seed=1 + rank, device=local)
             if path == "staged":

@@ -167,16 +167,17 @@ int lbcad_step(lbcad_ctx* c, int64_t n);
 #define LBCAD_PATH_TWO_KERNEL 1
 /* LBCAD_PATH_STAGED: per-site kernels in the order fields -> LB (force, pull, collision;
  * writes u of this step) -> order-parameter update, and for LBCAD_HEUN a second fields
- * pass at the predicted Q, psi and the corrector (Sec. 3).  The only path for LBCAD_HEUN or
- * LBCAD_STENCIL_R2, selected at create; other contexts may select it as a cross-check (same
- * per-site arithmetic).  Scratch: 15 values per site, 27 with LBCAD_HEUN.  Fused/two-kernel
- * paths, tile shapes, autotune and the adjoint return LBCAD_E_UNSUPPORTED on those contexts.
- * LBCAD_EULER with LBCAD_SYNC runs on the fused path as two kernels per step: the fused kernel
- * on one fixed tile shape does the LB half (u of this step; H and mu into a scratch of 6 values
- * per site), then the order-parameter update; tile shapes, autotune, the two-kernel path and
- * the adjoint return LBCAD_E_UNSUPPORTED there.  LBCAD_D3Q15 and LBCAD_LB_STRESS_EQ run on the
- * fused path (tile shapes 0 and 3 only) and the staged path; the two-kernel path and the
- * adjoint return LBCAD_E_UNSUPPORTED for them. */
+ * pass at the predicted Q, psi and the corrector (Sec. 3).  The only path for
+ * LBCAD_STENCIL_R2, selected at create (fused/two-kernel paths, tile shapes, autotune and the
+ * adjoint return LBCAD_E_UNSUPPORTED there); other contexts may select it as a cross-check
+ * (same per-site arithmetic).  Scratch: 15 values per site, 27 with LBCAD_HEUN.
+ * LBCAD_SYNC or LBCAD_HEUN on the fused path (their default): the fused kernel on one fixed
+ * tile shape does the LB half (u of this step; H and mu into the scratch), then the staged
+ * path's order-parameter kernels (sync: the update; Heun: predictor, fields at the predicted
+ * state, corrector); tile shapes, autotune, the two-kernel path and the adjoint return
+ * LBCAD_E_UNSUPPORTED there.  LBCAD_D3Q15 and LBCAD_LB_STRESS_EQ run on the fused path (tile
+ * shapes 0 and 3 only) and the staged path; the two-kernel path and the adjoint return
+ * LBCAD_E_UNSUPPORTED for them. */
 #define LBCAD_PATH_STAGED 2
 int lbcad_set_path(lbcad_ctx* c, int32_t path);
 

@@ -96,6 +96,10 @@ struct Launch {
   // The order-parameter update with the velocity of this step (u_out) and H, mu from the
   // scratch: the second half of a sync-coupled step after LaunchFused::step_lb.
   static cudaError_t op_sync(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, cudaStream_t s);
+  // Heun after LaunchFused::step_lb: predictor, H and mu at the predicted Q, psi, corrector
+  // (advecting with u of this step when sync, else with u of the previous step).
+  static cudaError_t op_heun(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, bool sync,
+                             cudaStream_t s);
   static cudaError_t get_fields(const InstDesc<T>& I, uint32_t mask, double* dst, cudaStream_t s);
   static cudaError_t set_fields(const InstDesc<T>& I, uint32_t mask, const double* src, T* g_target,
                                 T* q_target, T* psi_target, T* u_target, cudaStream_t s);
@@ -146,8 +150,9 @@ struct LaunchFused {
   // obs: the kernel that also forms the a6 sums of the new state (FusedObs)
   static cudaError_t step(int variant, int cfg_index, const InstDesc<T>* d_desc, const FusedTile* tiles,
                           int ntiles, long long total, int grid, const FusedObs& ob, bool obs, cudaStream_t s);
-  // Sync coupling: the first half of the step (force, pull, collision, u of this step; H and mu
-  // of every site into the scratch), on tile shape sync_config(); Launch::op_sync finishes it.
+  // Sync coupling or Heun: the first half of the step (force, pull, collision, u of this step;
+  // H and mu of every site into the scratch), on tile shape sync_config(); Launch::op_sync or
+  // Launch::op_heun finishes it.
   static int sync_config();
   static cudaError_t step_lb(int variant, const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles,
                              long long total, int grid, const FusedObs& ob, cudaStream_t s);

@@ -100,11 +100,11 @@ struct lbcad_ctx {
   void* adj_lam = nullptr;  // cotangent of the initial state of the last lbcad_adjoint
   std::string err;
   size_t elem() const { return prec == LBCAD_FP64 ? sizeof(double) : sizeof(float); }
-  // Heun and the radius-2 stencils run on the staged path only
-  bool staged_only() const { return integrator != LBCAD_EULER || stencil != LBCAD_STENCIL_ISO; }
-  // Euler with sync coupling on the fused path: the LB half in the fused kernel on a fixed tile
-  // shape, then the order-parameter kernel
-  bool sync_split() const { return !staged_only() && coupling == LBCAD_SYNC; }
+  // the radius-2 stencils run on the staged path only
+  bool staged_only() const { return stencil != LBCAD_STENCIL_ISO; }
+  // sync coupling or Heun on the fused path: the LB half in the fused kernel on a fixed tile
+  // shape, then the order-parameter kernels
+  bool sync_split() const { return !staged_only() && (coupling == LBCAD_SYNC || integrator == LBCAD_HEUN); }
   // D3Q19 with the body force: the two-kernel path and the adjoint cover this LB only
   bool default_lb() const { return vel == LBCAD_D3Q19 && lb_form == LBCAD_LB_BODY_FORCE; }
   // variant of the fused kernels (see LaunchFused)
@@ -566,12 +566,19 @@ int launch_steps(lbcad_ctx* c, int64_t n) {
     const bool heun = c->integrator == LBCAD_HEUN, sync = c->coupling == LBCAD_SYNC;
     if (c->path == LBCAD_PATH_FUSED && c->sync_split()) {
       e = launch_fused_lb(c, par);
-      if (e == cudaSuccess)
+      const int ni = (int)c->inst.size();
+      if (e == cudaSuccess && heun)
         e = (c->prec == LBCAD_FP64)
-                ? Launch<double, false>::op_sync((const InstDesc<double>*)c->desc[par], (int)c->inst.size(),
-                                                 c->total_blocks, kStepBlock, c->stream)
-                : Launch<float, true>::op_sync((const InstDesc<float>*)c->desc[par], (int)c->inst.size(),
-                                               c->total_blocks, kStepBlock, c->stream);
+                ? Launch<double, false>::op_heun((const InstDesc<double>*)c->desc[par], ni, c->total_blocks,
+                                                 kStepBlock, sync, c->stream)
+                : Launch<float, true>::op_heun((const InstDesc<float>*)c->desc[par], ni, c->total_blocks, kStepBlock,
+                                               sync, c->stream);
+      else if (e == cudaSuccess)
+        e = (c->prec == LBCAD_FP64)
+                ? Launch<double, false>::op_sync((const InstDesc<double>*)c->desc[par], ni, c->total_blocks,
+                                                 kStepBlock, c->stream)
+                : Launch<float, true>::op_sync((const InstDesc<float>*)c->desc[par], ni, c->total_blocks, kStepBlock,
+                                               c->stream);
     } else if (c->path == LBCAD_PATH_FUSED) {
       e = launch_fused(c, par);
     } else if (c->path == LBCAD_PATH_STAGED) {
@@ -651,9 +658,9 @@ int lbcad_set_path(lbcad_ctx* c, int32_t path) {
   if (path != LBCAD_PATH_FUSED && path != LBCAD_PATH_TWO_KERNEL && path != LBCAD_PATH_STAGED)
     return fail(c, LBCAD_E_INVALID_ARG, "unknown path");
   if (path != LBCAD_PATH_STAGED && c->staged_only())
-    return fail(c, LBCAD_E_UNSUPPORTED, "Heun or radius-2 contexts run on the staged path only");
-  if (path == LBCAD_PATH_TWO_KERNEL && (!c->default_lb() || c->coupling != LBCAD_LAGGED))
-    return fail(c, LBCAD_E_UNSUPPORTED, "the two-kernel path covers lagged D3Q19 with the body force only");
+    return fail(c, LBCAD_E_UNSUPPORTED, "radius-2 contexts run on the staged path only");
+  if (path == LBCAD_PATH_TWO_KERNEL && (!c->default_lb() || c->sync_split()))
+    return fail(c, LBCAD_E_UNSUPPORTED, "the two-kernel path covers the Euler, lagged step of D3Q19 with the body force");
   DeviceGuard dg(c->device);
   if (path != LBCAD_PATH_FUSED) {
     int r = ensure_scratch(c);
@@ -671,7 +678,7 @@ int lbcad_set_path(lbcad_ctx* c, int32_t path) {
 int lbcad_autotune(lbcad_ctx* c, int32_t reps, int32_t* chosen, float* ms_per_cfg, int32_t ncfg) {
   if (!c || reps < 1) return LBCAD_E_INVALID_ARG;
   if (c->staged_only()) return fail(c, LBCAD_E_UNSUPPORTED, "tile shapes belong to the fused path (Euler, lagged)");
-  if (c->sync_split()) return fail(c, LBCAD_E_UNSUPPORTED, "sync coupling runs on one fixed fused tile shape");
+  if (c->sync_split()) return fail(c, LBCAD_E_UNSUPPORTED, "sync coupling and Heun run on one fixed fused tile shape");
   DeviceGuard dg(c->device);
   const int n = (c->prec == LBCAD_FP64) ? LaunchFused<double, false>::num_configs()
                                         : LaunchFused<float, true>::num_configs();
@@ -721,7 +728,7 @@ int lbcad_autotune(lbcad_ctx* c, int32_t reps, int32_t* chosen, float* ms_per_cf
 int lbcad_set_tiles(lbcad_ctx* c, int32_t cfg) {
   if (!c) return LBCAD_E_INVALID_ARG;
   if (c->staged_only()) return fail(c, LBCAD_E_UNSUPPORTED, "tile shapes belong to the fused path (Euler, lagged)");
-  if (c->sync_split()) return fail(c, LBCAD_E_UNSUPPORTED, "sync coupling runs on one fixed fused tile shape");
+  if (c->sync_split()) return fail(c, LBCAD_E_UNSUPPORTED, "sync coupling and Heun run on one fixed fused tile shape");
   DeviceGuard dg(c->device);
   const int n = (c->prec == LBCAD_FP64) ? LaunchFused<double, false>::num_configs()
                                         : LaunchFused<float, true>::num_configs();
@@ -1075,7 +1082,7 @@ int lbcad_adjoint(lbcad_ctx* c, int64_t nsteps, int32_t ckpt_every, double* dJ_d
                   double* dJ_dQ0, double* J) {
   if (!c) return LBCAD_E_INVALID_ARG;
   if (c->inst.size() != 1) return fail(c, LBCAD_E_UNSUPPORTED, "the adjoint runs on single-instance contexts");
-  if (c->staged_only() || c->coupling != LBCAD_LAGGED || !c->default_lb())
+  if (c->staged_only() || c->sync_split() || !c->default_lb())
     return fail(c, LBCAD_E_UNSUPPORTED, "the adjoint differentiates the Euler, lagged step of D3Q19 with the body force");
   if (nsteps < 1 || ckpt_every < 1) return fail(c, LBCAD_E_INVALID_ARG, "need nsteps >= 1 and ckpt_every >= 1");
   DeviceGuard dg(c->device);

@@ -1,5 +1,5 @@
-"""The staged path: Heun predictor-corrector and sync coupling (Sec. 3) on the GPU against
-the FP64 oracle, through the C ABI.
+"""Heun predictor-corrector and sync coupling (Sec. 3) on the GPU against the FP64 oracle,
+through the C ABI, on the fused split and the staged path.
 
 Tolerances as for the default step: FP64 within 1e-12 max abs per field after 10 steps,
 FP32 within 1e-5 relative L2 per field after 100 steps.
@@ -35,8 +35,8 @@ def built():
     ((4, 5, 6), dict(R=2.0, p0=6.0)),
 ])
 def test_fp64_parity_10_steps(shape, kw, var, path):
-    """Heun runs on the staged path; Euler with sync coupling by default on the fused path
-    (the LB half in the fused kernel, then the order-parameter kernel), or staged."""
+    """By default on the fused path (the LB half in the fused kernel, then the
+    order-parameter kernels), or staged."""
     sim = L.Simulation([shape], [_lib_params(shape, L.FP64, **kw, **var)], seed=2)
     if path == "staged":
         sim.set_path(L.lbcad.PATH_STAGED)
@@ -86,14 +86,16 @@ def test_staged_euler_lagged_agrees_with_fused(prec):
             assert _rel_l2(x, y) <= 1e-6, k
 
 
+@pytest.mark.parametrize("var", VARIANTS, ids=["heun-lagged", "euler-sync", "heun-sync"])
 @pytest.mark.parametrize("prec", [L.FP32, L.FP64])
-def test_sync_split_agrees_with_the_staged_path(prec):
-    """Euler with sync coupling: the fused split (default) and the staged path evaluate the
-    same per-site functions in a different kernel split; agreement to rounding, also for a
-    batch of uneven instances replayed from a graph."""
+def test_split_agrees_with_the_staged_path(prec, var):
+    """Heun or sync coupling: the fused split (the LB half in the fused kernel, then the
+    order-parameter kernels; the default) and the staged path evaluate the same per-site
+    functions in a different kernel split; agreement to rounding, also for a batch of uneven
+    instances replayed from a graph."""
     shapes = [(40, 18, 12), (16, 12, 10)]
     kws = [dict(R=5.0, p0=8.0, zeta=0.01), dict(R=3.0, p0=8.0, zeta=0.004)]
-    prm = [_lib_params(s_, prec, **k, coupling=L.SYNC) for s_, k in zip(shapes, kws)]
+    prm = [_lib_params(s_, prec, **k, **var) for s_, k in zip(shapes, kws)]
     a = L.Simulation(shapes, prm, seed=3)
     b = L.Simulation(shapes, prm, seed=3)
     b.set_path(L.lbcad.PATH_STAGED)
@@ -108,17 +110,6 @@ def test_sync_split_agrees_with_the_staged_path(prec):
             else:
                 x, y = (_shifted(fa[k]), _shifted(fb[k])) if k == "g" else (fa[k], fb[k])
                 assert _rel_l2(x, y) <= 1e-6, (i, k)
-
-
-def test_sync_split_refuses_tile_choices_and_the_adjoint():
-    shape = (8, 8, 8)
-    sim = L.Simulation([shape], [_lib_params(shape, L.FP32, coupling=L.SYNC)], seed=1)
-    for call in (lambda: sim.set_tiles(0), lambda: sim.autotune(1), lambda: sim.adjoint(2, 1),
-                 lambda: sim.set_path(L.lbcad.PATH_TWO_KERNEL)):
-        with pytest.raises(L.LbcadError):
-            call()
-    sim.step(2)
-    assert np.isfinite(sim.observables(0)).all()
 
 
 def test_batch_heun_sync_instances_match_oracle():
@@ -146,13 +137,20 @@ def test_graph_replay_of_the_staged_step_is_bitwise_identical():
 
 
 def test_options_of_the_euler_lagged_step_are_refused():
+    """Heun and sync contexts run the LB half on one fixed fused tile shape: tile choices, the
+    two-kernel path and the adjoint are refused; the fused and staged paths both run."""
     shape = (8, 8, 8)
-    sim = L.Simulation([shape], [_lib_params(shape, L.FP32, integrator=L.HEUN)], seed=1)
-    for call in (lambda: sim.set_path(L.lbcad.PATH_FUSED), lambda: sim.set_path(L.lbcad.PATH_TWO_KERNEL),
-                 lambda: sim.set_tiles(0), lambda: sim.autotune(1), lambda: sim.adjoint(2, 1)):
-        with pytest.raises(L.LbcadError):
-            call()
-    sim.set_path(L.lbcad.PATH_STAGED)
-    sim.step(1)
+    for var in VARIANTS:
+        sim = L.Simulation([shape], [_lib_params(shape, L.FP32, **var)], seed=1)
+        for call in (lambda: sim.set_path(L.lbcad.PATH_TWO_KERNEL), lambda: sim.set_tiles(0),
+                     lambda: sim.autotune(1), lambda: sim.adjoint(2, 1)):
+            with pytest.raises(L.LbcadError):
+                call()
+        sim.step(1)
+        sim.set_path(L.lbcad.PATH_STAGED)
+        sim.step(1)
+        sim.set_path(L.lbcad.PATH_FUSED)
+        sim.step(1)
+        assert np.isfinite(sim.observables(0)).all()
     with pytest.raises(L.LbcadError):
         L.Simulation([shape, shape], [_lib_params(shape, L.FP32), _lib_params(shape, L.FP32, coupling=L.SYNC)])
