@@ -47,8 +47,10 @@ CASES = [("fp64", L.FP64, 0), ("fp32-32x8", L.FP32, 0), ("fp32-pipelined", L.FP3
 
 
 @pytest.mark.parametrize("name,prec,tiles", CASES, ids=[c[0] for c in CASES])
-@pytest.mark.parametrize("shape", [(32, 32, 32), (21, 13, 10), (40, 18, 12)])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (21, 13, 10), (40, 18, 12), (4, 5, 6), (8, 4, 4)])
 def test_fused_sums_match_the_separate_pass(shape, name, prec, tiles):
+    """Includes the smallest boxes (edges of 4): many short column segments per block, so
+    many a6 slots per instance, and tiles far larger than the box."""
     sim = L.Simulation([shape], [_lib_params(shape, prec, R=5.0, p0=8.0, zeta=0.01)], seed=3)
     sim.set_tiles(tiles)
     sim.step(7)
