@@ -500,6 +500,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
           dq[qidx<QP>(5, k)] = ld(pin + gs);
         }
       }
+      if constexpr (MODE == kFusedLbOnly) return;  // the LB half reads no previous u
       T* du = sU + uslot(pu) * G::USLOT;
       const long long gzu = (long long)wrap_plane(pu, nz) * plane;
 #pragma unroll
@@ -528,7 +529,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
     load_q_all(zb - 2);
     load_q_all(zb - 1);
     load_q_all(zb);
-    load_u_all(zb - 1);
+    if constexpr (MODE != kFusedLbOnly) load_u_all(zb - 1);  // the LB half reads no previous u
     T Hc[5] = {T(0), T(0), T(0), T(0), T(0)};
     for (int z = zb - 2; z < ze; ++z) {
       __syncthreads();  // Q(z .. z+2) and u(z-1 .. z+1) resident; the previous output phase is done
@@ -763,7 +764,7 @@ __global__ void __launch_bounds__(512, 1)
 
     for (int k = zb - 2; k <= ze; ++k) {
       issue_q(k + 3);
-      issue_u(k + 1);
+      if constexpr (MODE != kFusedLbOnly) issue_u(k + 1);  // the LB half reads no previous u
       if (tid < G::NS) {
         // sigma, mu (and H on interior sites) of plane k+1
 #pragma unroll 1
