@@ -849,17 +849,17 @@ __global__ void __launch_bounds__(kStepBlock) k_fields(const InstDesc<T>* __rest
   else gather_fields<T>(acc, q0, p0, dq, lapq, dp, lapp, hp);
   T H[5], sig[9], mu;
   local_fields<T>(I.c, q0, p0, dq, lapq, dp, lapp, hp, H, mu, sig);
-  if (PRED) {
+  if constexpr (PRED) {
 #pragma unroll
     for (int k = 0; k < 5; ++k) I.sig[k * N + s] = H[k];
     I.sig[5 * N + s] = mu;
-    return;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) I.H[k * N + s] = H[k];
+    I.mu[s] = mu;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) I.sig[k * N + s] = sig[k];
   }
-#pragma unroll
-  for (int k = 0; k < 5; ++k) I.H[k * N + s] = H[k];
-  I.mu[s] = mu;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) I.sig[k * N + s] = sig[k];
 }
 
 // ---------------------------------------------------------------- staged path

@@ -93,6 +93,8 @@ def test_null_arguments_of_the_exchange_and_option_calls(lib):
     assert lib.lbcad_set_path(None, 0) == L.LBCAD_E_INVALID_ARG
     assert lib.lbcad_set_tiles(None, 0) == L.LBCAD_E_INVALID_ARG
     assert lib.lbcad_autotune(None, 1, None, None, 0) == L.LBCAD_E_INVALID_ARG
+    assert lib.lbcad_set_observe(None, 1) == L.LBCAD_E_INVALID_ARG
+    assert lib.lbcad_set_graph(None, 2) == L.LBCAD_E_INVALID_ARG
 
 
 @pytest.mark.parametrize("code,q", [(L.D3Q19, 19), (L.D3Q15, 15)])
