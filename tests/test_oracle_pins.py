@@ -830,3 +830,39 @@ def test_forward_mode_tangent_matches_central_differences():
     # tangent of the values: unchanged arithmetic for the state itself
     s2 = O.State(shape, O.default_params(shape, **kw), seed=3).step(2)
     np.testing.assert_array_equal(s.psi, s2.psi)
+
+
+# ---------------------------------------------------------------- a6: the conserved and centroid sums
+
+@pytest.mark.parametrize("q", [19, 15])
+def test_observables_closed_forms(q):
+    """The oracle's a6 sums against closed forms.  Populations at equilibrium with uniform
+    density rho and velocity v: mass N rho and momentum N rho v, from the lattice moments
+    (sum w = 1, sum w c = 0, sum w c c = I/3, sum w c c c = 0), not from the sum itself.
+    psi = A cos(2 pi (r_a - r0)/L_a) + B along one axis a at a time: sum psi = B N, sum phi_c =
+    (1 + B) N / 2, the phi_c moments along a are (A/2)(L_a/2)(N/L_a) (cos, sin)(2 pi r0/L_a),
+    and along the other two axes they vanish (a constant summed against a full period)."""
+    c, w = O.lattice(q)
+    shp = (8, 6, 5)
+    nx, ny, nz = shp
+    N = nx * ny * nz
+    rho, v = 1.2, np.array([0.01, -0.02, 0.005])
+    f = _feq(np.full((nz, ny, nx), rho), v.reshape(3, 1, 1, 1) * np.ones((3, nz, ny, nx)), c, w)
+    A, B, r0 = 0.6, -0.3, 1.7
+    for a, La in enumerate(shp):
+        r = np.arange(La, dtype=float)
+        prof = A * np.cos(2 * np.pi * (r - r0) / La) + B
+        shape_a = [1, 1, 1]
+        shape_a[2 - a] = La  # arrays are [z][y][x]
+        psi = np.ascontiguousarray(np.broadcast_to(prof.reshape(shape_a), (nz, ny, nx)))
+        o = O.observables(np.ascontiguousarray(f), psi)
+        assert abs(o[0] - N * rho) <= 1e-12 * N
+        np.testing.assert_allclose(o[2:5], N * rho * v, rtol=0, atol=1e-12 * N)
+        assert abs(o[1] - B * N) <= 1e-12 * N
+        assert abs(o[11] - 0.5 * (1 + B) * N) <= 1e-12 * N
+        amp = 0.5 * A * 0.5 * La * (N / La)
+        for b in range(3):
+            want_c = amp * np.cos(2 * np.pi * r0 / La) if b == a else 0.0
+            want_s = amp * np.sin(2 * np.pi * r0 / La) if b == a else 0.0
+            assert abs(o[5 + b] - want_c) <= 1e-11 * N, (a, b)
+            assert abs(o[8 + b] - want_s) <= 1e-11 * N, (a, b)
