@@ -513,6 +513,9 @@ int prepare_fused(lbcad_ctx* c, int cfg_index) {
     c->obs_map_cap = map.size();
   }
   CK(c, cudaMemcpyAsync(c->obs_map, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  // the kernels leave the per-instance counters at zero; reset them here as well, so that a
+  // launch that failed part-way cannot shift the next sums
+  CK(c, cudaMemsetAsync(c->obs_cnt, 0, (size_t)ninst * sizeof(unsigned), c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   c->obs_maxseg = maxseg;
   c->obs_valid = false;
