@@ -403,6 +403,24 @@ def test_onsager_reciprocity_reactive_stress():
         np.testing.assert_allclose(sR[:, :, z, y, x] - sR[:, :, z, y, x].T, 2 * (Qs @ Hs - Hs @ Qs), atol=1e-14)
 
 
+def test_corotation_closed_forms():
+    """The co-rotation term of Eq. 2 in two limits that fix it apart from the stress: a pure
+    rotation of the flow (W antisymmetric, so D = 0 and tr(QW) = 0) rotates Q, S = Omega Q -
+    Q Omega; a pure strain acting on the isotropic phase (Q = 0) gives S = 2 xi D / 3."""
+    rng = np.random.default_rng(11)
+    for xi in (0.7, -0.4):
+        for _ in range(10):
+            A = rng.standard_normal((3, 3))
+            Q = 0.5 * (A + A.T)
+            Q -= np.eye(3) * np.trace(Q) / 3
+            B = rng.standard_normal((3, 3))
+            Om = 0.5 * (B - B.T)
+            np.testing.assert_allclose(O.corotation(Om, Q, xi), Om @ Q - Q @ Om, atol=1e-14)
+            D = 0.5 * (B + B.T)
+            D -= np.eye(3) * np.trace(D) / 3
+            np.testing.assert_allclose(O.corotation(D, np.zeros((3, 3)), xi), 2 * xi * D / 3, atol=1e-14)
+
+
 def test_active_stress_eq4():
     """Eq. 4: sigma_act = -zeta Q inside the droplet (phi_c = 1), zero outside."""
     n = 4
