@@ -472,6 +472,29 @@ def test_upwind_exact_for_linear_profiles():
         assert abs(rp.sum()) < 1e-14
 
 
+def test_relaxation_and_diffusion_terms():
+    """At rest (u = 0) the right-hand side of Eq. 2 is Gamma_Q H and that of Eq. 1 is M lap mu.
+    For mu = cos(k x) the isotropic D3Q19 Laplacian 6 sum_i w_i (mu(x + c_i) - mu(x)) has the
+    exact symbol 6 (2/18 + 8/36)(cos k - 1) = 2 (cos k - 1): the two faces along x and the eight
+    edges with c_x != 0; every other neighbour sees the same mu."""
+    n = 8
+    p = O.default_params((n, n, n), gammaQ=0.3, M=0.1)
+    rng = np.random.default_rng(5)
+    q5 = 0.1 * rng.standard_normal((5, n, n, n))
+    psi = 0.2 * rng.standard_normal((n, n, n))
+    H = rng.standard_normal((5, n, n, n))
+    kx = 2 * np.pi * 3 / n
+    for axis in range(3):
+        r = np.arange(n, dtype=float)
+        shape_a = [1, 1, 1]
+        shape_a[2 - axis] = n
+        mu = np.ascontiguousarray(np.broadcast_to(np.cos(kx * r).reshape(shape_a), (n, n, n)))
+        rq, rp, W = O.op_rhs(q5, psi, np.zeros((3, n, n, n)), H, mu, p)
+        np.testing.assert_allclose(rq, 0.3 * H, atol=1e-15)
+        np.testing.assert_allclose(rp, 0.1 * 2 * (np.cos(kx) - 1) * mu, atol=1e-14)
+        assert np.abs(W).max() == 0.0
+
+
 # ---------------------------------------------------------------- full step: conservation and symmetry
 
 def _droplet_state(n=16, R=5.0, **kw):
