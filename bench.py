@@ -48,6 +48,59 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+# the sources that define the step kernels: an ncu figure is current only while these are
+# unchanged since the capture (the profile records their fingerprint)
+STEP_SOURCES = ["lbcad_fused.cuh", "lbcad_kernels.cuh", "lbcad_internal.h", "lbcad_f32.cu"]
+
+
+def kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in STEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_2011_00287_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_is_current(name="lbcad_step_fp32_128cube.md"):
+    """True when the committed ncu summary was taken of the kernels as they are now."""
+    p = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(p):
+        return False
+    for line in open(p):
+        if line.startswith("kernel_source_sha:"):
+            return line.split(":", 1)[1].strip().split()[0] == kernel_source_sha()
+    return False
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def measured_alu_peaks(device=0):
+    """FP64 and FP32 dense FMA throughput of this GPU (TFLOP/s), measured by the FMA-chain
+    probe (csrc/peaks.cu); None where the probe fails."""
+    import ctypes
+    from paper_2011_00287_gb300 import build as B
+    try:
+        lib = ctypes.CDLL(B.PEAKS_LIB)
+    except OSError:
+        return None, None
+    out = []
+    for fn, iters in ((lib.peak_fp64_tflops, 256), (lib.peak_fp32_tflops, 8192)):
+        fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        v = ctypes.c_double()
+        out.append(v.value if fn(device, iters, ctypes.byref(v)) == 0 else None)
+    return out[0], out[1]
+
+
 def committed_profile_value(key, name="lbcad_step_fp32_128cube.md"):
     """A figure ('key: value ...') from a committed ncu summary of the step."""
     p = os.path.join(ROOT, "profiles", name)
@@ -157,12 +210,13 @@ def time_steps(sim, torch, K):
     return e0.elapsed_time(e1) / K
 
 
-def cpu_oracle_rate(n, budget_s=12.0, max_steps=None):
-    """Oracle site updates per second on a bounded sample of the workload (1 thread)."""
+def cpu_oracle_rate(n, budget_s=12.0, max_steps=None, omp=False):
+    """Oracle site updates per second on a bounded sample of the workload (1 thread, or all
+    host cores with the oracle's OpenMP build)."""
     from oracle import oracle as O
-    O.build()
+    O.build(omp=omp)
     p = O.default_params((n, n, n), R=n / 4.0, p0=n / 4.0, zeta=0.005)
-    s = O.State((n, n, n), p, seed=1)
+    s = O.State((n, n, n), p, seed=1, omp=omp)
     steps, t0 = 0, time.perf_counter()
     while True:
         s.step(1)
@@ -175,24 +229,26 @@ def cpu_oracle_rate(n, budget_s=12.0, max_steps=None):
 
 
 def run_reference(args):
-    """--impl reference: the FP64 CPU oracle, as it stands, on this host's cores."""
+    """--impl reference: the FP64 CPU oracle, as it stands, on all of this host's cores (its
+    OpenMP build: the same per-site arithmetic, stage loops split over z)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import numpy as np  # noqa: F401
     from oracle import oracle as O
-    O.build()
+    O.build(omp=True)
+    threads = O.num_threads(True)
     K, W = args.steps, args.warmup
     # each step is one oracle step on the largest droplet box (same workload family,
     # R = n/4, pitch n/4) whose K + W steps fit in about two minutes
-    rate_probe, _, _ = cpu_oracle_rate(32, budget_s=1.0)
+    rate_probe, _, _ = cpu_oracle_rate(32, budget_s=1.0, omp=True)
     n = 32
     for cand in (128, 96, 64, 48, 32):
         if cand ** 3 * (K + W) / rate_probe <= 120.0:
             n = cand
             break
     p = O.default_params((n, n, n), R=n / 4.0, p0=n / 4.0, zeta=0.005)
-    s = O.State((n, n, n), p, seed=1)
+    s = O.State((n, n, n), p, seed=1, omp=True)
     s.step(W)
     t0 = time.perf_counter()
     for _ in range(K):  # each step with its a6 sums, as the GPU step forms them
@@ -200,43 +256,55 @@ def run_reference(args):
         s.observables()
     el = time.perf_counter() - t0
     mlups = n ** 3 * K / el / 1e6
-    sample = ("oracle FP64 single-thread, %d^3 droplet (R=%d, pitch %d), %d timed steps (each with its "
-              "conserved and centroid sums) after %d warm-up") % (n, n // 4, n // 4, K, W)
+    sample = ("oracle FP64 on %d threads (OpenMP over z in each stage loop), %d^3 droplet (R=%d, pitch %d), %d "
+              "timed steps (each with its conserved and centroid sums) after %d warm-up") % (
+                  threads, n, n // 4, n // 4, K, W)
     line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": 1, "steps": K,
             "warmup": W, "ms_per_step": el / K * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "active cholesteric droplet %d^3 (CPU sample of 128^3, R=32, pitch 32)" % n,
                        "box": [n, n, n]},
-            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle", "sample": sample,
+                             "nproc": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-def run_batch(args):
-    """64 independent droplets (edges from {48, 64, 80, 96}, seed 7) advanced together by
-    one persistent launch per step, replayed from a CUDA graph; aggregate MLUPS."""
-    import torch
-    import paper_2011_00287_gb300 as L
-    from paper_2011_00287_gb300 import build as B
+def batch_leg(torch, L, steps=100, warmup=3):
+    """64 independent droplets (edges from {48, 64, 80, 96}, seed 7) advanced together by one
+    persistent launch per step, replayed from a CUDA graph: aggregate MLUPS."""
     from paper_2011_00287_gb300 import workloads as WL
-    B.build()
     work = WL.batch_uneven(seed=7, count=64)
     prms = [L.default_params(w["grid"], R=w["R"], p0=w["p0"], zeta=w["zeta"], precision=L.FP32) for w in work]
     sim = L.Simulation([w["grid"] for w in work], prms, seed=7)
     cfg, tms = sim.autotune(3)
     sim.set_graph(50)
-    sim.step(max(args.warmup, 3))
-    K = max(50, (args.steps // 50) * 50)
+    sim.step(max(warmup, 3))
+    K = max(50, (steps // 50) * 50)
     with ClockSampler(0) as clk:
         ms = time_steps(sim, torch, K)
     sites = sim.sites()
-    print(json.dumps({"metric": METRIC + " (batched 64 uneven droplets)", "value": sites / (ms * 1e-3) / 1e6,
-                      "unit": "MLUPS", "n_gpus": 1, "steps": K, "ms_per_step": ms, "sites": sites,
-                      "dtype": "f32", "data": "synthetic", "tiles": {"chosen": TILE_NAMES[cfg], "ms_per_cfg": dict(zip(TILE_NAMES, tms))},
-                      "config": {"workload": "64 droplets, edges from {48,64,80,96}, seed 7"},
-                      "clocks": clk.summary()}))
+    out = {"mlups": sites / (ms * 1e-3) / 1e6, "ms_per_step": ms, "steps": K, "sites": sites,
+           "tiles": {"chosen": TILE_NAMES[cfg], "ms_per_cfg": dict(zip(TILE_NAMES, tms))},
+           "workload": "64 droplets, edges from {48,64,80,96}, R = edge/4, zeta in [0.001, 0.01], pitch in "
+                       "[12, 40], seed 7, FP32, one launch per step replayed from a CUDA graph, a6 sums fused",
+           "clocks": clk.summary()}
     sim.close()
+    return out
+
+
+def run_batch(args):
+    """--workload batch64: the batched leg alone, as its own JSON line."""
+    import torch
+    import paper_2011_00287_gb300 as L
+    from paper_2011_00287_gb300 import build as B
+    B.build()
+    b = batch_leg(torch, L, args.steps, args.warmup)
+    print(json.dumps({"metric": METRIC + " (batched 64 uneven droplets)", "value": b["mlups"], "unit": "MLUPS",
+                      "n_gpus": 1, "steps": b["steps"], "ms_per_step": b["ms_per_step"], "sites": b["sites"],
+                      "dtype": "f32", "data": "synthetic", "tiles": b["tiles"],
+                      "config": {"workload": b["workload"]}, "clocks": b["clocks"]}))
     return 0
 
 
@@ -257,6 +325,9 @@ def main():
     ap.add_argument("--no-staged", action="store_true",
                     help="skip the sync / Heun, LB-variant and bulk legs")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg (64^3, 500 steps)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-droplet leg")
+    ap.add_argument("--min-timed-s", type=float, default=1.0,
+                    help="repeat the K-step timed region until this much device time has passed")
     ap.add_argument("--workload", default="droplet", choices=["droplet", "batch64"],
                     help="droplet: the 128^3 benchmark line; batch64: 64 uneven droplets in one launch")
     args = ap.parse_args()
@@ -297,9 +368,20 @@ def main():
         dist.barrier()
     # every timed step is the whole hot path: stencils, fields, stress and force, the order-
     # parameter update, the LB collision and streaming, and the FP64 conserved and centroid
-    # sums of the new state (fused into the same kernel; the library default)
+    # sums of the new state (fused into the same kernel; the library default).  The region of
+    # exactly K steps is timed repeatedly (the same count on every rank) until about a second of
+    # device time has passed, so that the clock sampler sees it; the step time is the median.
+    ms_probe = time_steps(sim, torch, K)
+    reps = max(1, int(math.ceil(args.min_timed_s / max(K * ms_probe * 1e-3, 1e-9))))
+    if dist:
+        reps = int(max_over_ranks(reps, dist))
+    region_ms = []
     with ClockSampler(local) as clk:
-        ms = time_steps(sim, torch, K)
+        for _ in range(reps):
+            if dist:
+                dist.barrier()
+            region_ms.append(time_steps(sim, torch, K))
+    ms = statistics.median(region_ms)
     if dist:
         ms = max_over_ranks(ms, dist)
     obs = sim.observables(0)
@@ -322,13 +404,16 @@ def main():
         s64.step(3)
         ms64 = time_steps(s64, torch, args.fp64_steps)
         fp64 = {"mlups": N / (ms64 * 1e-3) / 1e6, "ms_per_step": ms64, "steps": args.fp64_steps}
-        # bound by the FP64 pipe: flops per site from the committed ncu counters, peak the
-        # nominal FP64 rate of the part (1.25 TFLOP/s)
+        # bound by the FP64 pipe: flops per site from the committed ncu counters, peak the FP64
+        # FMA throughput measured on this GPU by the FMA-chain probe
         fl = committed_profile_value("fp64_flops_per_site", "lbcad_step_fp64_128cube.md")
-        if fl:
+        p64, p32 = measured_alu_peaks(local)
+        fp64["measured_peak_tflops"] = {"fp64": p64, "fp32": p32,
+                                        "how": "FMA-chain probe (csrc/peaks.cu), best of 5 launches on every SM"}
+        if fl and p64:
             ach = fl * N / (ms64 * 1e-3) / 1e12
-            fp64["roofline"] = {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
-                                "peak_kind": "nominal FP64 rate", "flops_per_site": fl,
+            fp64["roofline"] = {"bound": "alu", "achieved": ach, "peak": p64, "unit": "TFLOP/s", "frac": ach / p64,
+                                "peak_kind": "measured DFMA throughput of this GPU", "flops_per_site": fl,
                                 "fp64_pipe_active_pct": committed_profile_value(
                                     "fp64_pipe_active_pct", "lbcad_step_fp64_128cube.md")}
         s64.close()
@@ -411,6 +496,11 @@ def main():
                    "seconds": t_adj, "forward_seconds": t_fwd, "ratio_to_forward": t_adj / t_fwd,
                    "site_steps_per_s": na ** 3 * 500 / t_adj, "dJ_dzeta": dz, "finite": bool(math.isfinite(dz))}
 
+    # batched sweep: 64 uneven droplets in one launch per step (CUDA graph)
+    batch = None
+    if not args.no_batch and world == 1:
+        batch = batch_leg(torch, L)
+
     # end to end through the public API with host buffers: every step sets the whole state
     # from pinned host memory (lbcad_set_state, the storage precision), advances one step and
     # reads the whole state back (lbcad_get_state)
@@ -436,7 +526,8 @@ def main():
 
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_SITE["fp32"] * N / (ms * 1e-3) / 1e9
-    traffic_site = committed_traffic()
+    current = profile_is_current()
+    traffic_site = committed_traffic() if current else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (traffic_site * N) if traffic_site else None,
                 "kernel": "k_step_pipe (one launch = one whole hybrid step, a6 sums included)",
@@ -444,12 +535,13 @@ def main():
                 "peak_kind": peak_kind,
                 # the design floor also moves u in and out (224 B per site)
                 "design_bytes_per_site": 224, "design_frac": 224 * N / (ms * 1e-3) / 1e9 / peak,
-                "ncu_dram_throughput_pct": committed_profile_value("dram_throughput_pct"),
-                "ncu_fma_pipe_active_pct": committed_profile_value("fma_pipe_active_pct")}
+                "ncu_dram_throughput_pct": committed_profile_value("dram_throughput_pct") if current else None,
+                "ncu_fma_pipe_active_pct": committed_profile_value("fma_pipe_active_pct") if current else None,
+                "ncu_capture_current": current}
 
     # the bound the step actually meets: warp-instruction issue (one per cycle per SM
     # sub-partition, 4 per SM, 152 SMs) at the SM clock sampled during the timed region
-    ipsite = committed_profile_value("warp_instructions_per_site")
+    ipsite = committed_profile_value("warp_instructions_per_site") if current else None
     csum = clk.summary()
     roofline_issue = None
     if ipsite and csum.get("sm_mhz"):
@@ -461,10 +553,17 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        rate, steps, el = cpu_oracle_rate(n, budget_s=12.0)
-        cpu = {"value": rate / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": "FP64 oracle, single thread, %d step(s) of the same %d^3 droplet workload (%.1f s)" % (
-                   steps, n, el)}
+        from oracle import oracle as O
+        threads = O.num_threads(True)
+        rate_n, steps_n, el_n = cpu_oracle_rate(n, budget_s=10.0, omp=True)
+        rate, steps, el = cpu_oracle_rate(n, budget_s=10.0)
+        cpu = {"value": rate_n / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+               "sample": "FP64 oracle on %d threads (OpenMP over z in each stage loop), %d step(s) of the same %d^3 "
+                         "droplet workload, each with its a6 sums (%.1f s)" % (threads, steps_n, n, el_n),
+               "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+               "single_thread": {"value": rate / 1e6, "unit": "MLUPS", "cores": 1,
+                                 "sample": "FP64 oracle, single thread, %d step(s) of the same workload (%.1f s)" % (
+                                     steps, el)}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": W,
@@ -477,7 +576,9 @@ def main():
                            "a6": "FP64 mass, psi, momentum and centroid sums of every step, fused"},
                 "roofline": roofline, "roofline_issue": roofline_issue, "cpu_baseline": cpu, "e2e": e2e,
                 "tiles": {"chosen": TILE_NAMES[tile_cfg], "ms_per_cfg": dict(zip(TILE_NAMES, tile_ms))},
-                "gpu_launches": K, "clocks": csum, "step_without_sums": without_sums, "fp64_gpu": fp64, "integrators_fp32": staged, "lb_variants_fp32": variants, "bulk_fp32": bulk, "adjoint_fp32": adjoint,
+                "timing": {"regions": len(region_ms), "steps_per_region": K, "median_ms_per_step": ms,
+                           "min_ms_per_step": min(region_ms), "max_ms_per_step": max(region_ms)},
+                "gpu_launches": K, "clocks": csum, "batch64": batch, "step_without_sums": without_sums, "fp64_gpu": fp64, "integrators_fp32": staged, "lb_variants_fp32": variants, "bulk_fp32": bulk, "adjoint_fp32": adjoint,
                 "speedup_fp32_vs_fp64": (value / world / fp64["mlups"]) if fp64 else None,
                 "observables_finite": finite}
         print(json.dumps(line))

@@ -207,7 +207,11 @@ int lbcad_set_tiles(lbcad_ctx* c, int32_t cfg);
  * reduction pass over the state.  Either way the state is the same.  Drops a captured graph. */
 int lbcad_set_observe(lbcad_ctx* c, int32_t on);
 
-/* Capture steps in a CUDA graph of `steps_per_graph` steps (0 disables; default 0). */
+/* Capture steps in a CUDA graph of `steps_per_graph` steps (0 disables; default 0).  The
+ * state buffers alternate by step parity and a replay must leave the parity unchanged, so
+ * steps_per_graph must be even: an odd or negative value returns LBCAD_E_INVALID_ARG and
+ * leaves the previous setting.  lbcad_step(n) replays the graph n / steps_per_graph times
+ * (after one plain step when the step count is odd) and launches the remaining steps plainly. */
 int lbcad_set_graph(lbcad_ctx* c, int32_t steps_per_graph);
 
 /* Copy the selected fields of instance `inst` to dst (FP64, layout above).  bytes must
@@ -295,15 +299,25 @@ int lbcad_sync(lbcad_ctx* c);
  * legacy default stream); integrator/coupling must be Euler/lagged; alloc callbacks are
  * ignored.  Returns after enqueueing the work on that stream.
  *
+ * Checks: the grid and params go through the same validation as lbcad_create (edges >= 4,
+ * every floating-point parameter finite, tau > 1/2, rho0 > 0, known option codes), then the
+ * size limit below, then the buffer pointers; all of these run on the host before any device
+ * is touched, and a failure returns LBCAD_E_INVALID_ARG (LBCAD_E_UNSUPPORTED for an option
+ * this call does not run) with a message in lbcad_last_error(NULL).
  * Limits: 15 * round_up_256(n * element size) bytes must fit in the scratch array, i.e.
- * up to 279,616 sites in FP32 (64^3 fits) and 139,808 in FP64; larger grids return
- * LBCAD_E_INVALID_ARG with a message in lbcad_last_error(NULL).
+ * up to 279,616 sites in FP32 (64^3 fits) and 139,808 in FP64; larger grids are rejected.
+ * Work: two launches on the stream, one that writes the launch descriptor (passed by value
+ * as a kernel argument, so no host memory is read after the call returns) into a second
+ * static array of 512 bytes, then the step kernels.
  * Sharing: every call on a device uses the same scratch and descriptor, so calls whose
  * work overlaps on the GPU (different streams, or host threads) race and corrupt each
  * other; serialise them.  The array keeps the last call's contents; nothing needs to
  * start at zero because each call writes every scratch value before reading it.
  * Set-up: the first call on a device looks up the device addresses of the static arrays
- * with cudaGetSymbolAddress; make that first call before any stream capture. */
+ * with cudaGetSymbolAddress and keeps them for that device; make that first call before any
+ * stream capture.  The addresses belong to the CUDA runtime's context of the device (its
+ * primary context): call this only while that context is current, not under a context the
+ * caller created with the driver API. */
 #define LBCAD_NOALLOC_SCRATCH_BYTES (16u << 20)
 int lbcad_step_noalloc(const lbcad_grid* grid, const lbcad_params* params, const void* g_in, const void* q_in,
                        const void* psi_in, const void* u_in, void* g_out, void* q_out, void* psi_out, void* u_out);

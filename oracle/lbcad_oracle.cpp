@@ -8,7 +8,11 @@
 // the stresses and the seeded initial state are written out again here.
 //
 // Everything is a plain loop in double precision, one stage after another, in the
-// order of the paper's model (Sec. 2, Eqs. 1-5) and scheme (Sec. 3, Eqs. 6-11):
+// order of the paper's model (Sec. 2, Eqs. 1-5) and scheme (Sec. 3, Eqs. 6-11).  Each
+// per-site stage loop carries an OpenMP parallel-for over z, which compiles away without
+// -fopenmp: every site's outputs are written by that site's iteration alone (streaming
+// writes each population to one destination), so the threaded build computes the same
+// numbers in the same order per site.  The stages:
 //   1. stencils on Q and psi                 (Sec. 3: finite differences for the order parameters)
 //   2. molecular field H = -dF/dQ            (Eq. 2, Eq. 5)
 //   3. chemical potential mu = dF/dphi       (Eq. 1, Eq. 5)
@@ -35,6 +39,9 @@
 #include <cstdint>
 #include <cstring>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 extern "C" {
 
@@ -512,6 +519,7 @@ template <typename R>
 void fields_all(const Box& B, const PR<R>& P, const R* q5, const R* psi, R* H5, R* mu,
                 R* sig9, R* sE9, R* sR9, R* sA9, R* fden) {
   long N = B.n();
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < B.nz; ++z)
     for (int y = 0; y < B.ny; ++y)
       for (int x = 0; x < B.nx; ++x) {
@@ -541,6 +549,7 @@ void fields_all(const Box& B, const PR<R>& P, const R* q5, const R* psi, R* H5, 
 template <typename R>
 void force_all(const Box& B, const R* sig9, R* F3, int stencil = 0) {
   long N = B.n();
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < B.nz; ++z)
     for (int y = 0; y < B.ny; ++y)
       for (int x = 0; x < B.nx; ++x) {
@@ -572,6 +581,7 @@ void lb_all(const Box& B, const PR<R>& P, const R* f, const R* F3, R* fnew, R* u
   long N = B.n();
   const LBSet L = lb_set(P.lattice);
   const R tau = P.tau;
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < B.nz; ++z)
     for (int y = 0; y < B.ny; ++y)
       for (int x = 0; x < B.nx; ++x) {
@@ -611,6 +621,7 @@ void lb_all_stress(const Box& B, const PR<R>& P, const R* f, const R* FA3, const
   long N = B.n();
   const LBSet L = lb_set(P.lattice);
   const R tau = P.tau;
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < B.nz; ++z)
     for (int y = 0; y < B.ny; ++y)
       for (int x = 0; x < B.nx; ++x) {
@@ -652,6 +663,7 @@ template <typename R>
 void op_rhs(const Box& B, const PR<R>& P, const R* q5, const R* psi, const R* uadv,
             const R* H5, const R* mu, R* rq5, R* rp) {
   long N = B.n();
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < B.nz; ++z)
     for (int y = 0; y < B.ny; ++y)
       for (int x = 0; x < B.nx; ++x) {
@@ -762,6 +774,15 @@ uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
 extern "C" {
 
 // D3Q19 table as used here (for index matching in tests).
+// Threads the stage loops use (1 in the single-thread build).
+int orc_num_threads() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 void orc_lattice(int* c57, double* w19) {
   for (int i = 0; i < NQ; ++i) {
     for (int a = 0; a < 3; ++a) c57[3 * i + a] = CV[i][a];

@@ -19,8 +19,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbcad_oracle.cpp")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liblbcad_oracle.so")
+# the same source with its per-stage OpenMP parallel-for over z switched on (all host cores)
+_LIB_OMP = os.path.join(_BUILD, "liblbcad_oracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 
 class orc_params(ctypes.Structure):
@@ -51,27 +53,30 @@ def default_params(n=(32, 32, 32), R=8.0, p0=16.0, **kw) -> orc_params:
     return p
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with g++ (no fast-math, no FP contraction)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle with g++ (no fast-math, no FP contraction); omp=True builds the
+    variant whose stage loops run on all host cores (same arithmetic per site)."""
+    out = _LIB_OMP if omp else _LIB
     with _lock:
-        if (not force and os.path.exists(_LIB)
-                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-            return _LIB
+        if (not force and os.path.exists(out)
+                and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+            return out
         os.makedirs(_BUILD, exist_ok=True)
-        tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC",
+        tmp = out + ".%d.tmp" % os.getpid()
+        extra = ["-fopenmp"] if omp else []
+        subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", *extra,
                                "-shared", _SRC, "-o", tmp])
-        os.replace(tmp, _LIB)
-        return _LIB
+        os.replace(tmp, out)
+        return out
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = ctypes.CDLL(build())
+def lib(omp: bool = False):
+    if omp not in _libs:
+        L = ctypes.CDLL(build(omp=omp))
         dp = ctypes.POINTER(ctypes.c_double)
         P = ctypes.POINTER(orc_params)
         i = ctypes.c_int
+        L.orc_num_threads.restype = ctypes.c_int
         L.orc_lattice.argtypes = [ctypes.POINTER(ctypes.c_int), dp]
         L.orc_lattice_q.argtypes = [i, ctypes.POINTER(ctypes.c_int), dp]
         L.orc_lb_stress.argtypes = [i, i, i, P, dp, dp, dp, dp, dp]
@@ -90,8 +95,13 @@ def lib():
         L.orc_lb.argtypes = [i, i, i, P, dp, dp, dp, dp]
         L.orc_observables.argtypes = [i, i, i, dp, dp, dp]
         L.orc_step_tangent.argtypes = [i, i, i, P, ctypes.c_double, ctypes.c_double] + [dp] * 8 + [ctypes.c_long]
-        _lib = L
-    return _lib
+        _libs[omp] = L
+    return _libs[omp]
+
+
+def num_threads(omp: bool = False) -> int:
+    """Threads the oracle's stage loops run on (1 for the single-thread build)."""
+    return int(lib(omp).orc_num_threads())
 
 
 def _p(a):
@@ -111,10 +121,14 @@ def lattice(q=19):
 
 class State:
     """Oracle state: f (q, nz, ny, nx) pre-collision populations (q = params.lattice),
-    q (5, ...), psi (nz, ny, nx), u (3, ...) = velocity of the previous step."""
+    q (5, ...), psi (nz, ny, nx), u (3, ...) = velocity of the previous step.  omp=True
+    steps it with the all-cores build (same arithmetic per site)."""
 
-    def __init__(self, shape, params: orc_params, seed: int = 1, inst: int = 0):
+    omp = False
+
+    def __init__(self, shape, params: orc_params, seed: int = 1, inst: int = 0, omp: bool = False):
         nx, ny, nz = shape
+        self.omp = omp
         self.shape = (nx, ny, nz)
         self.p = params
         g = (nz, ny, nx)
@@ -128,7 +142,7 @@ class State:
 
     def step(self, n: int = 1):
         nx, ny, nz = self.shape
-        lib().orc_step(nx, ny, nz, ctypes.byref(self.p), _p(self.f), _p(self.q),
+        lib(self.omp).orc_step(nx, ny, nz, ctypes.byref(self.p), _p(self.f), _p(self.q),
                        _p(self.psi), _p(self.u), n)
         self.t += n
         return self
@@ -143,14 +157,14 @@ class State:
         nx, ny, nz = self.shape
         t = {k: np.ascontiguousarray(tangent.get(k, np.zeros_like(getattr(self, k))), dtype=np.float64).copy()
              for k in ("f", "q", "psi", "u")}
-        lib().orc_step_tangent(nx, ny, nz, ctypes.byref(self.p), float(dzeta), float(dq0), _p(self.f), _p(t["f"]),
+        lib(self.omp).orc_step_tangent(nx, ny, nz, ctypes.byref(self.p), float(dzeta), float(dq0), _p(self.f), _p(t["f"]),
                                _p(self.q), _p(t["q"]), _p(self.psi), _p(t["psi"]), _p(self.u), _p(t["u"]), n)
         self.t += n
         return t
 
     def copy(self):
         s = State.__new__(State)
-        s.shape, s.p, s.t = self.shape, self.p, self.t
+        s.shape, s.p, s.t, s.omp = self.shape, self.p, self.t, self.omp
         s.f, s.q, s.psi, s.u = self.f.copy(), self.q.copy(), self.psi.copy(), self.u.copy()
         return s
 

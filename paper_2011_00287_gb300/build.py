@@ -13,6 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblbcad.so")
+# arithmetic-throughput probes for the bench's roofline denominators (not part of the step)
+PEAKS_LIB = os.path.join(LIBDIR, "libpeaks.so")
 UNITS = ["lbcad_runtime.cu", "lbcad_f32.cu", "lbcad_f64.cu", "lbcad_noalloc.cu", "lbcad_adj_f32.cu",
          "lbcad_adj_f64.cu"]
 # Units with FP32 kernels flush FP32 subnormals to zero.  Subnormal values (below 1.2e-38)
@@ -37,7 +39,7 @@ def _sources():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PEAKS_LIB):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(s) <= t for s in _sources() + [os.path.abspath(__file__)])
@@ -63,11 +65,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError("nvcc failed for %s:\n%s" % (u, r.stderr[-4000:]))
         return obj
 
-    with cf.ThreadPoolExecutor(len(UNITS)) as ex:
-        objs = list(ex.map(compile_one, UNITS))
+    with cf.ThreadPoolExecutor(len(UNITS) + 1) as ex:
+        objs = list(ex.map(compile_one, UNITS + ["peaks.cu"]))
     tmp = LIB + ".%d.tmp" % os.getpid()
-    subprocess.run([cc, "-shared", *ARCH, "-o", tmp, *objs], check=True)
+    subprocess.run([cc, "-shared", *ARCH, "-o", tmp, *objs[:-1]], check=True)
     os.replace(tmp, LIB)
+    tmp = PEAKS_LIB + ".%d.tmp" % os.getpid()
+    subprocess.run([cc, "-shared", *ARCH, "-o", tmp, objs[-1]], check=True)
+    os.replace(tmp, PEAKS_LIB)
     if verbose:
         print("built", LIB)
     return LIB

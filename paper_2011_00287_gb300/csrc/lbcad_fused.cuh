@@ -275,29 +275,43 @@ __device__ __forceinline__ void output_site(const InstDesc<T>& I, const Coef<T>&
 
 // The a6 sums within a block.  Per plane they are added in the compute type T: FP64
 // arithmetic is slow on this part, and a few FP64 operations per plane on the critical path of
-// the step cost a third of its speed.  Each warp keeps Kahan-compensated sums (sum,
-// compensation) of the twelve values, so that summing over the planes of a segment loses
-// nothing to T's rounding; FP64 takes over at the end of the segment.
+// the step cost a third of its speed.  The additions are error-free instead (two_sum_add):
+// every sum is kept as an unevaluated pair (s, c) whose exact value is s + c, each addition
+// split into its rounded result and its exact rounding error, the errors gathered in c.  The pair carries about twice T's precision (the only loss is the
+// rounding of c itself, second order in T's unit roundoff), and FP64 takes over at the end of
+// each column segment as (double)s + (double)c.  So the sums of the FP32 state come out as its
+// FP64 sums, up to the FP32 rounding of each site's own share.
 
-// Butterfly sum of the twelve values across the warp (every lane receives the sums), then
-// lane k < 12 adds value k to the warp's accumulator acc_w[k] = (sum, compensation).
+// Butterfly sum of the twelve values across the warp as (sum, error) pairs (every lane receives
+// the pair of the warp), then lane k < 12 adds pair k to the warp's accumulator acc_w[k] =
+// (sum, error).
 template <typename T>
 __device__ __forceinline__ void obs_warp_add(T v[12], T* acc_w) {
+  T e[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
+    e[k] = T(0);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    for (int o = 16; o > 0; o >>= 1) {
+      const T vo = __shfl_xor_sync(0xffffffffu, v[k], o);
+      const T eo = __shfl_xor_sync(0xffffffffu, e[k], o);
+      two_sum_add(v[k], e[k], vo);
+      e[k] += eo;
+    }
   }
   const int lane = threadIdx.x & 31;
-  T mine = T(0);
+  T mine = T(0), mine_e = T(0);
 #pragma unroll
-  for (int k = 0; k < 12; ++k) mine = lane == k ? v[k] : mine;
+  for (int k = 0; k < 12; ++k) {
+    mine = lane == k ? v[k] : mine;
+    mine_e = lane == k ? e[k] : mine_e;
+  }
   if (lane < 12) {
     T* a = acc_w + 2 * lane;
-    const T y = mine - a[1];
-    const T t = a[0] + y;
-    a[1] = (t - a[0]) - y;
-    a[0] = t;
+    T s = a[0], c = a[1];
+    two_sum_add(s, c, mine);
+    a[0] = s;
+    a[1] = c + mine_e;
   }
 }
 
@@ -305,7 +319,7 @@ __device__ __forceinline__ void obs_warp_add(T v[12], T* acc_w) {
 template <typename T>
 __device__ __forceinline__ double obs_acc_value(const T* acc, int nw, int k) {
   double v = 0.0;
-  for (int w = 0; w < nw; ++w) v += (double)acc[(w * 12 + k) * 2] - (double)acc[(w * 12 + k) * 2 + 1];
+  for (int w = 0; w < nw; ++w) v += (double)acc[(w * 12 + k) * 2] + (double)acc[(w * 12 + k) * 2 + 1];
   return v;
 }
 
@@ -352,27 +366,24 @@ __device__ __forceinline__ void obs_segment_end(const FusedObs& ob, int slot, in
 // memory by the output warps) are added up in the next phase by the sigma threads that have no
 // site in the last sigma round, while the others finish it: threads R0 .. R0 + NR - 1 (G::R0,
 // G::NR, NR a multiple of 12).  Thread t = tid - R0 adds the elements t, t + NR, t + 2 NR, ...
-// (all of value t % 12, consecutive addresses across a warp) into its own Kahan accumulator
-// acc[t] = (sum, compensation): no shuffles and no atomics.
+// (all of value t % 12, consecutive addresses across a warp) into its own error-free pair
+// acc[t] = (sum, error): no shuffles and no atomics.
 template <typename T, class G>
 __device__ __forceinline__ void obs_sigma_reduce(const T* sh, T* acc) {
   const int t = (int)threadIdx.x - G::R0;
   if (t < 0 || t >= G::NR) return;
-  T v = T(0);
+  T s = acc[2 * t], c = acc[2 * t + 1];
 #pragma unroll 4
-  for (int e = t; e < 12 * G::IP; e += G::NR) v += sh[e];
-  T* a = acc + 2 * t;
-  const T y = v - a[1];
-  const T s = a[0] + y;
-  a[1] = (s - a[0]) - y;
-  a[0] = s;
+  for (int e = t; e < 12 * G::IP; e += G::NR) two_sum_add(s, c, sh[e]);
+  acc[2 * t] = s;
+  acc[2 * t + 1] = c;
 }
 
 // The FP64 value k of a pipelined segment from the sigma threads' accumulators.
 template <typename T, class G>
 __device__ __forceinline__ double obs_sigma_value(const T* acc, int k) {
   double v = 0.0;
-  for (int t = k; t < G::NR; t += 12) v += (double)acc[2 * t] - (double)acc[2 * t + 1];
+  for (int t = k; t < G::NR; t += 12) v += (double)acc[2 * t] + (double)acc[2 * t + 1];
   return v;
 }
 

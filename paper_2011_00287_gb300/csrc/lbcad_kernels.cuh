@@ -1094,12 +1094,28 @@ __global__ void k_set_fields(InstDesc<T> I, long long oG, long long oU, long lon
 // populations stored at each site (streaming only permutes them, so the sums equal those of
 // the pulled populations).  Each warp takes whole x rows (no index division per site); a lane
 // adds its sites of a row in T, then into FP64; cos and sin come from the instance's tables.
-// k_obs_partial writes partial[block][12]; k_obs_final sums them in a fixed order.
+// (s, c) += x, with s + x split by TwoSum (Knuth, TAOCP vol. 2, 4.2.2) into its rounded sum
+// and its exact rounding error, which c gathers: s + c carries about twice T's precision.  The
+// a6 sums of the FP32 path are formed this way, so they come out as the FP64 sums of the
+// per-site FP32 shares.
+template <typename T>
+__device__ __forceinline__ void two_sum_add(T& s, T& c, T x) {
+  const T t = s + x;
+  const T bp = t - s;
+  const T err = (s - (t - bp)) + (x - bp);
+  s = t;
+  c += err;
+}
+
+// k_obs_partial writes partial[block][12]; k_obs_final sums them in a fixed order.  Each
+// thread adds the per-site shares (mass and momentum of the site's 19 stored populations, psi,
+// phi_c and phi_c times the cos/sin tables, each formed in T as the fused step forms them) into
+// error-free (sum, error) pairs, then FP64 takes over.
 template <typename T, bool SHIFT, class V>
 __global__ void __launch_bounds__(kObsBlock) k_obs_partial(InstDesc<T> I, double* __restrict__ partial) {
-  double acc[12];
+  T as[12], ac[12];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) acc[k] = 0.0;
+  for (int k = 0; k < 12; ++k) as[k] = ac[k] = T(0);
   const int nx = I.nx, ny = I.ny;
   const long long N = I.N;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1108,9 +1124,11 @@ __global__ void __launch_bounds__(kObsBlock) k_obs_partial(InstDesc<T> I, double
   for (int r = blockIdx.x * WPB + wid; r < rows; r += gridDim.x * WPB) {
     const int y = r % ny, z = r / ny;
     const long long base = (long long)r * nx;
-    T m = T(0), j0 = T(0), j1 = T(0), j2 = T(0), ps = T(0), pc = T(0), pcc = T(0), pcs = T(0);
+    const T cy = __ldg(I.trig + 2 * (nx + y)), sy = __ldg(I.trig + 2 * (nx + y) + 1);
+    const T cz = __ldg(I.trig + 2 * (nx + ny + z)), sz = __ldg(I.trig + 2 * (nx + ny + z) + 1);
     for (int x = lane; x < nx; x += 32) {
       const long long st = base + x;
+      T m = T(0), j0 = T(0), j1 = T(0), j2 = T(0);
 #pragma unroll
       for (int i = 0; i < V::Q; ++i) {
         const T f = __ldg(I.g_in + i * N + st);
@@ -1120,26 +1138,16 @@ __global__ void __launch_bounds__(kObsBlock) k_obs_partial(InstDesc<T> I, double
         if (V::c(i, 2)) j2 += V::c(i, 2) > 0 ? f : -f;
       }
       const T p = __ldg(I.psi_in + st);
-      ps += p;
       const T h = T(0.5) * (T(1) + p);
-      pc += h;
-      pcc += h * __ldg(I.trig + 2 * x);
-      pcs += h * __ldg(I.trig + 2 * x + 1);
+      const T v[12] = {m, p, j0, j1, j2, h * __ldg(I.trig + 2 * x), h * cy, h * cz, h * __ldg(I.trig + 2 * x + 1),
+                       h * sy, h * sz, h};
+#pragma unroll
+      for (int k = 0; k < 12; ++k) two_sum_add(as[k], ac[k], v[k]);
     }
-    acc[0] += (double)m;
-    acc[1] += (double)ps;
-    acc[2] += (double)j0;
-    acc[3] += (double)j1;
-    acc[4] += (double)j2;
-    acc[5] += (double)pcc;
-    acc[8] += (double)pcs;
-    const double dpc = (double)pc;
-    acc[6] += dpc * (double)__ldg(I.trig + 2 * (nx + y));
-    acc[9] += dpc * (double)__ldg(I.trig + 2 * (nx + y) + 1);
-    acc[7] += dpc * (double)__ldg(I.trig + 2 * (nx + ny + z));
-    acc[10] += dpc * (double)__ldg(I.trig + 2 * (nx + ny + z) + 1);
-    acc[11] += dpc;
   }
+  double acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = (double)as[k] + (double)ac[k];
   if (SHIFT && blockIdx.x == 0 && threadIdx.x == 0) acc[0] += (double)N * (double)I.c.rho0;
   __shared__ double sh[WPB][12];
 #pragma unroll

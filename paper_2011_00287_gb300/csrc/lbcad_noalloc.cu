@@ -14,6 +14,7 @@
 
 #include "lbcad.h"
 #include "lbcad_internal.h"
+#include "lbcad_validate.h"
 
 using namespace lbcad;
 
@@ -83,6 +84,13 @@ InstDesc<T> one_desc(const lbcad_grid& g, const lbcad_params& p, const void* g_i
   return d;
 }
 
+// Writes the launch descriptor into the file-scope slot.  The descriptor travels as a kernel
+// argument, so nothing is read from host memory once the launch is enqueued.
+template <typename T>
+__global__ void k_noalloc_set_desc(InstDesc<T> d) {
+  *reinterpret_cast<InstDesc<T>*>(g_noalloc_desc) = d;
+}
+
 template <typename T, bool SHIFT>
 int run(const lbcad_grid& g, const lbcad_params& p, const void* g_in, const void* q_in, const void* psi_in,
         const void* u_in, void* g_out, void* q_out, void* psi_out, void* u_out, void* scratch, void* desc_dev) {
@@ -90,8 +98,9 @@ int run(const lbcad_grid& g, const lbcad_params& p, const void* g_in, const void
   const InstDesc<T> d = one_desc<T>(g, p, g_in, q_in, psi_in, u_in, g_out, q_out, psi_out, u_out,
                                     (unsigned char*)scratch);
   cudaStream_t s = (cudaStream_t)p.stream;
-  cudaError_t e = cudaMemcpyToSymbolAsync(g_noalloc_desc, &d, sizeof(d), 0, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return reject(LBCAD_E_CUDA, std::string("descriptor copy: ") + cudaGetErrorString(e));
+  k_noalloc_set_desc<T><<<1, 1, 0, s>>>(d);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return reject(LBCAD_E_CUDA, std::string("descriptor launch: ") + cudaGetErrorString(e));
   e = Launch<T, SHIFT>::step((const InstDesc<T>*)desc_dev, 1, d.nblk, kStepBlock, s);
   if (e != cudaSuccess) return reject(LBCAD_E_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
   return LBCAD_OK;
@@ -104,14 +113,11 @@ extern "C" int lbcad_step_noalloc(const lbcad_grid* grid, const lbcad_params* pa
                                   void* q_out, void* psi_out, void* u_out) {
   set_thread_error("");
   if (!grid || !params) return reject(LBCAD_E_INVALID_ARG, "grid and params are required");
-  if (!g_in || !q_in || !psi_in || !u_in || !g_out || !q_out || !psi_out || !u_out)
-    return reject(LBCAD_E_INVALID_ARG, "every input and output pointer is required");
   const lbcad_grid& g = *grid;
   const lbcad_params& p = *params;
-  if (g.nx < 4 || g.ny < 4 || g.nz < 4) return reject(LBCAD_E_INVALID_ARG, "grid: every edge must be >= 4");
-  if (p.precision != LBCAD_FP32 && p.precision != LBCAD_FP64)
-    return reject(LBCAD_E_INVALID_ARG, "params: precision must be FP32 or FP64");
-  if (!(p.tau > 0.5) || !(p.rho0 > 0.0)) return reject(LBCAD_E_INVALID_ARG, "params: need tau > 1/2 and rho0 > 0");
+  // every host-side check comes before the buffer pointers are looked at, and none touches a device
+  const std::string bad = validate(g, p);
+  if (!bad.empty()) return reject(LBCAD_E_INVALID_ARG, bad);
   if (p.integrator != LBCAD_EULER || p.coupling != LBCAD_LAGGED)
     return reject(LBCAD_E_UNSUPPORTED, "only the Euler integrator with lagged coupling");
   if (p.lattice != LBCAD_D3Q19 || p.lb_form != LBCAD_LB_BODY_FORCE || p.stencil != LBCAD_STENCIL_ISO)
@@ -123,6 +129,8 @@ extern "C" int lbcad_step_noalloc(const lbcad_grid* grid, const lbcad_params* pa
     return reject(LBCAD_E_INVALID_ARG,
                   "grid too large for lbcad_step_noalloc: needs " + std::to_string(15 * part) +
                       " bytes of scratch, the static limit is " + std::to_string((size_t)LBCAD_NOALLOC_SCRATCH_BYTES));
+  if (!g_in || !q_in || !psi_in || !u_in || !g_out || !q_out || !psi_out || !u_out)
+    return reject(LBCAD_E_INVALID_ARG, "every input and output pointer is required");
   int dev = p.device;
   if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return reject(LBCAD_E_CUDA, "no CUDA device");
   int prev = -1;

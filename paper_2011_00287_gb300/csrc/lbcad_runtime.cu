@@ -13,6 +13,7 @@
 
 #include "lbcad.h"
 #include "lbcad_internal.h"
+#include "lbcad_validate.h"
 
 using namespace lbcad;
 
@@ -150,29 +151,6 @@ void release(lbcad_ctx* c) {
   }
   c->allocs.clear();
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
-}
-
-bool finite_params(const lbcad_params& p) {
-  const double v[] = {p.tau, p.rho0, p.A0, p.chi0, p.chis, p.K, p.q0, p.gammaQ, p.xi, p.a, p.b, p.kphi,
-                      p.M, p.W, p.zeta, p.R, p.centre[0], p.centre[1], p.centre[2], p.S0, p.noise};
-  for (double x : v)
-    if (!std::isfinite(x)) return false;
-  return true;
-}
-
-std::string validate(const lbcad_grid& g, const lbcad_params& p) {
-  if (g.nx < 4 || g.ny < 4 || g.nz < 4) return "grid: every edge must be >= 4";
-  if ((long long)g.nx * g.ny * g.nz > (1LL << 31)) return "grid: more than 2^31 sites";
-  if (!finite_params(p)) return "params: non-finite value";
-  if (!(p.tau > 0.5)) return "params: tau must be > 1/2";
-  if (!(p.rho0 > 0.0)) return "params: rho0 must be > 0";
-  if (p.precision != LBCAD_FP32 && p.precision != LBCAD_FP64) return "params: precision must be FP32 or FP64";
-  if (p.integrator != LBCAD_EULER && p.integrator != LBCAD_HEUN) return "params: unknown integrator";
-  if (p.coupling != LBCAD_LAGGED && p.coupling != LBCAD_SYNC) return "params: unknown coupling";
-  if (p.lattice != LBCAD_D3Q19 && p.lattice != LBCAD_D3Q15) return "params: unknown lattice";
-  if (p.lb_form != LBCAD_LB_BODY_FORCE && p.lb_form != LBCAD_LB_STRESS_EQ) return "params: unknown lb_form";
-  if (p.stencil != LBCAD_STENCIL_ISO && p.stencil != LBCAD_STENCIL_R2) return "params: unknown stencil";
-  return "";
 }
 
 template <typename T>
@@ -753,11 +731,14 @@ int lbcad_set_observe(lbcad_ctx* c, int32_t on) {
 }
 
 int lbcad_set_graph(lbcad_ctx* c, int32_t steps_per_graph) {
-  if (!c || steps_per_graph < 0) return LBCAD_E_INVALID_ARG;
+  if (!c) return LBCAD_E_INVALID_ARG;
+  // a replay must leave the ping-pong parity unchanged, so a graph holds an even number of steps
+  if (steps_per_graph < 0 || (steps_per_graph & 1))
+    return fail(c, LBCAD_E_INVALID_ARG, "steps_per_graph must be 0 or a positive even number");
   DeviceGuard dg(c->device);
   if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
   if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
-  c->graph_steps = steps_per_graph + (steps_per_graph & 1);  // even: parity is unchanged by a replay
+  c->graph_steps = steps_per_graph;
   return LBCAD_OK;
 }
 

@@ -115,3 +115,33 @@ def test_velocity_sets_on_the_host(lib, code, q):
 def test_create_rejects_unknown_scheme_options_on_the_host(lib, kw):
     got, msg = _create(lib, (8, 8, 8), **kw)
     assert got == L.LBCAD_E_INVALID_ARG and msg
+
+
+def _noalloc_rc(lib, grid, **kw):
+    """lbcad_step_noalloc with NULL buffers: every host check except the buffer pointers runs
+    first, so the message tells which check stopped the call; no device is touched."""
+    p = L._fill_params(L.default_params(grid, **kw), None, 0, None)
+    g = L.lbcad_grid(*grid)
+    rc = lib.lbcad_step_noalloc(ctypes.byref(g), ctypes.byref(p), *([None] * 8))
+    return rc, lib.lbcad_last_error(None).decode()
+
+
+@pytest.mark.parametrize("prec,fits,too_big", [
+    # 15 parts of round_up_256(n * element size) bytes in the 16 MiB static scratch:
+    # n = 279,616 = 64 * 17 * 257 in FP32 and 139,808 = 32 * 17 * 257 in FP64 are the largest
+    (L.FP32, (64, 17, 257), (4, 5, 13981)),
+    (L.FP64, (32, 17, 257), (4, 4, 8739)),
+])
+def test_noalloc_size_limit_on_the_host(lib, prec, fits, too_big):
+    rc, msg = _noalloc_rc(lib, fits, precision=prec)
+    assert rc == L.LBCAD_E_INVALID_ARG and "pointer" in msg, msg  # past the size check
+    rc, msg = _noalloc_rc(lib, too_big, precision=prec)
+    assert rc == L.LBCAD_E_INVALID_ARG and "static limit" in msg, msg
+
+
+@pytest.mark.parametrize("kw", [dict(zeta=math.nan), dict(K=math.inf), dict(tau=0.4), dict(precision=3)])
+def test_noalloc_validates_parameters_like_create(lib, kw):
+    rc, msg = _noalloc_rc(lib, (8, 8, 8), **kw)
+    assert rc == L.LBCAD_E_INVALID_ARG and "params" in msg, msg
+    rc2, msg2 = _create(lib, (8, 8, 8), **kw)
+    assert rc2 == rc and msg2.endswith(msg), (msg, msg2)

@@ -449,6 +449,83 @@ def test_force_is_divergence_of_total_stress():
     assert np.abs(F.sum(axis=(1, 2, 3))).max() < 1e-13
 
 
+def _grad_symbol(k, stencil):
+    """Symbol of the gradient stencils on cos(k.x + ph): d_b -> -s_b(k) sin(k.x + ph), written
+    out from the stencil definitions of Sec. 3 (not from the oracle's tables).
+    Isotropic D3Q19 (stencil 0): 3 sum_i w_i c_ib sin(k.c_i) = sin(k_b)(1 + cos k_c + cos k_d)/3 with
+    c, d the other two axes (two faces of weight 1/18, eight edges of weight 1/36).  Fourth-order
+    radius-2 differences (stencil 1): (8 sin k_b - sin 2k_b)/6."""
+    if stencil == 1:
+        return [(8 * np.sin(k[b]) - np.sin(2 * k[b])) / 6 for b in range(3)]
+    return [np.sin(k[b]) * (1 + np.cos(k[(b + 1) % 3]) + np.cos(k[(b + 2) % 3])) / 3 for b in range(3)]
+
+
+def _distinct_modes(rng, count, shape):
+    """count wave vectors with every component nonzero and no two alike."""
+    seen, out = set(), []
+    while len(out) < count:
+        m = tuple(int(v) for v in rng.integers(1, 3, size=3) * rng.choice([-1, 1], size=3))
+        if m not in seen:
+            seen.add(m)
+            out.append([2 * np.pi * m[a] / shape[a] for a in range(3)])
+    return out
+
+
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_force_symbols_fix_the_divergence_index(stencil):
+    """F_a = d_b sigma_ab (Sec. 3 stress divergence) on sigma_ab = A_ab cos(k_ab . x + ph_ab), each
+    component with its own wave vector, against the closed-form symbols of both stencil sets.
+    The index swaps F_a = d_b sigma_ba and F_a = d_a sigma_ab, and a sign error in either
+    difference, give O(1) differences here (asserted), so each would fail."""
+    shape = (8, 10, 12)
+    nx, ny, nz = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    rng = np.random.default_rng(31 + stencil)
+    ks = _distinct_modes(rng, 9, shape)
+    A = rng.uniform(0.5, 1.5, size=9)
+    ph = rng.uniform(0, 2 * np.pi, size=9)
+    theta = [ks[c][0] * x + ks[c][1] * y + ks[c][2] * z + ph[c] for c in range(9)]
+    sig = np.array([A[c] * np.cos(theta[c]) for c in range(9)])
+    F = O.force(np.ascontiguousarray(sig), stencil=stencil)
+
+    def div(index):
+        out = np.zeros((3, nz, ny, nx))
+        for a in range(3):
+            for b in range(3):
+                c, d = index(a, b)
+                out[a] += -A[c] * _grad_symbol(ks[c], stencil)[d] * np.sin(theta[c])
+        return out
+
+    exp = div(lambda a, b: (3 * a + b, b))
+    np.testing.assert_allclose(F, exp, atol=1e-13)
+    for wrong in (lambda a, b: (3 * b + a, b), lambda a, b: (3 * a + b, a)):
+        assert np.abs(div(wrong) - exp).max() > 1e-2
+
+
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_velocity_gradient_symbols_fix_its_orientation(stencil):
+    """The co-rotation term of Eq. 2 takes W_ab = d_b u_a.  On u_a = B_a sin(k_a . x + ph_a), each
+    component with its own wave vector, W_ab = B_a s_b(k_a) cos(k_a . x + ph_a) with the closed-form
+    symbols of both stencil sets.  A transposed W (d_a u_b) differs at O(1) (asserted)."""
+    shape = (8, 10, 12)
+    nx, ny, nz = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    rng = np.random.default_rng(41 + stencil)
+    ks = _distinct_modes(rng, 3, shape)
+    Bm = rng.uniform(1e-3, 2e-3, size=3)
+    ph = rng.uniform(0, 2 * np.pi, size=3)
+    theta = [ks[a][0] * x + ks[a][1] * y + ks[a][2] * z + ph[a] for a in range(3)]
+    u = np.ascontiguousarray(np.array([Bm[a] * np.sin(theta[a]) for a in range(3)]))
+    p = O.default_params(shape, stencil=stencil)
+    zero = np.zeros((nz, ny, nx))
+    _, _, W = O.op_rhs(np.zeros((5, nz, ny, nx)), zero, u, np.zeros((5, nz, ny, nx)), zero, p)
+    W = W.reshape(3, 3, nz, ny, nx)
+    exp = np.array([[Bm[a] * _grad_symbol(ks[a], stencil)[b] * np.cos(theta[a]) for b in range(3)]
+                    for a in range(3)])
+    np.testing.assert_allclose(W, exp, atol=1e-16)
+    assert np.abs(np.swapaxes(exp, 0, 1) - exp).max() > 1e-4
+
+
 # ---------------------------------------------------------------- the order-parameter update
 
 def test_upwind_exact_for_linear_profiles():
@@ -527,11 +604,15 @@ def test_heun_sync_and_lb_variants_conserve():
     for kw in (dict(integrator=1), dict(coupling=1), dict(lb_form=1), dict(lattice=15),
                dict(lattice=15, lb_form=1, integrator=1, coupling=1), dict(stencil=1)):
         s = _droplet_state(n=12, R=4.0, **kw)
-        m0, p0_, _ = _sums(s)
+        m0, p0_, j0 = _sums(s)
         s.step(5)
-        m1, p1, _ = _sums(s)
-        assert abs(p1 - p0_) < 1e-14 * 12 ** 3
-        assert abs(m1 - m0) < 1e-14 * 12 ** 3
+        m1, p1, j1 = _sums(s)
+        assert abs(p1 - p0_) < 1e-14 * 12 ** 3, kw
+        assert abs(m1 - m0) < 1e-14 * 12 ** 3, kw
+        # every force here is a telescoping difference (radius 1 or 2), so momentum is conserved
+        # too; a one-sided or non-antisymmetric radius-2 difference would break this
+        assert np.abs(j1 - j0).max() < 1e-14 * 12 ** 3, kw
+        assert np.abs(s.u).max() > 1e-7, kw
 
 
 # ---------------------------------------------------------------- D3Q15 and the stress-in-equilibrium form (Eqs. 9-11)
@@ -907,3 +988,17 @@ def test_observables_closed_forms(q):
             want_s = amp * np.sin(2 * np.pi * r0 / La) if b == a else 0.0
             assert abs(o[5 + b] - want_c) <= 1e-11 * N, (a, b)
             assert abs(o[8 + b] - want_s) <= 1e-11 * N, (a, b)
+
+
+def test_openmp_build_is_bitwise_identical():
+    """The all-cores build of the oracle (its per-stage parallel-for over z) computes every
+    site's values in the same order as the single-thread build, so the states are identical."""
+    shape = (12, 10, 14)
+    p = O.default_params(shape, R=4.0, p0=8.0, zeta=0.01)
+    a = O.State(shape, p, seed=2)
+    b = O.State(shape, p, seed=2, omp=True)
+    a.step(4)
+    b.step(4)
+    for k in ("f", "q", "psi", "u"):
+        assert np.array_equal(getattr(a, k), getattr(b, k)), k
+    assert O.num_threads(False) == 1 and O.num_threads(True) >= 1
