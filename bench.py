@@ -31,7 +31,7 @@ METRIC = "hybrid-step MLUPS & % of HBM roofline, FP32 vs plain FP64 at stated er
 BYTES_PER_SITE = {"fp32": 200, "fp64": 400}
 # fused-step schedules offered to the autotuner, in candidate order
 TILE_NAMES = ["32x8", "32x16", "64x8", "32x8-pipelined-8+8", "32x8-pipelined-6+10", "32x6-pipelined-9+7",
-              "32x6-pipelined-10+6"]
+              "32x6-pipelined-10+6", "32x8-pipelined-8+8-prefetch", "32x8-pipelined-8+8-decoupled"]
 
 
 def workload_params(L, n, prec, **kw):

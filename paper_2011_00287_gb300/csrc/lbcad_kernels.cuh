@@ -149,9 +149,23 @@ __host__ __device__ constexpr int sig_lane(int c) { return c < 6 ? c / 3 : (c < 
 __host__ __device__ constexpr int pair_c0(int j) { return j < 3 ? j : (j == 3 ? 6 : 8); }
 __host__ __device__ constexpr int pair_c1(int j) { return j < 3 ? j + 3 : (j == 3 ? 7 : -1); }
 
+// The pressure a/2 - b/4 of the uniform binary phase at psi = +-1 with Q = 0 (-f of Eq. 5
+// there).  The step stores and differentiates sigma + pref I instead of sigma: the stencil
+// divergence of a constant is exactly zero, so the force is the same, but in FP32 the stored
+// values no longer carry this large, nearly uniform part, whose rounding the divergence (a
+// difference of neighbouring values) would otherwise amplify.  The form of Eqs. 9-11, which
+// puts sigma itself into the equilibrium, takes pref back out (lb_collide_stress).
+template <typename T>
+__device__ __forceinline__ T pressure_ref(const Coef<T>& c) {
+  return T(0.5) * c.a - T(0.25) * c.b;
+}
+
 // H (5), mu and the total stress sigma (9, row-major a*3+b) at one site from Q, psi and
 // their stencils: dq[a][k] = d_a of stored component k, lapq[k], dp[a] = d_a psi,
-// lapp, hp = Hessian of psi (xx, yy, zz, xy, xz, yz).
+// lapp, hp = Hessian of psi (xx, yy, zz, xy, xz, yz).  sig is returned as sigma + pref I
+// (pressure_ref): the binary part of the free energy enters the pressure relative to its value
+// at psi = +-1, (psi - 1)(psi + 1)[(b/4)(psi^2 + 1) - a/2] = f_bin(psi) - f_bin(1), a form in
+// which the subtraction is exact rather than a cancellation of two FP32 values.
 template <typename T>
 __device__ __forceinline__ void local_fields(const Coef<T>& c, const T q[5], T psi, const T dq[3][5],
                                              const T lapq[5], const T dp[3], T lapp, const T hp[6], T H[5],
@@ -235,7 +249,7 @@ __device__ __forceinline__ void local_fields(const Coef<T>& c, const T q[5], T p
 #pragma unroll
   for (int i = 0; i < 3; ++i) Qdp[i] = Q[i][0] * dp[0] + Q[i][1] * dp[1] + Q[i][2] * dp[2];
   const T anch = dp[0] * Qdp[0] + dp[1] * Qdp[1] + dp[2] * Qdp[2];
-  const T fden = psi2 * (T(0.25) * c.b * psi2 - T(0.5) * c.a) + T(0.5) * c.kphi * g2 +
+  const T fden = (psi - T(1)) * (psi + T(1)) * (T(0.25) * c.b * (psi2 + T(1)) - T(0.5) * c.a) + T(0.5) * c.kphi * g2 +
                  c.A0 * (T(0.5) * (T(1) - chi / T(3)) * trQ2 - chi / T(3) * trQ3 + chi / T(4) * trQ2 * trQ2) +
                  T(0.5) * c.K * (G[0][0] + G[1][1] + G[2][2]) + Kq * QC + Kq * c.q0 * trQ2 + c.W * anch;
   const T P0 = psi * mu - fden;
@@ -451,16 +465,21 @@ __device__ __forceinline__ void gather_op(const A& acc, T& lapmu, T Wg[3][3], T 
     uf[4] = f[5];
     uf[5] = f[6];
   }
+  // Q and psi at the centre and the six faces, as the field pairs (Q_xx, Q_xy), (Q_xz, Q_yy),
+  // (Q_yz, psi) of A::pair
 #pragma unroll
-  for (int i = 1; i < 7; ++i) {
+  for (int i = 0; i < 7; ++i) {
     const int cx = lat_c(i, 0), cy = lat_c(i, 1), cz = lat_c(i, 2);
+    T* qd = i ? qf[i - 1] : q0;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) qf[i - 1][k] = acc.q(k, cx, cy, cz);
-    pf[i - 1] = acc.psi(cx, cy, cz);
+    for (int j = 0; j < 3; ++j) {
+      const Vec2<T> v = acc.pair(j, cx, cy, cz);
+      qd[2 * j] = v.x;
+      if (j < 2) qd[2 * j + 1] = v.y;
+      else if (i) pf[i - 1] = v.y;
+      else p0 = v.y;
+    }
   }
-#pragma unroll
-  for (int k = 0; k < 5; ++k) q0[k] = acc.q(k, 0, 0, 0);
-  p0 = acc.psi(0, 0, 0);
 }
 
 // a3 + the stencils of a4, for the one-pass step.
@@ -593,7 +612,8 @@ __device__ __forceinline__ void lb_collide(const Coef<T>& c, const T F[3], T g[V
   }
 }
 
-// a5 in the form of Eqs. 9-11 at one site: the equilibrium carries the symmetric stress,
+// a5 in the form of Eqs. 9-11 at one site (sig given as sigma + pref I, as local_fields
+// returns it): the equilibrium carries the symmetric stress,
 //   f_eq_i = w_i [rho + 3 rho c.u + (9/2)(c c - I/3) : (rho u u - sigma^S)],
 // the antisymmetric stress enters as F_i = 3 w_i c . FA with FA = div sigma^A (moments 0, FA,
 // 0: Eq. 10), rho u = sum f c (Eq. 8), f* = f - (f - f_eq)/tau + F_i (Eq. 7).  sig is the full
@@ -613,6 +633,8 @@ __device__ __forceinline__ void lb_collide_stress(const Coef<T>& c, const T FA[3
   }
   const T rho = SHIFT ? (c.rho0 + m0) : m0;
   const T rinv = T(1) / rho;
+  // sig arrives as sigma + pref I (local_fields): the equilibrium carries sigma itself
+  const T pref = pressure_ref(c);
 #pragma unroll
   for (int a = 0; a < 3; ++a) u[a] = j[a] * rinv;
   if (mom) {  // as in lb_collide: the forcing adds FA to the momentum (Eq. 10)
@@ -621,7 +643,8 @@ __device__ __forceinline__ void lb_collide_stress(const Coef<T>& c, const T FA[3
     for (int a = 0; a < 3; ++a) mom[1 + a] = j[a] + FA[a];
   }
   // Pi = rho u u - sigma^S (symmetric: xx, yy, zz, xy, xz, yz)
-  const T Pxx = rho * u[0] * u[0] - sig[0], Pyy = rho * u[1] * u[1] - sig[4], Pzz = rho * u[2] * u[2] - sig[8];
+  const T Pxx = rho * u[0] * u[0] - (sig[0] - pref), Pyy = rho * u[1] * u[1] - (sig[4] - pref),
+          Pzz = rho * u[2] * u[2] - (sig[8] - pref);
   const T Pxy = rho * u[0] * u[1] - T(0.5) * (sig[1] + sig[3]);
   const T Pxz = rho * u[0] * u[2] - T(0.5) * (sig[2] + sig[6]);
   const T Pyz = rho * u[1] * u[2] - T(0.5) * (sig[5] + sig[7]);
@@ -1098,6 +1121,11 @@ __global__ void k_set_fields(InstDesc<T> I, long long oG, long long oU, long lon
 // and its exact rounding error, which c gathers: s + c carries about twice T's precision.  The
 // a6 sums of the FP32 path are formed this way, so they come out as the FP64 sums of the
 // per-site FP32 shares.
+// a * b rounded to T before any later use: the a6 shares are products that must come out as
+// the same T values in every pass, so they may not be contracted into a following addition.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 template <typename T>
 __device__ __forceinline__ void two_sum_add(T& s, T& c, T x) {
   const T t = s + x;
@@ -1139,8 +1167,8 @@ __global__ void __launch_bounds__(kObsBlock) k_obs_partial(InstDesc<T> I, double
       }
       const T p = __ldg(I.psi_in + st);
       const T h = T(0.5) * (T(1) + p);
-      const T v[12] = {m, p, j0, j1, j2, h * __ldg(I.trig + 2 * x), h * cy, h * cz, h * __ldg(I.trig + 2 * x + 1),
-                       h * sy, h * sz, h};
+      const T v[12] = {m, p, j0, j1, j2, mul_rn(h, __ldg(I.trig + 2 * x)), mul_rn(h, cy), mul_rn(h, cz),
+                       mul_rn(h, __ldg(I.trig + 2 * x + 1)), mul_rn(h, sy), mul_rn(h, sz), h};
 #pragma unroll
       for (int k = 0; k < 12; ++k) two_sum_add(as[k], ac[k], v[k]);
     }

@@ -32,7 +32,7 @@ LB_BODY_FORCE, LB_STRESS_EQ = 0, 1
 STENCIL_ISO, STENCIL_R2 = 0, 1
 FIELD_G, FIELD_RHO, FIELD_U, FIELD_Q, FIELD_PSI = 1, 2, 4, 8, 16
 PATH_FUSED, PATH_TWO_KERNEL, PATH_STAGED = 0, 1, 2
-N_TILE_CONFIGS = 7  # candidates of lbcad_autotune / lbcad_set_tiles (FP32; FP64 has one)
+N_TILE_CONFIGS = 9  # candidates of lbcad_autotune / lbcad_set_tiles (FP32; FP64 has one)
 FIELD_NCOMP = {FIELD_G: 19, FIELD_RHO: 1, FIELD_U: 3, FIELD_Q: 5, FIELD_PSI: 1}
 FIELD_NAMES = {FIELD_G: "g", FIELD_RHO: "rho", FIELD_U: "u", FIELD_Q: "q", FIELD_PSI: "psi"}
 
@@ -289,8 +289,8 @@ class Simulation:
         """Time each fused tile shape without advancing the state; keep the fastest.
         Returns (chosen index, ms per launch of each candidate)."""
         chosen = ctypes.c_int32(-1)
-        ms = (ctypes.c_float * 8)()
-        _check(library().lbcad_autotune(self.ctx, int(reps), ctypes.byref(chosen), ms, 8), self.ctx)
+        ms = (ctypes.c_float * 16)()
+        _check(library().lbcad_autotune(self.ctx, int(reps), ctypes.byref(chosen), ms, 16), self.ctx)
         return chosen.value, [v for v in ms][:N_TILE_CONFIGS]
 
     def set_tiles(self, cfg: int):

@@ -47,7 +47,8 @@ def _check(a, b, N, fp64):
     assert abs(a[0] - b[0]) <= 1e-10 * N and np.abs(a[2:5] - b[2:5]).max() <= 1e-10 * N, (a, b)
 
 
-CASES = [("fp64", L.FP64, 0), ("fp32-32x8", L.FP32, 0), ("fp32-pipelined", L.FP32, 3), ("fp32-32x16", L.FP32, 1)]
+CASES = [("fp64", L.FP64, 0), ("fp32-32x8", L.FP32, 0), ("fp32-pipelined", L.FP32, 3), ("fp32-32x16", L.FP32, 1),
+         ("fp32-pipelined-prefetch", L.FP32, 7)]
 
 
 @pytest.mark.parametrize("name,prec,tiles", CASES, ids=[c[0] for c in CASES])
@@ -178,7 +179,7 @@ def _host_sums(sim, inst, rho0=1.0):
     return out, scale, _plane_fsum(np.abs(g), nz)
 
 
-@pytest.mark.parametrize("tiles", [3, 0], ids=["pipelined-8+8", "32x8"])
+@pytest.mark.parametrize("tiles", [3, 0, 7], ids=["pipelined-8+8", "32x8", "pipelined-8+8-prefetch"])
 def test_fp32_fused_sums_are_the_fp64_sums_of_the_state(tiles):
     """The benchmarked workload (128^3, R = 32, pitch 32): the FP64 sums the FP32 step forms
     against FP64 sums of its stored state formed on the host.
