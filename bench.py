@@ -31,7 +31,7 @@ METRIC = "hybrid-step MLUPS & % of HBM roofline, FP32 vs plain FP64 at stated er
 BYTES_PER_SITE = {"fp32": 200, "fp64": 400}
 # fused-step schedules offered to the autotuner, in candidate order
 TILE_NAMES = ["32x8", "32x16", "64x8", "32x8-pipelined-8+8", "32x8-pipelined-6+10", "32x6-pipelined-9+7",
-              "32x6-pipelined-10+6", "32x8-pipelined-8+8-prefetch", "32x8-pipelined-8+8-decoupled"]
+              "32x6-pipelined-10+6"]
 
 
 def workload_params(L, n, prec, **kw):
@@ -99,6 +99,22 @@ def measured_alu_peaks(device=0):
         v = ctypes.c_double()
         out.append(v.value if fn(device, iters, ctypes.byref(v)) == 0 else None)
     return out[0], out[1]
+
+
+def add_latencies(device=0):
+    """Cycles of one dependent FP64 and FP32 addition on this GPU (chain probe, csrc/peaks.cu)."""
+    import ctypes
+    from paper_2011_00287_gb300 import build as B
+    try:
+        lib = ctypes.CDLL(B.PEAKS_LIB)
+    except OSError:
+        return None
+    out = {}
+    for name, fn in (("fp64", lib.add_latency_fp64_cycles), ("fp32", lib.add_latency_fp32_cycles)):
+        fn.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        v = ctypes.c_double()
+        out[name] = v.value if fn(device, ctypes.byref(v)) == 0 else None
+    return out
 
 
 def committed_profile_value(key, name="lbcad_step_fp32_128cube.md"):
@@ -410,6 +426,7 @@ def main():
         p64, p32 = measured_alu_peaks(local)
         fp64["measured_peak_tflops"] = {"fp64": p64, "fp32": p32,
                                         "how": "FMA-chain probe (csrc/peaks.cu), best of 5 launches on every SM"}
+        fp64["add_latency_cycles"] = add_latencies(local)
         if fl and p64:
             ach = fl * N / (ms64 * 1e-3) / 1e12
             fp64["roofline"] = {"bound": "alu", "achieved": ach, "peak": p64, "unit": "TFLOP/s", "frac": ach / p64,

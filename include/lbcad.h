@@ -190,11 +190,8 @@ int lbcad_set_path(lbcad_ctx* c, int32_t path);
  * Candidates: 0 = 32x8 tiles (default), 1 = 32x16, 2 = 64x8, 3 and 4 = 32x8 software-pipelined
  * (sigma of plane k+1 on 8 or 6 warps while the other 8 or 10 warps output plane k-1, in
  * one phase), 5 and 6 = 32x6 software-pipelined (9 or 10 sigma warps, one round per
- * plane), 7 = candidate 3 with each output thread's population pulls of the next plane
- * prefetched into shared memory, 8 = candidate 3 with the two warp groups synchronised by
- * named producer/consumer barriers instead of a block barrier per plane (the sigma warps run
- * up to one plane ahead); 1-8 are FP32 only.  With LBCAD_D3Q15 or LBCAD_LB_STRESS_EQ
- * only 0 and 3 are candidates (-1 for the others). */
+ * plane); 1-6 are FP32 only.  With LBCAD_D3Q15 or LBCAD_LB_STRESS_EQ only 0 and 3 are
+ * candidates (-1 for the others). */
 int lbcad_autotune(lbcad_ctx* c, int32_t reps, int32_t* chosen, float* ms_per_cfg, int32_t ncfg);
 
 /* Selects tile shape `cfg` of the fused step explicitly (same candidates as above;

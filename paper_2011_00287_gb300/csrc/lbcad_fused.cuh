@@ -189,6 +189,9 @@ struct AntiPairAcc {
 // (GlobalPull: from global memory at those offsets).  ob (OBS): the site's share of the a6
 // sums of the new state (see FusedObs); trg(tx, ty, tz) gives (cos, sin) of 2 pi x/nx,
 // 2 pi y/ny and 2 pi z/nz of the site.
+// The pulls address population i of plane z - c_z through a base pointer that is the same for
+// the whole block (g_in + i N + plane offset) plus the site's in-plane offset of row y - c_y and
+// column x - c_x (below 2^31, so 32-bit): one 64-bit addition per pull.
 template <typename T, class V>
 struct GlobalPull {
   const T* g_in;
@@ -196,10 +199,20 @@ struct GlobalPull {
   __device__ __forceinline__ void operator()(T g[V::Q], const long long zo[3], const int pyo[3],
                                              const int pxo[3]) const {
 #pragma unroll
-    for (int i = 0; i < V::Q; ++i)
-      g[i] = ld(g_in + i * N + zo[1 - V::c(i, 2)] + pyo[1 - V::c(i, 1)] + pxo[1 - V::c(i, 0)]);
+    for (int i = 0; i < V::Q; ++i) {
+      const T* base = g_in + (i * N + zo[1 - V::c(i, 2)]);
+      const unsigned o = (unsigned)(pyo[1 - V::c(i, 1)] + pxo[1 - V::c(i, 0)]);
+      g[i] = ld(base + o);
+    }
   }
 };
+
+// A store of an output value to global memory, cached in L2 only: the next step reads the new
+// state back through L2, and the pulls of this step keep L1 to themselves.
+template <typename T>
+__device__ __forceinline__ void st_out(T* p, T v) {
+  __stcg(p, v);
+}
 
 template <typename T, bool SHIFT, class V, int FORM, int MODE, class A, class Offs, class HS, class TR, class PL>
 __device__ __forceinline__ void output_site(const InstDesc<T>& I, const Coef<T>& cf, const A& acc, const Offs& offs,
@@ -227,15 +240,18 @@ __device__ __forceinline__ void output_site(const InstDesc<T>& I, const Coef<T>&
       lb_collide_stress<T, SHIFT, V>(cf, F, sg, g, u);
     }
     const long long s = zo[1] + pyo[1] + pxo[1];
+    T* const go = I.g_out + s;
+    T* const uo = I.u_out + s;
 #pragma unroll
-    for (int i = 0; i < V::Q; ++i) I.g_out[i * N + s] = g[i];
+    for (int i = 0; i < V::Q; ++i) st_out(go + i * N, g[i]);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) I.u_out[a * N + s] = u[a];
+    for (int a = 0; a < 3; ++a) st_out(uo + a * N, u[a]);
     T Hs[5];
     hs(Hs);
+    T* const ho = I.H + s;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) I.H[k * N + s] = Hs[k];
-    I.mu[s] = acc.spair(4, 0, 0, 0).y;
+    for (int k = 0; k < 5; ++k) st_out(ho + k * N, Hs[k]);
+    st_out(I.mu + s, acc.spair(4, 0, 0, 0).y);
     return;
   }
   T F[3], lapmu, Wg[3][3], q0[5], qf[6][5], p0, pf[6], u0[3], uf[6];
@@ -259,13 +275,16 @@ __device__ __forceinline__ void output_site(const InstDesc<T>& I, const Coef<T>&
     lb_collide_stress<T, SHIFT, V>(cf, F, sg, g, u, OBS ? mom : nullptr);
   }
   const long long s = zo[1] + pyo[1] + pxo[1];
+  T* const qo = I.q_out + s;
+  T* const go = I.g_out + s;
+  T* const uo = I.u_out + s;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) I.q_out[k * N + s] = qn[k];
-  I.psi_out[s] = pn;
+  for (int k = 0; k < 5; ++k) st_out(qo + k * N, qn[k]);
+  st_out(I.psi_out + s, pn);
 #pragma unroll
-  for (int i = 0; i < V::Q; ++i) I.g_out[i * N + s] = g[i];
+  for (int i = 0; i < V::Q; ++i) st_out(go + i * N, g[i]);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) I.u_out[a * N + s] = u[a];
+  for (int a = 0; a < 3; ++a) st_out(uo + a * N, u[a]);
   // a6: mass, psi and momentum of the new state, and phi_c with its centroid moments
   if constexpr (OBS) {
     const T pc = T(0.5) * (T(1) + pn);
@@ -348,51 +367,68 @@ __device__ __forceinline__ void obs_warp_add(T v[12], T* acc_w) {
   }
 }
 
-// The FP64 value k of a segment from nw warp accumulators acc[nw][12][2].
-template <typename T>
-__device__ __forceinline__ double obs_acc_value(const T* acc, int nw, int k) {
-  double v = 0.0;
-  for (int w = 0; w < nw; ++w) v += (double)acc[(w * 12 + k) * 2] + (double)acc[(w * 12 + k) * 2 + 1];
-  return v;
+
+// red[k + 12 m] (k < 12, m < M) summed over m into red[k] by a fixed pairing tree (all threads;
+// barriers between the levels).  FP64 additions are long-latency on this part, so the sums run
+// as trees of depth log2(M) rather than as chains of length M; the order is fixed, so the
+// result does not depend on timing.
+__device__ __forceinline__ void obs_tree12(double* red, int M) {
+  for (int len = M; len > 1;) {
+    const int half = (len + 1) >> 1;
+    for (int t = threadIdx.x; t < 12 * (len - half); t += blockDim.x) red[t] += red[t + 12 * half];
+    __syncthreads();
+    len = half;
+  }
 }
 
-// End of a column segment (all threads, after a barrier): seg[12] (shared memory, written by
-// threads 0-11 before the barrier) goes to the segment's slot; the block that fills the last
-// slot of the instance then sums the instance's slots into ob.latest, each of the twelve
-// values over fixed strided subsets of the slots and then over the subsets in order, so the
-// result does not depend on which block finishes last.  red: shared scratch of at least
-// 12 * (blockDim.x / 12) doubles.  mass_shift = N rho0 with shifted populations.
-__device__ __forceinline__ void obs_segment_end(const FusedObs& ob, int slot, int inst, const double* seg,
-                                                double* red, double mass_shift) {
+// End of a column segment: its twelve FP64 sums go to the segment's slot with plain stores
+// (threads 0-11, after a barrier that made seg[12] visible).  Nothing else happens per segment:
+// the completion of an instance is counted once per block, at the end of the kernel
+// (obs_block_end).
+__device__ __forceinline__ void obs_segment_write(const FusedObs& ob, int slot, const double* seg) {
+  if (threadIdx.x < 12) ob.slots[slot * 12 + threadIdx.x] = seg[threadIdx.x];
+}
+
+// End of the kernel (all threads): each segment of this block counts its slot on the
+// segment's instance (after one fence for all of this block's slot stores); the block whose
+// count completes an instance sums that instance's slots into ob.latest: each of the twelve
+// values over fixed strided subsets of the slots, the loads of a thread in flight together,
+// then over the subsets in order, so the result does not depend on which block finishes last.
+// No spin waits.  red: shared scratch of at least 12 * (blockDim.x / 12) doubles.
+// mass_shift(inst) = N rho0 with shifted populations, else 0.
+template <class MS>
+__device__ __forceinline__ void obs_block_end(const FusedObs& ob, int nseg, double* red, const MS& mass_shift) {
   __shared__ int last;
   const int tid = threadIdx.x;
-  if (tid < 12) {
-    ob.slots[slot * 12 + tid] = seg[tid];
-    __threadfence();
-  }
   __syncthreads();
-  if (tid == 0) last = atomicAdd(&ob.cnt[inst], 1u) == (unsigned)(ob.nslot[inst] - 1);
+  if (tid < 12) __threadfence();  // the slot stores of this block's segments, before the counting
   __syncthreads();
-  if (last) {
-    __threadfence();
-    const int per = blockDim.x / 12;
-    const int lo = ob.slot_lo[inst], hi = ob.slot_hi[inst];
-    if (tid < 12 * per) {
-      const int k = tid % 12, l = tid / 12;
-      double v = 0.0;
-      for (int sl = lo + l; sl < hi; sl += per)
-        if (ob.slot_inst[sl] == inst) v += __ldcg(ob.slots + sl * 12 + k);
-      red[l * 12 + k] = v;
+  for (int j = 0; j < nseg; ++j) {
+    const int inst = ob.slot_inst[blockIdx.x * ob.maxseg + j];
+    if (tid == 0) last = atomicAdd(&ob.cnt[inst], 1u) == (unsigned)(ob.nslot[inst] - 1);
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      const int per = blockDim.x / 12;
+      const int lo = ob.slot_lo[inst], hi = ob.slot_hi[inst];
+      if (tid < 12 * per) {
+        const int k = tid % 12, l = tid / 12;
+        double v = 0.0;
+#pragma unroll 8
+        for (int sl = lo + l; sl < hi; sl += per) {
+          const int si = __ldg(ob.slot_inst + sl);
+          const double x = __ldcg(ob.slots + sl * 12 + k);
+          v += si == inst ? x : 0.0;
+        }
+        red[l * 12 + k] = v;
+      }
+      __syncthreads();
+      obs_tree12(red, per);
+      if (tid < 12) ob.latest[inst * 12 + tid] = red[tid] + (tid == 0 ? mass_shift(inst) : 0.0);
+      if (tid == 0) ob.cnt[inst] = 0u;
     }
     __syncthreads();
-    if (tid < 12) {
-      double v = tid == 0 ? mass_shift : 0.0;
-      for (int l = 0; l < per; ++l) v += red[l * 12 + tid];
-      ob.latest[inst * 12 + tid] = v;
-    }
-    if (tid == 0) ob.cnt[inst] = 0u;
   }
-  __syncthreads();
 }
 
 // Pipelined kernel: the a6 shares of an output plane (sh[IP][12], site-major, left in shared
@@ -400,7 +436,8 @@ __device__ __forceinline__ void obs_segment_end(const FusedObs& ob, int slot, in
 // site in the last sigma round, while the others finish it: threads R0 .. R0 + NR - 1 (G::R0,
 // G::NR, NR a multiple of 12).  Thread t = tid - R0 adds the elements t, t + NR, t + 2 NR, ...
 // (all of value t % 12, consecutive addresses across a warp) into its own error-free pair
-// acc[t] = (sum, error): no shuffles and no atomics.
+// acc[t] = (sum, error): no shuffles and no atomics.  (A two-lane form, two values per thread
+// and f32x2 operations, measured slower: its dependency chains got no shorter.)
 template <typename T, class G>
 __device__ __forceinline__ void obs_sigma_reduce(const T* sh, T* acc) {
   const int t = (int)threadIdx.x - G::R0;
@@ -412,12 +449,17 @@ __device__ __forceinline__ void obs_sigma_reduce(const T* sh, T* acc) {
   acc[2 * t + 1] = c;
 }
 
-// The FP64 value k of a pipelined segment from the sigma threads' accumulators.
+// The twelve FP64 values of a pipelined segment from the sigma threads' accumulators: every
+// accumulator converted in parallel into dred[NR] (shared scratch), then value k added over its
+// threads t = k, k + 12, ... by a fixed tree.  All threads; seg[0..11] (threads 0-11) is visible
+// after the caller's next barrier.
 template <typename T, class G>
-__device__ __forceinline__ double obs_sigma_value(const T* acc, int k) {
-  double v = 0.0;
-  for (int t = k; t < G::NR; t += 12) v += (double)acc[2 * t] + (double)acc[2 * t + 1];
-  return v;
+__device__ __forceinline__ void obs_sigma_values(const T* acc, double* dred, double* seg) {
+  const int t = (int)threadIdx.x - G::R0;
+  if (t >= 0 && t < G::NR) dred[t] = (double)acc[2 * t] + (double)acc[2 * t + 1];
+  __syncthreads();
+  obs_tree12(dred, G::NR / 12);
+  if (threadIdx.x < 12) seg[threadIdx.x] = dred[threadIdx.x];
 }
 
 // Ring slots of plane p (p >= -2).
@@ -634,13 +676,19 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
     }
     if constexpr (OBS) {
       __syncthreads();
-      if (tid < 12) oseg[tid] = obs_acc_value<T>(oacc, G::NW, tid);
+      double* dred = reinterpret_cast<double*>(smem_raw);
+      if (tid < 12 * G::NW) dred[tid] = (double)oacc[2 * tid] + (double)oacc[2 * tid + 1];
       __syncthreads();
-      obs_segment_end(ob, blockIdx.x * ob.maxseg + seg, tl.inst, oseg, reinterpret_cast<double*>(smem_raw),
-                      SHIFT ? (double)cf.rho0 * (double)N : 0.0);
+      obs_tree12(dred, G::NW);
+      if (tid < 12) oseg[tid] = dred[tid];
+      __syncthreads();
+      obs_segment_write(ob, blockIdx.x * ob.maxseg + seg, oseg);
     }
     ++seg;
   }
+  if constexpr (OBS)
+    obs_block_end(ob, seg, reinterpret_cast<double*>(smem_raw),
+                  [&](int inst) { return SHIFT ? (double)D[inst].c.rho0 * (double)D[inst].N : 0.0; });
 }
 
 // ---------------------------------------------------------------- pipelined variant
@@ -695,16 +743,6 @@ struct PipeGeom {
                          sizeof(T) +
                      (QW + QH) * sizeof(int);
   }
-  // prefetched population pulls (pf): [2][19][IP] in T after everything else, double-buffered
-  // by output-plane parity
-  template <typename T>
-  __host__ __device__ static constexpr size_t pf_off(bool obs) {
-    return (bytes<T>(obs) + 15) / 16 * 16;
-  }
-  template <typename T>
-  __host__ __device__ static constexpr size_t bytes(bool obs, bool pf) {
-    return pf ? pf_off<T>(obs) + (size_t)2 * 19 * IP * sizeof(T) : bytes<T>(obs);
-  }
 };
 
 __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
@@ -723,21 +761,7 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
   if constexpr (sizeof(T) == 4) cp_async4(dst, src); else cp_async8(dst, src);
 }
 
-// Population pulls of the next output plane, prefetched by cp.async into shared memory during
-// the current phase (PF): each output thread copies its own 19 pulled values g_i(x - c_i) of
-// plane p into pbuf[p & 1][i][site] and reads them back one phase later, so the pulls wait on
-// no global-memory latency in the output phase.
-template <typename T, class V>
-struct SmemPull {
-  const T* buf;  // pbuf[p & 1] + site
-  int IP;
-  __device__ __forceinline__ void operator()(T g[V::Q], const long long*, const int*, const int*) const {
-#pragma unroll
-    for (int i = 0; i < V::Q; ++i) g[i] = buf[i * IP];
-  }
-};
-
-template <typename T, bool SHIFT, int TY, int NS, class V, int FORM, int MODE, bool PF = false>
+template <typename T, bool SHIFT, int TY, int NS, class V, int FORM, int MODE>
 __global__ void __launch_bounds__(512, 1)
     k_step_pipe(const InstDesc<T>* __restrict__ D, const FusedTile* __restrict__ tiles, int ntiles, long long total,
                 FusedObs ob) {
@@ -757,7 +781,6 @@ __global__ void __launch_bounds__(512, 1)
   T* xt = reinterpret_cast<T*>(smem_raw + G::template trig_off<T>());     // (cos, sin) of the tile's x
   T* yt = xt + 2 * TX;                                                     // ... and y
   double* oseg = reinterpret_cast<double*>(smem_raw + G::template seg_off<T>());
-  T* pbuf = reinterpret_cast<T*>(smem_raw + G::template pf_off<T>(OBS));  // PF: [2][19][IP]
   const int tid = threadIdx.x;
   auto q6 = [](int p) { return (p + 12) % 6; };
   auto s4 = [](int p) { return (p + 12) % 4; };
@@ -858,26 +881,6 @@ __global__ void __launch_bounds__(512, 1)
         if constexpr (OBS)
           if (k - 2 >= zb) obs_sigma_reduce<T, G>(oshare + ((k - 2) & 1) * G::IP * 12, oacc);
       } else {
-        if constexpr (PF) {
-          // prefetch the pulls of the next output plane p = k into pbuf[k & 1]
-          const int site = tid - G::NS;
-          const int tx = site % TX, ty = site / TX;
-          if (k >= zb && k < ze && site < G::IP && tl.x0 + tx < nx && tl.y0 + ty < ny) {
-            const long long zp[3] = {(long long)wrap_plane(k - 1, nz) * plane, (long long)k * plane,
-                                     (long long)wrap_plane(k + 1, nz) * plane};
-            int pyo[3], pxo[3];
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-              pyo[j] = ymap[ty + 1 + j];
-              pxo[j] = xmap[tx + 1 + j];
-            }
-            T* dst = pbuf + (k & 1) * 19 * G::IP + site;
-#pragma unroll
-            for (int i = 0; i < V::Q; ++i)
-              cp_async_elem(dst + i * G::IP,
-                            I.g_in + i * N + zp[1 - V::c(i, 2)] + pyo[1 - V::c(i, 1)] + pxo[1 - V::c(i, 0)]);
-          }
-        }
         if (k - 1 >= zb) {
           // output of plane z = k-1
           const int z = k - 1;
@@ -920,17 +923,14 @@ __global__ void __launch_bounds__(512, 1)
               cty = lds2(yt + 2 * ty);
               ctz = tz;
             };
-            if constexpr (PF)
-              output_site<T, SHIFT, V, FORM, MODE>(I, cf, acc, offs, hs, trg,
-                                                   SmemPull<T, V>{pbuf + (z & 1) * 19 * G::IP + site, G::IP}, ob6);
-            else
-              output_site<T, SHIFT, V, FORM, MODE>(I, cf, acc, offs, hs, trg, GlobalPull<T, V>{I.g_in, N}, ob6);
+            output_site<T, SHIFT, V, FORM, MODE>(I, cf, acc, offs, hs, trg, GlobalPull<T, V>{I.g_in, N}, ob6);
           }
           if (OBS && site < G::IP) {
             T* dst = oshare + (z & 1) * G::IP * 12 + site * 12;
 #pragma unroll
-            for (int c = 0; c < 12; c += 2) {
-              if constexpr (sizeof(T) == 4) *reinterpret_cast<float2*>(dst + c) = make_float2(ob6[c], ob6[c + 1]);
+            for (int c = 0; c < 12; c += (sizeof(T) == 4 ? 4 : 2)) {
+              if constexpr (sizeof(T) == 4)
+                *reinterpret_cast<float4*>(dst + c) = make_float4(ob6[c], ob6[c + 1], ob6[c + 2], ob6[c + 3]);
               else *reinterpret_cast<double2*>(dst + c) = make_double2(ob6[c], ob6[c + 1]);
             }
           }
@@ -943,328 +943,15 @@ __global__ void __launch_bounds__(512, 1)
       // the last output plane (ze - 1) has not been added up yet
       if (ze - 1 >= zb) obs_sigma_reduce<T, G>(oshare + ((ze - 1) & 1) * G::IP * 12, oacc);
       __syncthreads();
-      if (tid < 12) oseg[tid] = obs_sigma_value<T, G>(oacc, tid);
+      obs_sigma_values<T, G>(oacc, reinterpret_cast<double*>(smem_raw), oseg);
       __syncthreads();
-      obs_segment_end(ob, blockIdx.x * ob.maxseg + seg, tl.inst, oseg, reinterpret_cast<double*>(smem_raw),
-                      SHIFT ? (double)cf.rho0 * (double)N : 0.0);
+      obs_segment_write(ob, blockIdx.x * ob.maxseg + seg, oseg);
     }
     ++seg;
   }
-}
-
-// ---------------------------------------------------------------- decoupled pipelined variant
-// The pipelined schedule with the two warp groups decoupled: instead of one block barrier per
-// plane, each group signals the other through named barriers (bar.arrive by the producer,
-// bar.sync by the consumer) and the rings hold one plane more, so the sigma group can run up
-// to one plane ahead of the output group and neither waits on the other's slowest warp:
-//   sigma iteration k (sigma, mu, H of plane k+1; the Q/psi load of plane k+3) starts once the
-//   output group has finished iteration k-2 (EMPTY), whose plane was the last reader of the
-//   ring slots it reuses, and ends with FULL(k);
-//   output iteration k (plane k-1; the u load of plane k+1) starts once FULL(k-1) says that
-//   sigma of plane k and everything before it is in shared memory, and ends with EMPTY(k).
-// FULL and EMPTY cycle through three barrier ids each: a group can re-arrive on an id only
-// after the other group has consumed its previous use (sigma iteration k+3 needs EMPTY(k+1),
-// which needs the output group past its sync on FULL(k); output iteration k+3 needs FULL(k+2),
-// which needs the sigma group past its sync on EMPTY(k)).  Every arrival is matched by exactly
-// one sync: the arrivals the loop leaves open (EMPTY of the last two output iterations, FULL
-// of the last sigma iteration) are synced after it.  Each group also has a barrier of its own
-// for the planes its threads copy with cp.async.  The a6 shares of output plane z go to
-// buffer z mod 3; sigma iteration k adds up plane k-3, written by output iteration k-2.
-// Rings: Q/psi 7 planes, sigma/mu 5, H 4, u 4.  Barrier ids: 0 the block barrier (segment
-// start and end), 1 sigma group, 2 output group, 3-5 FULL, 6-8 EMPTY.
-template <int TY_>
-struct PipeDcGeom {
-  static constexpr int TX = 32, TY = TY_, NT = 512, NS = 256, NO = NT - NS;
-  static constexpr int QW = TX + 4, QH = TY + 4, QP = QW * QH;
-  static constexpr int SW = TX + 2, SH = TY + 2, SP = SW * SH;
-  static constexpr int IP = TX * TY;
-  static constexpr int NQS = 7, NSS = 5, NHS = 4, NUS = 4, NSHARE = 3;
-  static constexpr int QLD = (QP + NS - 1) / NS;  // Q/psi sites per sigma thread and plane
-  static constexpr int ULD = (SP + NO - 1) / NO;  // u sites per output thread and plane
-  static_assert(SP <= 2 * NS && NO >= IP && QLD <= 2 && ULD <= 2, "site counts per thread");
-  static constexpr int RL = SP - (SP - 1) / NS * NS;
-  static constexpr int R0 = ((RL + 31) / 32 * 32 < NS - 12) ? (RL + 31) / 32 * 32 : NS - 12;
-  static constexpr int NR = (NS - R0) / 12 * 12;
-  static_assert(NR >= 12, "a6 reducer threads");
-  template <typename T>
-  __host__ __device__ static constexpr size_t ring_bytes() {
-    return ((size_t)NQS * 6 * QP + (size_t)NSS * 10 * SP + (size_t)NHS * 5 * IP + (size_t)NUS * 3 * SP) * sizeof(T) +
-           (QW + QH) * sizeof(int);
-  }
-  template <typename T>
-  __host__ __device__ static constexpr size_t obs_off() {
-    return (ring_bytes<T>() + 15) / 16 * 16;
-  }
-  template <typename T>
-  __host__ __device__ static constexpr size_t acc_off() {
-    return obs_off<T>() + (size_t)NSHARE * IP * 12 * sizeof(T);
-  }
-  template <typename T>
-  __host__ __device__ static constexpr size_t trig_off() {
-    return acc_off<T>() + (size_t)NR * 2 * sizeof(T);
-  }
-  template <typename T>
-  __host__ __device__ static constexpr size_t seg_off() {
-    return (trig_off<T>() + (size_t)(TX + TY) * 2 * sizeof(T) + 7) / 8 * 8;
-  }
-  template <typename T>
-  __host__ __device__ static constexpr size_t bytes(bool obs) {
-    return obs ? seg_off<T>() + 12 * sizeof(double) : ring_bytes<T>();
-  }
-};
-
-__device__ __forceinline__ void named_sync(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
-}
-__device__ __forceinline__ void named_arrive(int id, int nthreads) {
-  asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
-}
-
-template <typename T, bool SHIFT, int TY, class V, int FORM, int MODE>
-__global__ void __launch_bounds__(512, 1)
-    k_step_pipe_dc(const InstDesc<T>* __restrict__ D, const FusedTile* __restrict__ tiles, int ntiles,
-                   long long total, FusedObs ob) {
-  static_assert(MODE != kFusedLbOnly, "the decoupled schedule runs the whole step");
-  constexpr bool OBS = MODE == kFusedSums;
-  using G = PipeDcGeom<TY>;
-  constexpr int QW = G::QW, QP = G::QP, SW = G::SW, SP = G::SP, TX = G::TX, NS = G::NS, NO = G::NO;
-  constexpr int QSLOT = 6 * QP, SSLOT = 10 * SP, HSLOT = 5 * G::IP, USLOT = 3 * SP;
-  constexpr int B_SIG = 1, B_OUT = 2, B_FULL = 3, B_EMPTY = 6;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sQ = reinterpret_cast<T*>(smem_raw);
-  T* sS = sQ + G::NQS * QSLOT;
-  T* sH = sS + G::NSS * SSLOT;
-  T* sU = sH + G::NHS * HSLOT;
-  int* xmap = reinterpret_cast<int*>(sU + G::NUS * USLOT);
-  int* ymap = xmap + QW;
-  T* oshare = reinterpret_cast<T*>(smem_raw + G::template obs_off<T>());  // a6 shares [3][IP][12]
-  T* oacc = reinterpret_cast<T*>(smem_raw + G::template acc_off<T>());    // sigma-thread sums [NR][2]
-  T* xt = reinterpret_cast<T*>(smem_raw + G::template trig_off<T>());
-  T* yt = xt + 2 * TX;
-  double* oseg = reinterpret_cast<double*>(smem_raw + G::template seg_off<T>());
-  const int tid = threadIdx.x;
-  // ring slots and barrier ids of plane / iteration p (p >= -6)
-  auto mod = [](int p, int m) { return (p + 6 * m) % m; };
-
-  const long long begin = (total * blockIdx.x) / gridDim.x;
-  const long long end = (total * (blockIdx.x + 1)) / gridDim.x;
-  long long it = begin;
-  int seg = 0;
-  while (it < end) {
-    int lo = 0, hi = ntiles - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (tiles[mid].start <= it) lo = mid; else hi = mid - 1;
-    }
-    const FusedTile tl = tiles[lo];
-    const InstDesc<T>& I = D[tl.inst];
-    const int nx = I.nx, ny = I.ny, nz = I.nz;
-    const long long N = I.N;
-    const long long plane = (long long)nx * ny;
-    const int zb = (int)(it - tl.start);
-    const long long seg_end = end < tl.start + tl.nz ? end : tl.start + tl.nz;
-    const int ze = (int)(seg_end - tl.start);
-    it = seg_end;
-    const Coef<T> cf = I.c;
-    const T* __restrict__ qin = I.q_in;
-    const T* __restrict__ pin = I.psi_in;
-    const T* __restrict__ uin = I.u_in;
-
-    __syncthreads();
-    for (int k = tid; k < QW; k += G::NT) xmap[k] = wrapmod(tl.x0 + k - 2, nx);
-    for (int k = tid; k < G::QH; k += G::NT) ymap[k] = wrapmod(tl.y0 + k - 2, ny) * nx;
-    if constexpr (OBS) {
-      for (int k = tid; k < G::NR * 2; k += G::NT) oacc[k] = T(0);
-      for (int k = tid; k < 2 * (TX + G::TY); k += G::NT) {
-        const int e = k >> 1, c = k & 1;
-        xt[k] = e < TX ? I.trig[2 * ((tl.x0 + e) % nx) + c] : I.trig[2 * (nx + (tl.y0 + e - TX) % ny) + c];
-      }
-    }
-    __syncthreads();
-    // load sites: sigma thread t copies Q/psi sites t and t + NS, output thread o the u sites
-    // o and o + NO
-    int qoff[2] = {0, 0}, uoff[2] = {0, 0};
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      if (tid < NS && tid + r * NS < QP) {
-        const int k = tid + r * NS, ly = k / QW, lx = k - ly * QW;
-        qoff[r] = ymap[ly] + xmap[lx];
-      }
-      if (tid >= NS && tid - NS + r * NO < SP) {
-        const int k = tid - NS + r * NO, sy = k / SW, sx = k - sy * SW;
-        uoff[r] = ymap[sy + 1] + xmap[sx + 1];
-      }
-    }
-    auto issue_q = [&](int p) {  // sigma threads
-      T* dst = sQ + mod(p, G::NQS) * QSLOT;
-      const long long gz = (long long)wrap_plane(p, nz) * plane;
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int k = tid + r * NS;
-        if (k < QP) {
-#pragma unroll
-          for (int f = 0; f < 5; ++f) cp_async_elem(dst + qidx<QP>(f, k), qin + f * N + gz + qoff[r]);
-          cp_async_elem(dst + qidx<QP>(5, k), pin + gz + qoff[r]);
-        }
-      }
-    };
-    auto issue_u = [&](int p) {  // output threads
-      T* dst = sU + mod(p, G::NUS) * USLOT;
-      const long long gz = (long long)wrap_plane(p, nz) * plane;
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int k = tid - NS + r * NO;
-        if (k < SP) {
-#pragma unroll
-          for (int a = 0; a < 3; ++a) cp_async_elem(dst + uidx<SP>(a, k), uin + a * N + gz + uoff[r]);
-        }
-      }
-    };
-    if (tid < NS) {
-      issue_q(zb - 2);
-      issue_q(zb - 1);
-      issue_q(zb);
-    }
-    cp_async_commit_wait_all();
-    __syncthreads();
-
-    for (int k = zb - 2; k <= ze; ++k) {
-      if (tid < NS) {
-        // ---- sigma group, iteration k: sigma, mu (and H) of plane k+1
-        if (k >= zb) named_sync(B_EMPTY + mod(k - 2, 3), G::NT);
-        issue_q(k + 3);
-#pragma unroll 1
-        for (int ss = tid; k + 1 <= ze && ss < SP; ss += NS) {
-          const int sy = ss / SW, sx = ss - sy * SW;
-          SmemFieldsAcc<T, QW, QP> acc;
-          acc.qc = (sy + 1) * QW + (sx + 1);
-#pragma unroll
-          for (int j = 0; j < 3; ++j) acc.pl[j] = sQ + mod(k + j, G::NQS) * QSLOT;
-          T q0[5], p0, dq[3][5], lapq[5], dp[3], lapp, hp[6];
-          gather_fields<T>(acc, q0, p0, dq, lapq, dp, lapp, hp);
-          T H[5], sig[9], mu;
-          local_fields<T>(cf, q0, p0, dq, lapq, dp, lapp, hp, H, mu, sig);
-          store_sigma<T, SP>(sS + mod(k + 1, G::NSS) * SSLOT, sy * SW + sx, sig, mu);
-          if (sx >= 1 && sx <= TX && sy >= 1 && sy <= G::TY) {
-            T* hd = sH + mod(k + 1, G::NHS) * HSLOT + (sy - 1) * TX + (sx - 1);
-#pragma unroll
-            for (int c = 0; c < 5; ++c) hd[c * G::IP] = H[c];
-          }
-        }
-        // a6: the shares of output plane k-3 (written by output iteration k-2)
-        if constexpr (OBS)
-          if (k - 3 >= zb) obs_sigma_reduce<T, G>(oshare + mod(k - 3, G::NSHARE) * G::IP * 12, oacc);
-        cp_async_commit_wait_all();
-        named_sync(B_SIG, NS);
-        named_arrive(B_FULL + mod(k, 3), G::NT);
-      } else {
-        // ---- output group, iteration k: output of plane k-1
-        if (k >= zb - 1) named_sync(B_FULL + mod(k - 1, 3), G::NT);
-        issue_u(k + 1);
-        if (k - 1 >= zb) {
-          const int z = k - 1;
-          const long long zo3[3] = {(long long)wrap_plane(z - 1, nz) * plane, (long long)z * plane,
-                                    (long long)wrap_plane(z + 1, nz) * plane};
-          Vec2<T> tz = v2(T(0), T(0));
-          if constexpr (OBS) tz = ldg2(I.trig + 2 * (nx + ny + z));
-          const int site = tid - NS;
-          const int tx = site % TX, ty = site / TX;
-          T ob6[12] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-          if (site < G::IP && tl.x0 + tx < nx && tl.y0 + ty < ny) {
-            SmemUpdateAcc<T, QW, QP, SW, SP> acc;
-            acc.qc = (ty + 2) * QW + (tx + 2);
-            acc.sc = (ty + 1) * SW + (tx + 1);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-              acc.qpl[j] = sQ + mod(z - 1 + j, G::NQS) * QSLOT;
-              acc.spl[j] = sS + mod(z - 1 + j, G::NSS) * SSLOT;
-              acc.upl[j] = sU + mod(z - 1 + j, G::NUS) * USLOT;
-            }
-            T Hs[5];
-#pragma unroll
-            for (int c = 0; c < 5; ++c) Hs[c] = sH[mod(z, G::NHS) * HSLOT + c * G::IP + site];
-            auto hs = [&](T H[5]) {
-#pragma unroll
-              for (int c = 0; c < 5; ++c) H[c] = Hs[c];
-            };
-            auto offs = [&](long long zo[3], int pyo[3], int pxo[3]) {
-#pragma unroll
-              for (int j = 0; j < 3; ++j) {
-                zo[j] = zo3[j];
-                pyo[j] = ymap[ty + 1 + j];
-                pxo[j] = xmap[tx + 1 + j];
-              }
-            };
-            auto trg = [&](Vec2<T>& ctx, Vec2<T>& cty, Vec2<T>& ctz) {
-              ctx = lds2(xt + 2 * tx);
-              cty = lds2(yt + 2 * ty);
-              ctz = tz;
-            };
-            output_site<T, SHIFT, V, FORM, MODE>(I, cf, acc, offs, hs, trg, GlobalPull<T, V>{I.g_in, N}, ob6);
-          }
-          if (OBS && site < G::IP) {
-            T* dst = oshare + mod(z, G::NSHARE) * G::IP * 12 + site * 12;
-#pragma unroll
-            for (int c = 0; c < 12; c += 2) {
-              if constexpr (sizeof(T) == 4) *reinterpret_cast<float2*>(dst + c) = make_float2(ob6[c], ob6[c + 1]);
-              else *reinterpret_cast<double2*>(dst + c) = make_double2(ob6[c], ob6[c + 1]);
-            }
-          }
-        }
-        cp_async_commit_wait_all();
-        named_sync(B_OUT, NO);
-        named_arrive(B_EMPTY + mod(k, 3), G::NT);
-      }
-    }
-    // consume the arrivals the loop left open
-    if (tid < NS) {
-      named_sync(B_EMPTY + mod(ze - 1, 3), G::NT);
-      named_sync(B_EMPTY + mod(ze, 3), G::NT);
-    } else {
-      named_sync(B_FULL + mod(ze, 3), G::NT);
-    }
-    __syncthreads();
-    if constexpr (OBS) {
-      // the last two output planes have not been added up yet
-      if (ze - 2 >= zb) obs_sigma_reduce<T, G>(oshare + mod(ze - 2, G::NSHARE) * G::IP * 12, oacc);
-      if (ze - 1 >= zb) obs_sigma_reduce<T, G>(oshare + mod(ze - 1, G::NSHARE) * G::IP * 12, oacc);
-      __syncthreads();
-      if (tid < 12) oseg[tid] = obs_sigma_value<T, G>(oacc, tid);
-      __syncthreads();
-      obs_segment_end(ob, blockIdx.x * ob.maxseg + seg, tl.inst, oseg, reinterpret_cast<double*>(smem_raw),
-                      SHIFT ? (double)cf.rho0 * (double)N : 0.0);
-    }
-    ++seg;
-  }
-}
-
-template <typename T, bool SHIFT, int TY, class V, int FORM>
-cudaError_t prepare_pipe_dc(FusedCfg* cfg) {
-  using G = PipeDcGeom<TY>;
-  auto k0 = k_step_pipe_dc<T, SHIFT, TY, V, FORM, kFusedPlain>;
-  auto k1 = k_step_pipe_dc<T, SHIFT, TY, V, FORM, kFusedSums>;
-  cfg->tx = G::TX;
-  cfg->ty = G::TY;
-  cfg->threads = G::NT;
-  cfg->smem = G::template bytes<T>(true);
-  cudaError_t e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::template bytes<T>(false));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::template bytes<T>(true));
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cfg->blocks_per_sm, k1, G::NT, cfg->smem);
-}
-
-template <typename T, bool SHIFT, int TY, class V, int FORM>
-cudaError_t launch_pipe_dc(const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles, long long total, int grid,
-                           const FusedObs& ob, bool obs, cudaStream_t s) {
-  using G = PipeDcGeom<TY>;
-  if (obs)
-    k_step_pipe_dc<T, SHIFT, TY, V, FORM, kFusedSums><<<grid, G::NT, G::template bytes<T>(true), s>>>(
-        d_desc, tiles, ntiles, total, ob);
-  else
-    k_step_pipe_dc<T, SHIFT, TY, V, FORM, kFusedPlain><<<grid, G::NT, G::template bytes<T>(false), s>>>(
-        d_desc, tiles, ntiles, total, ob);
-  return cudaGetLastError();
+  if constexpr (OBS)
+    obs_block_end(ob, seg, reinterpret_cast<double*>(smem_raw),
+                  [&](int inst) { return SHIFT ? (double)D[inst].c.rho0 * (double)D[inst].N : 0.0; });
 }
 
 template <typename T, bool SHIFT, int TX, int TY, class V, int FORM>
@@ -1301,44 +988,42 @@ cudaError_t prepare_cfg(FusedCfg* cfg) {
 }
 
 // Tile shapes offered to the autotuner: 32x8 (two blocks per SM in FP32), 32x16 and
-// 64x8 (one block per SM, fewer redundant halo sites), and the pipelined schedules: 7 with the
-// population pulls prefetched into shared memory, 8 with the two warp groups decoupled by
-// named barriers.  FP64 only fits 32x8.  The
+// 64x8 (one block per SM, fewer redundant halo sites), and the pipelined schedules.  FP64
+// only fits 32x8.  The
 // D3Q15 and Eq. 9-11 variants come in 32x8 and the pipelined 32x8 schedule with 8 + 8 warps.
 template <typename T, bool SHIFT>
 int LaunchFused<T, SHIFT>::num_configs() {
-  return sizeof(T) == 4 ? 9 : 1;
+  return sizeof(T) == 4 ? 7 : 1;
 }
 
-template <typename T, bool SHIFT, int TY, int NS, class V, int FORM, bool LB = false, bool PF = false>
+template <typename T, bool SHIFT, int TY, int NS, class V, int FORM, bool LB = false>
 cudaError_t prepare_pipe(FusedCfg* cfg) {
   using G = PipeGeom<TY, NS>;
-  auto k0 = k_step_pipe<T, SHIFT, TY, NS, V, FORM, kFusedPlain, PF>;
-  auto k1 = k_step_pipe<T, SHIFT, TY, NS, V, FORM, kFusedSums, PF>;
+  auto k0 = k_step_pipe<T, SHIFT, TY, NS, V, FORM, kFusedPlain>;
+  auto k1 = k_step_pipe<T, SHIFT, TY, NS, V, FORM, kFusedSums>;
   auto k2 = k_step_pipe<T, SHIFT, TY, NS, V, FORM, kFusedLbOnly>;
   cfg->tx = G::TX;
   cfg->ty = G::TY;
   cfg->threads = G::NT;
-  cfg->smem = G::template bytes<T>(true, PF);
-  cudaError_t e =
-      cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::template bytes<T>(false, PF));
+  cfg->smem = G::template bytes<T>(true);
+  cudaError_t e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::template bytes<T>(false));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::template bytes<T>(true, PF));
+    e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::template bytes<T>(true));
   if (e == cudaSuccess && LB)
     e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::template bytes<T>(false));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cfg->blocks_per_sm, k1, G::NT, cfg->smem);
 }
 
-template <typename T, bool SHIFT, int TY, int NS, class V, int FORM, bool PF = false>
+template <typename T, bool SHIFT, int TY, int NS, class V, int FORM>
 cudaError_t launch_pipe(const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles, long long total, int grid,
                         const FusedObs& ob, bool obs, cudaStream_t s) {
   using G = PipeGeom<TY, NS>;
   if (obs)
-    k_step_pipe<T, SHIFT, TY, NS, V, FORM, kFusedSums, PF><<<grid, G::NT, G::template bytes<T>(true, PF), s>>>(
+    k_step_pipe<T, SHIFT, TY, NS, V, FORM, kFusedSums><<<grid, G::NT, G::template bytes<T>(true), s>>>(
         d_desc, tiles, ntiles, total, ob);
   else
-    k_step_pipe<T, SHIFT, TY, NS, V, FORM, kFusedPlain, PF><<<grid, G::NT, G::template bytes<T>(false, PF), s>>>(
+    k_step_pipe<T, SHIFT, TY, NS, V, FORM, kFusedPlain><<<grid, G::NT, G::template bytes<T>(false), s>>>(
         d_desc, tiles, ntiles, total, ob);
   return cudaGetLastError();
 }
@@ -1355,8 +1040,6 @@ struct FusedVariant {
         if (k == 4) return prepare_pipe<T, SHIFT, 8, 192, V, FORM>(cfg);
         if (k == 5) return prepare_pipe<T, SHIFT, 6, 288, V, FORM>(cfg);
         if (k == 6) return prepare_pipe<T, SHIFT, 6, 320, V, FORM>(cfg);
-        if (k == 7) return prepare_pipe<T, SHIFT, 8, 256, V, FORM, false, true>(cfg);
-        if (k == 8) return prepare_pipe_dc<T, SHIFT, 8, V, FORM>(cfg);
       }
       if (k == 3) return prepare_pipe<T, SHIFT, 8, 256, V, FORM, true>(cfg);
     }
@@ -1385,8 +1068,6 @@ struct FusedVariant {
         if (k == 4) return launch_pipe<T, SHIFT, 8, 192, V, FORM>(d, t, nt, total, grid, ob, obs, s);
         if (k == 5) return launch_pipe<T, SHIFT, 6, 288, V, FORM>(d, t, nt, total, grid, ob, obs, s);
         if (k == 6) return launch_pipe<T, SHIFT, 6, 320, V, FORM>(d, t, nt, total, grid, ob, obs, s);
-        if (k == 7) return launch_pipe<T, SHIFT, 8, 256, V, FORM, true>(d, t, nt, total, grid, ob, obs, s);
-        if (k == 8) return launch_pipe_dc<T, SHIFT, 8, V, FORM>(d, t, nt, total, grid, ob, obs, s);
       }
       if (k == 3) return launch_pipe<T, SHIFT, 8, 256, V, FORM>(d, t, nt, total, grid, ob, obs, s);
     }

@@ -149,23 +149,9 @@ __host__ __device__ constexpr int sig_lane(int c) { return c < 6 ? c / 3 : (c < 
 __host__ __device__ constexpr int pair_c0(int j) { return j < 3 ? j : (j == 3 ? 6 : 8); }
 __host__ __device__ constexpr int pair_c1(int j) { return j < 3 ? j + 3 : (j == 3 ? 7 : -1); }
 
-// The pressure a/2 - b/4 of the uniform binary phase at psi = +-1 with Q = 0 (-f of Eq. 5
-// there).  The step stores and differentiates sigma + pref I instead of sigma: the stencil
-// divergence of a constant is exactly zero, so the force is the same, but in FP32 the stored
-// values no longer carry this large, nearly uniform part, whose rounding the divergence (a
-// difference of neighbouring values) would otherwise amplify.  The form of Eqs. 9-11, which
-// puts sigma itself into the equilibrium, takes pref back out (lb_collide_stress).
-template <typename T>
-__device__ __forceinline__ T pressure_ref(const Coef<T>& c) {
-  return T(0.5) * c.a - T(0.25) * c.b;
-}
-
 // H (5), mu and the total stress sigma (9, row-major a*3+b) at one site from Q, psi and
 // their stencils: dq[a][k] = d_a of stored component k, lapq[k], dp[a] = d_a psi,
-// lapp, hp = Hessian of psi (xx, yy, zz, xy, xz, yz).  sig is returned as sigma + pref I
-// (pressure_ref): the binary part of the free energy enters the pressure relative to its value
-// at psi = +-1, (psi - 1)(psi + 1)[(b/4)(psi^2 + 1) - a/2] = f_bin(psi) - f_bin(1), a form in
-// which the subtraction is exact rather than a cancellation of two FP32 values.
+// lapp, hp = Hessian of psi (xx, yy, zz, xy, xz, yz).
 template <typename T>
 __device__ __forceinline__ void local_fields(const Coef<T>& c, const T q[5], T psi, const T dq[3][5],
                                              const T lapq[5], const T dp[3], T lapp, const T hp[6], T H[5],
@@ -249,7 +235,7 @@ __device__ __forceinline__ void local_fields(const Coef<T>& c, const T q[5], T p
 #pragma unroll
   for (int i = 0; i < 3; ++i) Qdp[i] = Q[i][0] * dp[0] + Q[i][1] * dp[1] + Q[i][2] * dp[2];
   const T anch = dp[0] * Qdp[0] + dp[1] * Qdp[1] + dp[2] * Qdp[2];
-  const T fden = (psi - T(1)) * (psi + T(1)) * (T(0.25) * c.b * (psi2 + T(1)) - T(0.5) * c.a) + T(0.5) * c.kphi * g2 +
+  const T fden = psi2 * (T(0.25) * c.b * psi2 - T(0.5) * c.a) + T(0.5) * c.kphi * g2 +
                  c.A0 * (T(0.5) * (T(1) - chi / T(3)) * trQ2 - chi / T(3) * trQ3 + chi / T(4) * trQ2 * trQ2) +
                  T(0.5) * c.K * (G[0][0] + G[1][1] + G[2][2]) + Kq * QC + Kq * c.q0 * trQ2 + c.W * anch;
   const T P0 = psi * mu - fden;
@@ -514,39 +500,36 @@ __device__ __forceinline__ void op_update(const Coef<T>& c, T lapmu, const T Wg[
   }
   T Q[3][3];
   full3(q0, Q);
-  T Dm[3][3], Om[3][3];
+  // co-rotation S = (xi D + Om)(Q + I/3) + (Q + I/3)(xi D - Om) - 2 xi tr(QW)(Q + I/3), with
+  // D, Om the symmetric and antisymmetric parts of W.  With M = xi D + Om, (xi D - Om) = M^T, so
+  // S = P + P^T - 2 xi tr(QW)(Q + I/3) for P = M (Q + I/3); it is projected to its traceless part
+  // (its trace is 2 xi tr(D)/3).  M_ij = (xi + 1)/2 W_ij + (xi - 1)/2 W_ji.
+  const T mp = T(0.5) * (c.xi + T(1)), mm = T(0.5) * (c.xi - T(1));
+  T M[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      Dm[i][j] = T(0.5) * (Wg[i][j] + Wg[j][i]);
-      Om[i][j] = T(0.5) * (Wg[i][j] - Wg[j][i]);
-    }
+    for (int j = 0; j < 3; ++j) M[i][j] = mp * Wg[i][j] + mm * Wg[j][i];
+  T Qt[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Qt[i][j] = i == j ? Q[i][j] + T(1.0 / 3.0) : Q[i][j];
   T trQW = T(0);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) trQW += Q[i][j] * Wg[j][i];
-  const T trD = Dm[0][0] + Dm[1][1] + Dm[2][2];
-  // co-rotation S = xi (DQ + QD) + (2 xi/3) D + (Om Q - Q Om) - 2 xi tr(QW)(Q + I/3),
-  // projected to its traceless part (its trace is 2 xi tr(D)/3)
+  const T trD = Wg[0][0] + Wg[1][1] + Wg[2][2];
   const T cq = -T(2) * c.xi * trQW;
-  const T cdiag = cq / T(3) - (T(2) * c.xi / T(9)) * trD;
-  const T c23 = T(2) * c.xi / T(3);
+  const T cdiag = -(T(2) * c.xi / T(9)) * trD;
+  auto P = [&](int i, int j) { return M[i][0] * Qt[0][j] + M[i][1] * Qt[1][j] + M[i][2] * Qt[2][j]; };
   const int I5[5] = {0, 0, 0, 1, 1};
   const int J5[5] = {0, 1, 2, 1, 2};
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     const int i = I5[k], j = J5[k];
-    T DQ = T(0), QD = T(0), OQ = T(0), QO = T(0);
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      DQ += Dm[i][m] * Q[m][j];
-      QD += Q[i][m] * Dm[m][j];
-      OQ += Om[i][m] * Q[m][j];
-      QO += Q[i][m] * Om[m][j];
-    }
-    T S = c.xi * (DQ + QD) + c23 * Dm[i][j] + (OQ - QO) + cq * Q[i][j];
+    T S = (i == j ? T(2) * P(i, i) : P(i, j) + P(j, i)) + cq * Qt[i][j];
     if (i == j) S += cdiag;
     if (RHS) qn[k] = -adv[k] + S + c.gammaQ * Hs[k];
     else qn[k] = q0[k] - adv[k] + S + c.gammaQ * Hs[k];
@@ -575,45 +558,47 @@ __device__ __forceinline__ void lb_collide(const Coef<T>& c, const T F[3], T g[V
   }
   const T rho = SHIFT ? (c.rho0 + m0) : m0;
   const T rinv = T(1) / rho;
+  // every product-sum below is an explicit fma: the collision then rounds identically in every
+  // kernel that inlines it, whatever the compiler would contract
 #pragma unroll
-  for (int a = 0; a < 3; ++a) u[a] = (j[a] + T(0.5) * F[a]) * rinv;
+  for (int a = 0; a < 3; ++a) u[a] = fma(T(0.5), F[a], j[a]) * rinv;
   if (mom) {
     mom[0] = m0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) mom[1 + a] = j[a] + F[a];
   }
-  const T u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-  const T uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
-  // equilibrium w rho (1 + 3 cu + 4.5 cu^2 - 1.5 u^2) (shifted: minus w rho0) and Guo
-  // term guo w (3 (c - u).F + 9 (c.u)(c.F)), split into even (A, C) and odd (B, E) parts
-  const T base = SHIFT ? (m0 - T(1.5) * rho * u2) : (rho - T(1.5) * rho * u2);
+  const T u2 = fma(u[2], u[2], fma(u[1], u[1], u[0] * u[0]));
+  const T uF = fma(u[2], F[2], fma(u[1], F[1], u[0] * F[0]));
+  // BGK + Guo as g' = (1 - om) g + om f_eq + F_i, with the equilibrium
+  // w rho (1 + 3 cu + 4.5 cu^2 - 1.5 u^2) (shifted: minus w rho0) and the Guo term
+  // guo w (3 (c - u).F + 9 (c.u)(c.F)).  For the pair (c, -c) the new values are
+  // (1 - om) g_(+-) + (X +- Y), with the even part X = om w (base + 4.5 rho cu^2) + guo w
+  // (9 cu cF - 3 uF) and the odd part Y = 3 om w rho cu + 3 guo w cF; their coefficients depend
+  // on the weight class only, so each class forms them once.
+  const T base = fma(T(-1.5) * rho, u2, SHIFT ? m0 : rho);
+  const T om = c.tau_inv;
+  const T omc = T(1) - om;
   const T r45 = T(4.5) * rho;
   const T r3 = T(3) * rho;
-  const T om = c.tau_inv;
   {
     const T w = T(V::w(0));
-    const T geq = w * base;
-    const T Fi = -T(3) * c.guo * w * uF;
-    g[0] = g[0] - (g[0] - geq) * om + Fi;
+    g[0] = fma(omc, g[0], fma(om * w, base, (T(-3) * c.guo * w) * uF));
   }
 #pragma unroll
   for (int i = 1; i < V::Q; i += 2) {
     const T w = T(V::w(i));
+    const T omw = om * w, gw = c.guo * w;
     const T cu = T(V::c(i, 0)) * u[0] + T(V::c(i, 1)) * u[1] + T(V::c(i, 2)) * u[2];
     const T cF = T(V::c(i, 0)) * F[0] + T(V::c(i, 1)) * F[1] + T(V::c(i, 2)) * F[2];
-    const T Aeq = w * (base + r45 * cu * cu);
-    const T Beq = w * r3 * cu;
-    const T gw = c.guo * w;
-    const T Cf = gw * (T(9) * cu * cF - T(3) * uF);
-    const T Ef = T(3) * gw * cF;
+    const T X = fma(omw * r45, cu * cu, fma(omw, base, fma((T(9) * gw) * cu, cF, (T(-3) * gw) * uF)));
+    const T Y = fma(omw * r3, cu, (T(3) * gw) * cF);
     const T gp = g[i], gm = g[i + 1];
-    g[i] = gp - (gp - (Aeq + Beq)) * om + (Cf + Ef);
-    g[i + 1] = gm - (gm - (Aeq - Beq)) * om + (Cf - Ef);
+    g[i] = fma(omc, gp, X + Y);
+    g[i + 1] = fma(omc, gm, X - Y);
   }
 }
 
-// a5 in the form of Eqs. 9-11 at one site (sig given as sigma + pref I, as local_fields
-// returns it): the equilibrium carries the symmetric stress,
+// a5 in the form of Eqs. 9-11 at one site: the equilibrium carries the symmetric stress,
 //   f_eq_i = w_i [rho + 3 rho c.u + (9/2)(c c - I/3) : (rho u u - sigma^S)],
 // the antisymmetric stress enters as F_i = 3 w_i c . FA with FA = div sigma^A (moments 0, FA,
 // 0: Eq. 10), rho u = sum f c (Eq. 8), f* = f - (f - f_eq)/tau + F_i (Eq. 7).  sig is the full
@@ -633,8 +618,6 @@ __device__ __forceinline__ void lb_collide_stress(const Coef<T>& c, const T FA[3
   }
   const T rho = SHIFT ? (c.rho0 + m0) : m0;
   const T rinv = T(1) / rho;
-  // sig arrives as sigma + pref I (local_fields): the equilibrium carries sigma itself
-  const T pref = pressure_ref(c);
 #pragma unroll
   for (int a = 0; a < 3; ++a) u[a] = j[a] * rinv;
   if (mom) {  // as in lb_collide: the forcing adds FA to the momentum (Eq. 10)
@@ -643,8 +626,7 @@ __device__ __forceinline__ void lb_collide_stress(const Coef<T>& c, const T FA[3
     for (int a = 0; a < 3; ++a) mom[1 + a] = j[a] + FA[a];
   }
   // Pi = rho u u - sigma^S (symmetric: xx, yy, zz, xy, xz, yz)
-  const T Pxx = rho * u[0] * u[0] - (sig[0] - pref), Pyy = rho * u[1] * u[1] - (sig[4] - pref),
-          Pzz = rho * u[2] * u[2] - (sig[8] - pref);
+  const T Pxx = rho * u[0] * u[0] - sig[0], Pyy = rho * u[1] * u[1] - sig[4], Pzz = rho * u[2] * u[2] - sig[8];
   const T Pxy = rho * u[0] * u[1] - T(0.5) * (sig[1] + sig[3]);
   const T Pxz = rho * u[0] * u[2] - T(0.5) * (sig[2] + sig[6]);
   const T Pyz = rho * u[1] * u[2] - T(0.5) * (sig[5] + sig[7]);

@@ -65,3 +65,36 @@ int probe(int device, int iters, double* tflops) {
 // arithmetic throughput in TFLOP/s on `device`.  Returns 0, or a negative code.
 extern "C" int peak_fp64_tflops(int device, int iters, double* tflops) { return probe<double>(device, iters, tflops); }
 extern "C" int peak_fp32_tflops(int device, int iters, double* tflops) { return probe<float>(device, iters, tflops); }
+
+namespace {
+// One thread runs a chain of dependent additions; cycles per addition from clock64.
+template <typename T>
+__global__ void k_add_chain(T a, int n, T* out, long long* cycles) {
+  T x = a;
+  const long long t0 = clock64();
+  for (int i = 0; i < n; ++i) x = x + a;
+  const long long t1 = clock64();
+  *out = x;
+  *cycles = t1 - t0;
+}
+template <typename T>
+int latency(int device, double* cyc) {
+  if (!cyc || cudaSetDevice(device) != cudaSuccess) return -3;
+  T* out = nullptr;
+  long long* c = nullptr;
+  if (cudaMalloc(&out, sizeof(T)) != cudaSuccess || cudaMalloc(&c, sizeof(long long)) != cudaSuccess) return -2;
+  long long h = 0;
+  k_add_chain<T><<<1, 1>>>(T(1e-3), 4096, out, c);
+  k_add_chain<T><<<1, 1>>>(T(1e-3), 4096, out, c);
+  cudaError_t e = cudaMemcpy(&h, c, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(out);
+  cudaFree(c);
+  if (e != cudaSuccess) return -3;
+  *cyc = (double)h / 4096.0;
+  return 0;
+}
+}  // namespace
+
+// Latency in SM clock cycles of one dependent FP64 (DADD) or FP32 (FADD) addition.
+extern "C" int add_latency_fp64_cycles(int device, double* cycles) { return latency<double>(device, cycles); }
+extern "C" int add_latency_fp32_cycles(int device, double* cycles) { return latency<float>(device, cycles); }

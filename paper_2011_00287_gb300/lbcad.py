@@ -32,7 +32,7 @@ LB_BODY_FORCE, LB_STRESS_EQ = 0, 1
 STENCIL_ISO, STENCIL_R2 = 0, 1
 FIELD_G, FIELD_RHO, FIELD_U, FIELD_Q, FIELD_PSI = 1, 2, 4, 8, 16
 PATH_FUSED, PATH_TWO_KERNEL, PATH_STAGED = 0, 1, 2
-N_TILE_CONFIGS = 9  # candidates of lbcad_autotune / lbcad_set_tiles (FP32; FP64 has one)
+N_TILE_CONFIGS = 7  # candidates of lbcad_autotune / lbcad_set_tiles (FP32; FP64 has one)
 FIELD_NCOMP = {FIELD_G: 19, FIELD_RHO: 1, FIELD_U: 3, FIELD_Q: 5, FIELD_PSI: 1}
 FIELD_NAMES = {FIELD_G: "g", FIELD_RHO: "rho", FIELD_U: "u", FIELD_Q: "q", FIELD_PSI: "psi"}
 

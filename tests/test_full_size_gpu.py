@@ -155,14 +155,34 @@ def test_256cube_fp32_against_fp64_first_100_steps(lib_built):
     for k in ("q", "psi", "u"):
         errs[k] = _rel_l2(f32[k], f64[k])
     print("256^3 after 100 steps, FP32 vs FP64 rel L2:", errs, "rms |u| %.2e" % np.sqrt((f64["u"] ** 2).sum(0).mean()))
-    # Q and psi within 1e-5.  The populations (shifted) and the velocity are held to 1e-4
-    # (measured 1.2e-5 and 1.4e-5): 100 FP32 roundings of about 6e-8 each reach 6e-6 where
-    # they add up, and the trajectory amplifies them; the 100-step check of the R = 8 droplet
-    # against the oracle stays within 1e-5.
-    tol = {"g": 1e-4, "u": 1e-4, "q": 1e-5, "psi": 1e-5}
+    # What the FP32 storage alone costs: the FP64 step with Q and psi rounded to FP32 after every
+    # step (on the device), against the plain FP64 run.  Rounding u and the populations as well
+    # adds nothing measurable (32^3 and 128^3), so Q and psi carry it.  The FP32 path may add as
+    # much again through its arithmetic (measured ratios of its error to this one: 1.44-1.51).
+    import torch
+    sr = L.Simulation([shape], [L.default_params(shape, precision=L.FP64, **kw)], seed=1)
+    N = 256 ** 3
+    buf = torch.empty(sr.state_bytes(0), dtype=torch.uint8, device="cuda:0")
+    qpsi = buf.view(torch.float64)[19 * N:25 * N]
+    for _ in range(100):
+        sr.get_state(0, out=buf)
+        qpsi.copy_(qpsi.float().double())
+        torch.cuda.synchronize()  # the rounding runs on torch's stream, the library reads on its own
+        sr.set_state(0, buf)
+        sr.step(1)
+    fr = sr.get_fields(0)
+    sr.close()
+    del buf, qpsi
+    store = {"g": _rel_l2(_shifted(fr["g"]), _shifted(f64["g"]))}
+    for k in ("q", "psi", "u"):
+        store[k] = _rel_l2(fr[k], f64[k])
+    print("256^3 after 100 steps, FP64 with FP32-rounded Q and psi vs FP64 rel L2:", store)
+    # Q and psi within 1e-5.  The populations (shifted) and the velocity within 1e-5 or twice the
+    # storage-only error, whichever is larger.
     for k, e in errs.items():
-        assert e <= tol[k], errs
-    del f32, f64
+        tol = 1e-5 if k in ("q", "psi") else max(1e-5, 2.0 * store[k])
+        assert e <= tol, (k, errs, store)
+    del f32, f64, fr
     # windows of both runs, two steps by the oracle
     W, steps = 24, 2
     origins = _windows_of(shape, 64.0)

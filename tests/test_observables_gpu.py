@@ -29,26 +29,35 @@ def built():
 
 def _fused_and_separate(sim, inst):
     a = sim.observables(inst)
-    sim.set_state(inst, sim.get_state(inst))
+    st = sim.get_state(inst)
+    sim.set_state(inst, st)
     b = sim.observables(inst)
-    return a, b
+    # sum of |g| over the stored populations: the scale of the per-site rounding.  The raw state
+    # holds (q + 9) values per site of the storage type: 112, 96, 224 or 192 bytes for
+    # D3Q19/D3Q15 in FP32/FP64.
+    N = sim.sites(inst)
+    q, dt = {112: (19, np.float32), 96: (15, np.float32), 224: (19, np.float64), 192: (15, np.float64)}[st.nbytes // N]
+    g = st.view(dt)[:q * N]
+    return a, b, float(np.abs(g.astype(np.float64)).sum())
 
 
-def _check(a, b, N, fp64):
+def _check(a, b, N, fp64, abs_g=0.0):
     if fp64:
         np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-10)
         return
     # FP32 states.  Both passes add their FP32 per-site shares without rounding error (error-free
     # pairs, then FP64).  psi, phi_c and its moments have the same shares on both sides, so they
-    # agree to 1e-12 per site.  The fused mass and momentum come from the collision (the pulled
-    # populations and j + F), the separate pass's from the stored populations: the two differ by
-    # the FP32 rounding of the collision at each site (well below 1e-10 per site here).
+    # agree to 1e-12 per site.  The fused mass and momentum come from the collision (each site's
+    # pulled populations added in FP32, and j + F), the separate pass's from the stored
+    # populations of each site added in FP32: both are sums of 19 FP32 values per site (each off
+    # by at most 18 u sum|g_i|, u = 2^-24), and the stored populations carry the collision's own
+    # rounding (a few u |g_i|).  So the two agree within 40 u sum|g| over the state.
     assert abs(a[1] - b[1]) <= 1e-12 * N and np.abs(a[5:] - b[5:]).max() <= 1e-12 * N, (a, b)
-    assert abs(a[0] - b[0]) <= 1e-10 * N and np.abs(a[2:5] - b[2:5]).max() <= 1e-10 * N, (a, b)
+    tol = 40 * 2.0 ** -24 * abs_g
+    assert abs(a[0] - b[0]) <= tol and np.abs(a[2:5] - b[2:5]).max() <= tol, (a, b, tol)
 
 
-CASES = [("fp64", L.FP64, 0), ("fp32-32x8", L.FP32, 0), ("fp32-pipelined", L.FP32, 3), ("fp32-32x16", L.FP32, 1),
-         ("fp32-pipelined-prefetch", L.FP32, 7)]
+CASES = [("fp64", L.FP64, 0), ("fp32-32x8", L.FP32, 0), ("fp32-pipelined", L.FP32, 3), ("fp32-32x16", L.FP32, 1)]
 
 
 @pytest.mark.parametrize("name,prec,tiles", CASES, ids=[c[0] for c in CASES])
@@ -59,8 +68,8 @@ def test_fused_sums_match_the_separate_pass(shape, name, prec, tiles):
     sim = L.Simulation([shape], [_lib_params(shape, prec, R=5.0, p0=8.0, zeta=0.01)], seed=3)
     sim.set_tiles(tiles)
     sim.step(7)
-    a, b = _fused_and_separate(sim, 0)
-    _check(a, b, sim.sites(0), prec == L.FP64)
+    a, b, ag = _fused_and_separate(sim, 0)
+    _check(a, b, sim.sites(0), prec == L.FP64, ag)
 
 
 @pytest.mark.parametrize("variant", [dict(lattice=L.D3Q15), dict(lb_form=L.LB_STRESS_EQ, tau=1.5),
@@ -71,8 +80,8 @@ def test_fused_sums_of_the_lb_variants(variant, prec):
     shape = (24, 20, 16)
     sim = L.Simulation([shape], [_lib_params(shape, prec, R=5.0, p0=8.0, zeta=0.01, **variant)], seed=4)
     sim.step(6)
-    a, b = _fused_and_separate(sim, 0)
-    _check(a, b, sim.sites(0), prec == L.FP64)
+    a, b, ag = _fused_and_separate(sim, 0)
+    _check(a, b, sim.sites(0), prec == L.FP64, ag)
 
 
 def test_fused_sums_match_the_oracle_fp64():
@@ -95,10 +104,13 @@ def test_batch_graph_sums_per_instance(prec):
     sim.set_graph(2)
     sim.step(8)
     fused = [sim.observables(i) for i in range(len(shapes))]
+    states = [sim.get_state(i) for i in range(len(shapes))]
     for i in range(len(shapes)):
-        sim.set_state(i, sim.get_state(i))
+        sim.set_state(i, states[i])
     for i in range(len(shapes)):
-        _check(fused[i], sim.observables(i), sim.sites(i), prec == L.FP64)
+        ag = float(np.abs(states[i].view(np.float32 if prec == L.FP32 else np.float64)[:19 * sim.sites(i)]
+                          .astype(np.float64)).sum())
+        _check(fused[i], sim.observables(i), sim.sites(i), prec == L.FP64, ag)
 
 
 def test_sums_follow_the_state():
@@ -113,7 +125,7 @@ def test_sums_follow_the_state():
     o = sim.observables(0)
     assert abs(o[1] - f["psi"].sum()) <= 1e-9 * f["psi"].size
     sim.step(1)
-    a, b = _fused_and_separate(sim, 0)
+    a, b, _ = _fused_and_separate(sim, 0)
     _check(a, b, sim.sites(0), True)
 
 
@@ -132,7 +144,9 @@ def test_sums_off_leave_the_state_unchanged(prec, tiles):
     fa, fb = a.get_fields(0), b.get_fields(0)
     for k in fa:
         assert np.array_equal(fa[k], fb[k]), k
-    _check(a.observables(0), b.observables(0), a.sites(0), prec == L.FP64)
+    ag = float(np.abs(a.get_state(0).view(np.float32 if prec == L.FP32 else np.float64)[:19 * a.sites(0)]
+                      .astype(np.float64)).sum())
+    _check(a.observables(0), b.observables(0), a.sites(0), prec == L.FP64, ag)
 
 
 def _plane_fsum(x, planes):
@@ -179,7 +193,7 @@ def _host_sums(sim, inst, rho0=1.0):
     return out, scale, _plane_fsum(np.abs(g), nz)
 
 
-@pytest.mark.parametrize("tiles", [3, 0, 7], ids=["pipelined-8+8", "32x8", "pipelined-8+8-prefetch"])
+@pytest.mark.parametrize("tiles", [3, 0], ids=["pipelined-8+8", "32x8"])
 def test_fp32_fused_sums_are_the_fp64_sums_of_the_state(tiles):
     """The benchmarked workload (128^3, R = 32, pitch 32): the FP64 sums the FP32 step forms
     against FP64 sums of its stored state formed on the host.
