@@ -954,6 +954,260 @@ __global__ void __launch_bounds__(512, 1)
                   [&](int inst) { return SHIFT ? (double)D[inst].c.rho0 * (double)D[inst].N : 0.0; });
 }
 
+// ---------------------------------------------------------------- tiled order-parameter half
+// The order-parameter half of a sync-coupled or Heun step (after LaunchFused::step_lb), as
+// z-marching kernels on the tiles and work split of the fused step (32 x 8 columns, persistent
+// blocks): rings of planes with a halo of 1 in shared memory, filled by cp.async one plane
+// ahead, one barrier per plane, and the per-site functions of the staged path on them.
+//   k_op_tiled<STAGE>: STAGE 0 the update Q + R(Q) (Euler, sync), 1 the Heun predictor
+//     (rq = R(Q), qp = Q + rq), 2 the Heun corrector Q + (rq + R(qp))/2, R from gather_op and
+//     op_update with u of this step (sync) or of the previous one, H and mu of the scratch;
+//   k_fields_pred_tiled: H and mu of the predicted state qp (gather_fields, local_fields) into
+//     the sigma scratch, as k_fields<T, true> writes them.
+// Ring slots: planes z-1 .. z+2 (the last one arriving).
+template <typename T>
+struct OpTileGeom {
+  static constexpr int TX = 32, TY = 8, NT = TX * TY;
+  static constexpr int SW = TX + 2, SH = TY + 2, SP = SW * SH;
+  static constexpr int NSLOT = 4;
+  static constexpr int QSLOT = 6 * SP, USLOT = 3 * SP, MSLOT = SP;
+  static constexpr size_t op_bytes = (size_t)NSLOT * (QSLOT + USLOT + MSLOT) * sizeof(T) + (SW + SH) * sizeof(int);
+  static constexpr size_t fields_bytes = (size_t)NSLOT * QSLOT * sizeof(T) + (SW + SH) * sizeof(int);
+  static constexpr int LD = (SP + NT - 1) / NT;  // plane sites per thread
+};
+
+// Neighbour reads of gather_op from the tiles: Q/psi pairs, u, and mu (lane 1 of pair 4).
+template <typename T, int SW, int SP>
+struct SmemOpAcc {
+  const T* qpl[3];
+  const T* upl[3];
+  const T* mpl[3];
+  int sc;
+  __device__ __forceinline__ int at(int cx, int cy) const { return sc + cy * SW + cx; }
+  __device__ __forceinline__ Vec2<T> pair(int j, int cx, int cy, int cz) const {
+    return lds2(qpl[cz + 1] + qidx<SP>(2 * j, at(cx, cy)));
+  }
+  __device__ __forceinline__ Vec2<T> spair(int, int cx, int cy, int cz) const {
+    return Vec2<T>{T(0), mpl[cz + 1][at(cx, cy)]};
+  }
+  __device__ __forceinline__ Vec2<T> upair(int cx, int cy, int cz) const { return lds2(upl[cz + 1] + 2 * at(cx, cy)); }
+  __device__ __forceinline__ T u(int a, int cx, int cy, int cz) const { return upl[cz + 1][uidx<SP>(a, at(cx, cy))]; }
+};
+
+// The column segment [zb, ze) of tile tl, plane by plane, for both tiled kernels: load(p, slot,
+// site k, global offset) copies plane p's fields of tile site k; work(z, slots of z-1, z, z+1)
+// computes the interior site of this thread.
+template <class G, class Load, class Work>
+__device__ __forceinline__ void op_tile_march(const FusedTile& tl, int nx, int ny, int nz, int zb, int ze,
+                                              int* xmap, int* ymap, const Load& load, const Work& work) {
+  const int tid = threadIdx.x;
+  __syncthreads();  // the previous segment is done with the tiles
+  for (int k = tid; k < G::SW; k += G::NT) xmap[k] = wrapmod(tl.x0 + k - 1, nx);
+  for (int k = tid; k < G::SH; k += G::NT) ymap[k] = wrapmod(tl.y0 + k - 1, ny) * nx;
+  __syncthreads();
+  int off[G::LD];
+#pragma unroll
+  for (int r = 0; r < G::LD; ++r) {
+    const int k = tid + r * G::NT;
+    off[r] = k < G::SP ? ymap[k / G::SW] + xmap[k % G::SW] : 0;
+  }
+  const long long plane = (long long)nx * ny;
+  auto issue = [&](int p) {
+    const long long gz = (long long)wrap_plane(p, nz) * plane;
+    const int slot = (p + 4 * G::NSLOT) % G::NSLOT;
+#pragma unroll
+    for (int r = 0; r < G::LD; ++r) {
+      const int k = tid + r * G::NT;
+      if (k < G::SP) load(slot, k, gz + off[r]);
+    }
+  };
+  issue(zb - 1);
+  issue(zb);
+  issue(zb + 1);
+  cp_async_commit_wait_all();
+  __syncthreads();
+  for (int z = zb; z < ze; ++z) {
+    issue(z + 2);
+    work(z, (z - 1 + 4 * G::NSLOT) % G::NSLOT, z % G::NSLOT, (z + 1) % G::NSLOT);
+    cp_async_commit_wait_all();
+    __syncthreads();
+  }
+}
+
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(256) k_op_tiled(const InstDesc<T>* __restrict__ D, const FusedTile* __restrict__ tiles,
+                                                  int ntiles, long long total, int sync) {
+  using G = OpTileGeom<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sQ = reinterpret_cast<T*>(smem_raw);
+  T* sU = sQ + G::NSLOT * G::QSLOT;
+  T* sM = sU + G::NSLOT * G::USLOT;
+  int* xmap = reinterpret_cast<int*>(sM + G::NSLOT * G::MSLOT);
+  int* ymap = xmap + G::SW;
+  const int tid = threadIdx.x, tx = tid % G::TX, ty = tid / G::TX;
+  const long long begin = (total * blockIdx.x) / gridDim.x;
+  const long long end = (total * (blockIdx.x + 1)) / gridDim.x;
+  for (long long it = begin; it < end;) {
+    int lo = 0, hi = ntiles - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tiles[mid].start <= it) lo = mid; else hi = mid - 1;
+    }
+    const FusedTile tl = tiles[lo];
+    const InstDesc<T>& I = D[tl.inst];
+    const int nx = I.nx, ny = I.ny, nz = I.nz;
+    const long long N = I.N;
+    const int zb = (int)(it - tl.start);
+    const long long seg_end = end < tl.start + tl.nz ? end : tl.start + tl.nz;
+    const int ze = (int)(seg_end - tl.start);
+    it = seg_end;
+    const T* qsrc = STAGE == 2 ? I.qp : I.q_in;
+    const T* psrc = STAGE == 2 ? I.qp + 5 * N : I.psi_in;
+    const T* usrc = sync ? I.u_out : I.u_in;
+    const T* msrc = STAGE == 2 ? I.sig + 5 * N : I.mu;
+    const T* hsrc = STAGE == 2 ? I.sig : I.H;
+    auto load = [&](int slot, int k, long long gs) {
+      T* dq = sQ + slot * G::QSLOT;
+#pragma unroll
+      for (int f = 0; f < 5; ++f) cp_async_elem(dq + qidx<G::SP>(f, k), qsrc + f * N + gs);
+      cp_async_elem(dq + qidx<G::SP>(5, k), psrc + gs);
+      T* du = sU + slot * G::USLOT;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) cp_async_elem(du + uidx<G::SP>(a, k), usrc + a * N + gs);
+      cp_async_elem(sM + slot * G::MSLOT + k, msrc + gs);
+    };
+    auto work = [&](int z, int s0, int s1, int s2) {
+      if (tl.x0 + tx >= nx || tl.y0 + ty >= ny) return;
+      SmemOpAcc<T, G::SW, G::SP> acc;
+      const int sl[3] = {s0, s1, s2};
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        acc.qpl[j] = sQ + sl[j] * G::QSLOT;
+        acc.upl[j] = sU + sl[j] * G::USLOT;
+        acc.mpl[j] = sM + sl[j] * G::MSLOT;
+      }
+      acc.sc = (ty + 1) * G::SW + (tx + 1);
+      T lapmu, Wg[3][3], q0[5], qf[6][5], p0, pf[6], u0[3], uf[6];
+      gather_op<T>(acc, lapmu, Wg, q0, qf, p0, pf, u0, uf);
+      const long long s = (long long)z * nx * ny + (long long)(tl.y0 + ty) * nx + (tl.x0 + tx);
+      T Hs[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) Hs[k] = __ldg(hsrc + k * N + s);
+      T qn[5], pn;
+      if constexpr (STAGE == 0) {
+        op_update<T, false>(I.c, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hs, qn, pn);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) st_out(I.q_out + k * N + s, qn[k]);
+        st_out(I.psi_out + s, pn);
+      } else if constexpr (STAGE == 1) {
+        op_update<T, true>(I.c, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hs, qn, pn);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          I.rq[k * N + s] = qn[k];
+          I.qp[k * N + s] = q0[k] + qn[k];
+        }
+        I.rq[5 * N + s] = pn;
+        I.qp[5 * N + s] = p0 + pn;
+      } else {
+        op_update<T, true>(I.c, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hs, qn, pn);
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+          st_out(I.q_out + k * N + s, I.q_in[k * N + s] + T(0.5) * (I.rq[k * N + s] + qn[k]));
+        st_out(I.psi_out + s, I.psi_in[s] + T(0.5) * (I.rq[5 * N + s] + pn));
+      }
+    };
+    op_tile_march<G>(tl, nx, ny, nz, zb, ze, xmap, ymap, load, work);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fields_pred_tiled(const InstDesc<T>* __restrict__ D,
+                                                           const FusedTile* __restrict__ tiles, int ntiles,
+                                                           long long total) {
+  using G = OpTileGeom<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sQ = reinterpret_cast<T*>(smem_raw);
+  int* xmap = reinterpret_cast<int*>(sQ + G::NSLOT * G::QSLOT);
+  int* ymap = xmap + G::SW;
+  const int tid = threadIdx.x, tx = tid % G::TX, ty = tid / G::TX;
+  const long long begin = (total * blockIdx.x) / gridDim.x;
+  const long long end = (total * (blockIdx.x + 1)) / gridDim.x;
+  for (long long it = begin; it < end;) {
+    int lo = 0, hi = ntiles - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tiles[mid].start <= it) lo = mid; else hi = mid - 1;
+    }
+    const FusedTile tl = tiles[lo];
+    const InstDesc<T>& I = D[tl.inst];
+    const int nx = I.nx, ny = I.ny, nz = I.nz;
+    const long long N = I.N;
+    const int zb = (int)(it - tl.start);
+    const long long seg_end = end < tl.start + tl.nz ? end : tl.start + tl.nz;
+    const int ze = (int)(seg_end - tl.start);
+    it = seg_end;
+    const T* qsrc = I.qp;
+    auto load = [&](int slot, int k, long long gs) {
+      T* dq = sQ + slot * G::QSLOT;
+#pragma unroll
+      for (int f = 0; f < 6; ++f) cp_async_elem(dq + qidx<G::SP>(f, k), qsrc + f * N + gs);
+    };
+    auto work = [&](int z, int s0, int s1, int s2) {
+      if (tl.x0 + tx >= nx || tl.y0 + ty >= ny) return;
+      SmemFieldsAcc<T, G::SW, G::SP> acc;
+      acc.pl[0] = sQ + s0 * G::QSLOT;
+      acc.pl[1] = sQ + s1 * G::QSLOT;
+      acc.pl[2] = sQ + s2 * G::QSLOT;
+      acc.qc = (ty + 1) * G::SW + (tx + 1);
+      T q0[5], p0, dq[3][5], lapq[5], dp[3], lapp, hp[6];
+      gather_fields<T>(acc, q0, p0, dq, lapq, dp, lapp, hp);
+      T H[5], sig[9], mu;
+      local_fields<T>(I.c, q0, p0, dq, lapq, dp, lapp, hp, H, mu, sig);
+      const long long s = (long long)z * nx * ny + (long long)(tl.y0 + ty) * nx + (tl.x0 + tx);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) I.sig[k * N + s] = H[k];
+      I.sig[5 * N + s] = mu;
+    };
+    op_tile_march<G>(tl, nx, ny, nz, zb, ze, xmap, ymap, load, work);
+  }
+}
+
+// Grid of a tiled order-parameter kernel: every SM times the blocks that fit, at most the units.
+template <class K>
+int op_tiled_grid(K kernel, size_t smem, long long total) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 256, smem);
+  long long g = (long long)sms * (per > 0 ? per : 1);
+  return (int)(g < total ? g : total);
+}
+
+template <typename T, bool SHIFT>
+cudaError_t LaunchFused<T, SHIFT>::op_tiled(bool heun, bool sync, const InstDesc<T>* d, const FusedTile* t, int nt,
+                                            long long total, cudaStream_t s) {
+  using G = OpTileGeom<T>;
+  // the shared-memory limits are attributes of the functions on the current device (idempotent)
+  cudaError_t e = cudaFuncSetAttribute(k_op_tiled<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::op_bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_op_tiled<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::op_bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_op_tiled<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::op_bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fields_pred_tiled<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::fields_bytes);
+  if (e != cudaSuccess) return e;
+  const int go = op_tiled_grid(k_op_tiled<T, 0>, G::op_bytes, total);
+  if (!heun) {
+    k_op_tiled<T, 0><<<go, 256, G::op_bytes, s>>>(d, t, nt, total, sync ? 1 : 0);
+    return cudaGetLastError();
+  }
+  const int gf = op_tiled_grid(k_fields_pred_tiled<T>, G::fields_bytes, total);
+  k_op_tiled<T, 1><<<go, 256, G::op_bytes, s>>>(d, t, nt, total, sync ? 1 : 0);
+  k_fields_pred_tiled<T><<<gf, 256, G::fields_bytes, s>>>(d, t, nt, total);
+  k_op_tiled<T, 2><<<go, 256, G::op_bytes, s>>>(d, t, nt, total, sync ? 1 : 0);
+  return cudaGetLastError();
+}
+
 template <typename T, bool SHIFT, int TX, int TY, class V, int FORM>
 cudaError_t launch_cfg(const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles, long long total, int grid,
                        const FusedObs& ob, bool obs, cudaStream_t s) {

@@ -93,13 +93,6 @@ struct Launch {
   // stencil: 0 = isotropic D3Q19 finite differences, 1 = fourth-order radius-2 differences.
   static cudaError_t staged(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, bool heun,
                             bool sync, int vel, int form, int stencil, cudaStream_t s);
-  // The order-parameter update with the velocity of this step (u_out) and H, mu from the
-  // scratch: the second half of a sync-coupled step after LaunchFused::step_lb.
-  static cudaError_t op_sync(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, cudaStream_t s);
-  // Heun after LaunchFused::step_lb: predictor, H and mu at the predicted Q, psi, corrector
-  // (advecting with u of this step when sync, else with u of the previous step).
-  static cudaError_t op_heun(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, bool sync,
-                             cudaStream_t s);
   static cudaError_t get_fields(const InstDesc<T>& I, uint32_t mask, double* dst, cudaStream_t s);
   static cudaError_t set_fields(const InstDesc<T>& I, uint32_t mask, const double* src, T* g_target,
                                 T* q_target, T* psi_target, T* u_target, cudaStream_t s);
@@ -125,10 +118,10 @@ constexpr int kFusedPlain = 0, kFusedSums = 1, kFusedLbOnly = 2;
 
 // The FP64 conserved and centroid sums of the fused step (a6).  Each column segment a block
 // works on has a slot of 12 partial sums (block b, segment j of the block: slot b * maxseg + j);
-// slot_inst[slot] is its instance (-1: unused).  The block that fills the last slot of an
-// instance (cnt counts them; the kernel resets it) sums the instance's slots, in slot order,
-// into latest[inst][12]: mass, sum psi, momentum (3), sum phi_c cos (3), sum phi_c sin (3),
-// sum phi_c.
+// slot_inst[slot] is its instance (-1: unused).  At the end of the kernel each block counts its
+// slots on their instances (cnt; the kernel resets it), and the block whose count completes an
+// instance sums the instance's slots in a fixed order into latest[inst][12]: mass, sum psi,
+// momentum (3), sum phi_c cos (3), sum phi_c sin (3), sum phi_c.
 struct FusedObs {
   double* slots;
   const int* slot_inst;
@@ -151,11 +144,15 @@ struct LaunchFused {
   static cudaError_t step(int variant, int cfg_index, const InstDesc<T>* d_desc, const FusedTile* tiles,
                           int ntiles, long long total, int grid, const FusedObs& ob, bool obs, cudaStream_t s);
   // Sync coupling or Heun: the first half of the step (force, pull, collision, u of this step;
-  // H and mu of every site into the scratch), on tile shape sync_config(); Launch::op_sync or
-  // Launch::op_heun finishes it.
+  // H and mu of every site into the scratch), on tile shape sync_config(); op_tiled finishes it.
   static int sync_config();
   static cudaError_t step_lb(int variant, const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles,
                              long long total, int grid, const FusedObs& ob, cudaStream_t s);
+  // The order-parameter half after step_lb as tiled z-marching kernels on the same tiles (32 x 8,
+  // the tile shape of sync_config()): the update (Euler), or predictor, fields at the predicted
+  // state and corrector (Heun); sync advects with u of this step.
+  static cudaError_t op_tiled(bool heun, bool sync, const InstDesc<T>* d_desc, const FusedTile* tiles, int ntiles,
+                              long long total, cudaStream_t s);
 };
 
 // Buffers of one reverse step of the adjoint (lbcad_adjoint.cuh).

@@ -1236,23 +1236,6 @@ cudaError_t Launch<T, SHIFT>::staged(const InstDesc<T>* d_desc, int ninst, long 
   return staged_st<T, SHIFT, 0>(d_desc, ninst, g, bs, heun, sync, vel, form, s);
 }
 
-template <typename T, bool SHIFT>
-cudaError_t Launch<T, SHIFT>::op_sync(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs,
-                                      cudaStream_t s) {
-  k_op<T, 0, 0><<<(unsigned)total_blocks, bs, 0, s>>>(d_desc, ninst, 1);
-  return cudaGetLastError();
-}
-
-template <typename T, bool SHIFT>
-cudaError_t Launch<T, SHIFT>::op_heun(const InstDesc<T>* d_desc, int ninst, long long total_blocks, int bs, bool sync,
-                                      cudaStream_t s) {
-  const unsigned g = (unsigned)total_blocks;
-  k_op<T, 1, 0><<<g, bs, 0, s>>>(d_desc, ninst, sync ? 1 : 0);
-  k_fields<T, true, 0><<<g, bs, 0, s>>>(d_desc, ninst);
-  k_op<T, 2, 0><<<g, bs, 0, s>>>(d_desc, ninst, sync ? 1 : 0);
-  return cudaGetLastError();
-}
-
 inline unsigned grid_for(long long N, int bs) {
   long long g = (N + bs - 1) / bs;
   if (g > 152 * 16) g = 152 * 16;

@@ -546,20 +546,15 @@ int launch_steps(lbcad_ctx* c, int64_t n) {
     cudaError_t e;
     const bool heun = c->integrator == LBCAD_HEUN, sync = c->coupling == LBCAD_SYNC;
     if (c->path == LBCAD_PATH_FUSED && c->sync_split()) {
+      // the LB half in the fused kernel, then the order-parameter half as tiled kernels on the
+      // same tiles (Euler: the update; Heun: predictor, fields at the predicted state, corrector)
       e = launch_fused_lb(c, par);
-      const int ni = (int)c->inst.size();
-      if (e == cudaSuccess && heun)
+      if (e == cudaSuccess)
         e = (c->prec == LBCAD_FP64)
-                ? Launch<double, false>::op_heun((const InstDesc<double>*)c->desc[par], ni, c->total_blocks,
-                                                 kStepBlock, sync, c->stream)
-                : Launch<float, true>::op_heun((const InstDesc<float>*)c->desc[par], ni, c->total_blocks, kStepBlock,
-                                               sync, c->stream);
-      else if (e == cudaSuccess)
-        e = (c->prec == LBCAD_FP64)
-                ? Launch<double, false>::op_sync((const InstDesc<double>*)c->desc[par], ni, c->total_blocks,
-                                                 kStepBlock, c->stream)
-                : Launch<float, true>::op_sync((const InstDesc<float>*)c->desc[par], ni, c->total_blocks, kStepBlock,
-                                               c->stream);
+                ? LaunchFused<double, false>::op_tiled(heun, sync, (const InstDesc<double>*)c->desc[par], c->tiles,
+                                                       c->ntiles, c->fused_total, c->stream)
+                : LaunchFused<float, true>::op_tiled(heun, sync, (const InstDesc<float>*)c->desc[par], c->tiles,
+                                                     c->ntiles, c->fused_total, c->stream);
     } else if (c->path == LBCAD_PATH_FUSED) {
       e = launch_fused(c, par);
     } else if (c->path == LBCAD_PATH_STAGED) {
