@@ -964,14 +964,22 @@ __global__ void __launch_bounds__(512, 1)
 //     op_update with u of this step (sync) or of the previous one, H and mu of the scratch;
 //   k_fields_pred_tiled: H and mu of the predicted state qp (gather_fields, local_fields) into
 //     the sigma scratch, as k_fields<T, true> writes them.
-// Ring slots: planes z-1 .. z+2 (the last one arriving).
+// Ring slots: planes z-1 .. z+2 (the last one arriving).  The values a site reads only at
+// itself (H, and in the corrector R(Q) at t and Q, psi at t) arrive the same way, one plane
+// ahead, into two slots by plane parity: read from global memory after the stencils, their
+// latency stood between the update and the plane barrier.
 template <typename T>
 struct OpTileGeom {
   static constexpr int TX = 32, TY = 8, NT = TX * TY;
   static constexpr int SW = TX + 2, SH = TY + 2, SP = SW * SH;
   static constexpr int NSLOT = 4;
   static constexpr int QSLOT = 6 * SP, USLOT = 3 * SP, MSLOT = SP;
-  static constexpr size_t op_bytes = (size_t)NSLOT * (QSLOT + USLOT + MSLOT) * sizeof(T) + (SW + SH) * sizeof(int);
+  __host__ __device__ static constexpr int NSITE(int stage) { return stage == 2 ? 17 : 5; }  // H, rq, Q, psi
+  static constexpr size_t site_off = ((size_t)NSLOT * (QSLOT + USLOT + MSLOT) * sizeof(T) + 15) / 16 * 16;
+  __host__ __device__ static constexpr size_t maps_off(int stage) {
+    return site_off + (size_t)2 * NSITE(stage) * NT * sizeof(T);
+  }
+  __host__ __device__ static constexpr size_t op_bytes(int stage) { return maps_off(stage) + (SW + SH) * sizeof(int); }
   static constexpr size_t fields_bytes = (size_t)NSLOT * QSLOT * sizeof(T) + (SW + SH) * sizeof(int);
   static constexpr int LD = (SP + NT - 1) / NT;  // plane sites per thread
 };
@@ -994,12 +1002,14 @@ struct SmemOpAcc {
   __device__ __forceinline__ T u(int a, int cx, int cy, int cz) const { return upl[cz + 1][uidx<SP>(a, at(cx, cy))]; }
 };
 
-// The column segment [zb, ze) of tile tl, plane by plane, for both tiled kernels: load(p, slot,
-// site k, global offset) copies plane p's fields of tile site k; work(z, slots of z-1, z, z+1)
-// computes the interior site of this thread.
-template <class G, class Load, class Work>
+// The column segment [zb, ze) of tile tl, plane by plane, for both tiled kernels: load(slot,
+// site k, global offset) copies a plane's fields of tile site k; load_site(parity, global offset)
+// copies the site-local values of this thread's interior site of a plane (called only for a
+// site inside the lattice); work(z, slots of z-1, z, z+1) computes that site.
+template <class G, class Load, class LoadSite, class Work>
 __device__ __forceinline__ void op_tile_march(const FusedTile& tl, int nx, int ny, int nz, int zb, int ze,
-                                              int* xmap, int* ymap, const Load& load, const Work& work) {
+                                              int* xmap, int* ymap, const Load& load, const LoadSite& load_site,
+                                              const Work& work) {
   const int tid = threadIdx.x;
   __syncthreads();  // the previous segment is done with the tiles
   for (int k = tid; k < G::SW; k += G::NT) xmap[k] = wrapmod(tl.x0 + k - 1, nx);
@@ -1021,13 +1031,21 @@ __device__ __forceinline__ void op_tile_march(const FusedTile& tl, int nx, int n
       if (k < G::SP) load(slot, k, gz + off[r]);
     }
   };
+  const int tx = tid % G::TX, ty = tid / G::TX;
+  const bool inside = tl.x0 + tx < nx && tl.y0 + ty < ny;
+  const long long soff = (long long)(tl.y0 + ty) * nx + (tl.x0 + tx);
+  auto issue_site = [&](int p) {
+    if (inside) load_site(p & 1, (long long)p * plane + soff);
+  };
   issue(zb - 1);
   issue(zb);
   issue(zb + 1);
+  issue_site(zb);
   cp_async_commit_wait_all();
   __syncthreads();
   for (int z = zb; z < ze; ++z) {
     issue(z + 2);
+    if (z + 1 < ze) issue_site(z + 1);
     work(z, (z - 1 + 4 * G::NSLOT) % G::NSLOT, z % G::NSLOT, (z + 1) % G::NSLOT);
     cp_async_commit_wait_all();
     __syncthreads();
@@ -1039,10 +1057,12 @@ __global__ void __launch_bounds__(256) k_op_tiled(const InstDesc<T>* __restrict_
                                                   int ntiles, long long total, int sync) {
   using G = OpTileGeom<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NSV = G::NSITE(STAGE);
   T* sQ = reinterpret_cast<T*>(smem_raw);
   T* sU = sQ + G::NSLOT * G::QSLOT;
   T* sM = sU + G::NSLOT * G::USLOT;
-  int* xmap = reinterpret_cast<int*>(sM + G::NSLOT * G::MSLOT);
+  T* sI = reinterpret_cast<T*>(smem_raw + G::site_off);  // site-local values [2][NSV][NT]
+  int* xmap = reinterpret_cast<int*>(smem_raw + G::maps_off(STAGE));
   int* ymap = xmap + G::SW;
   const int tid = threadIdx.x, tx = tid % G::TX, ty = tid / G::TX;
   const long long begin = (total * blockIdx.x) / gridDim.x;
@@ -1076,8 +1096,21 @@ __global__ void __launch_bounds__(256) k_op_tiled(const InstDesc<T>* __restrict_
       for (int a = 0; a < 3; ++a) cp_async_elem(du + uidx<G::SP>(a, k), usrc + a * N + gs);
       cp_async_elem(sM + slot * G::MSLOT + k, msrc + gs);
     };
+    auto load_site = [&](int par, long long gs) {
+      T* d = sI + par * NSV * G::NT + tid;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) cp_async_elem(d + k * G::NT, hsrc + k * N + gs);
+      if constexpr (STAGE == 2) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) cp_async_elem(d + (5 + k) * G::NT, I.rq + k * N + gs);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) cp_async_elem(d + (11 + k) * G::NT, I.q_in + k * N + gs);
+        cp_async_elem(d + 16 * G::NT, I.psi_in + gs);
+      }
+    };
     auto work = [&](int z, int s0, int s1, int s2) {
       if (tl.x0 + tx >= nx || tl.y0 + ty >= ny) return;
+      const T* si = sI + (z & 1) * NSV * G::NT + tid;
       SmemOpAcc<T, G::SW, G::SP> acc;
       const int sl[3] = {s0, s1, s2};
 #pragma unroll
@@ -1092,7 +1125,7 @@ __global__ void __launch_bounds__(256) k_op_tiled(const InstDesc<T>* __restrict_
       const long long s = (long long)z * nx * ny + (long long)(tl.y0 + ty) * nx + (tl.x0 + tx);
       T Hs[5];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) Hs[k] = __ldg(hsrc + k * N + s);
+      for (int k = 0; k < 5; ++k) Hs[k] = si[k * G::NT];
       T qn[5], pn;
       if constexpr (STAGE == 0) {
         op_update<T, false>(I.c, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hs, qn, pn);
@@ -1112,11 +1145,11 @@ __global__ void __launch_bounds__(256) k_op_tiled(const InstDesc<T>* __restrict_
         op_update<T, true>(I.c, lapmu, Wg, q0, qf, p0, pf, u0, uf, Hs, qn, pn);
 #pragma unroll
         for (int k = 0; k < 5; ++k)
-          st_out(I.q_out + k * N + s, I.q_in[k * N + s] + T(0.5) * (I.rq[k * N + s] + qn[k]));
-        st_out(I.psi_out + s, I.psi_in[s] + T(0.5) * (I.rq[5 * N + s] + pn));
+          st_out(I.q_out + k * N + s, si[(11 + k) * G::NT] + T(0.5) * (si[(5 + k) * G::NT] + qn[k]));
+        st_out(I.psi_out + s, si[16 * G::NT] + T(0.5) * (si[10 * G::NT] + pn));
       }
     };
-    op_tile_march<G>(tl, nx, ny, nz, zb, ze, xmap, ymap, load, work);
+    op_tile_march<G>(tl, nx, ny, nz, zb, ze, xmap, ymap, load, load_site, work);
   }
 }
 
@@ -1168,7 +1201,7 @@ __global__ void __launch_bounds__(256) k_fields_pred_tiled(const InstDesc<T>* __
       for (int k = 0; k < 5; ++k) I.sig[k * N + s] = H[k];
       I.sig[5 * N + s] = mu;
     };
-    op_tile_march<G>(tl, nx, ny, nz, zb, ze, xmap, ymap, load, work);
+    op_tile_march<G>(tl, nx, ny, nz, zb, ze, xmap, ymap, load, [](int, long long) {}, work);
   }
 }
 
@@ -1188,23 +1221,26 @@ cudaError_t LaunchFused<T, SHIFT>::op_tiled(bool heun, bool sync, const InstDesc
                                             long long total, cudaStream_t s) {
   using G = OpTileGeom<T>;
   // the shared-memory limits are attributes of the functions on the current device (idempotent)
-  cudaError_t e = cudaFuncSetAttribute(k_op_tiled<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::op_bytes);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_op_tiled<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::op_bytes(0));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_op_tiled<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::op_bytes);
+    e = cudaFuncSetAttribute(k_op_tiled<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::op_bytes(1));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_op_tiled<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::op_bytes);
+    e = cudaFuncSetAttribute(k_op_tiled<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::op_bytes(2));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_fields_pred_tiled<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::fields_bytes);
   if (e != cudaSuccess) return e;
-  const int go = op_tiled_grid(k_op_tiled<T, 0>, G::op_bytes, total);
   if (!heun) {
-    k_op_tiled<T, 0><<<go, 256, G::op_bytes, s>>>(d, t, nt, total, sync ? 1 : 0);
+    const int g0 = op_tiled_grid(k_op_tiled<T, 0>, G::op_bytes(0), total);
+    k_op_tiled<T, 0><<<g0, 256, G::op_bytes(0), s>>>(d, t, nt, total, sync ? 1 : 0);
     return cudaGetLastError();
   }
+  const int g1 = op_tiled_grid(k_op_tiled<T, 1>, G::op_bytes(1), total);
   const int gf = op_tiled_grid(k_fields_pred_tiled<T>, G::fields_bytes, total);
-  k_op_tiled<T, 1><<<go, 256, G::op_bytes, s>>>(d, t, nt, total, sync ? 1 : 0);
+  const int g2 = op_tiled_grid(k_op_tiled<T, 2>, G::op_bytes(2), total);
+  k_op_tiled<T, 1><<<g1, 256, G::op_bytes(1), s>>>(d, t, nt, total, sync ? 1 : 0);
   k_fields_pred_tiled<T><<<gf, 256, G::fields_bytes, s>>>(d, t, nt, total);
-  k_op_tiled<T, 2><<<go, 256, G::op_bytes, s>>>(d, t, nt, total, sync ? 1 : 0);
+  k_op_tiled<T, 2><<<g2, 256, G::op_bytes(2), s>>>(d, t, nt, total, sync ? 1 : 0);
   return cudaGetLastError();
 }
 
