@@ -253,9 +253,11 @@ int lbcad_set_state(lbcad_ctx* c, int32_t inst, const void* src, size_t bytes, i
  * step (per-site vector-Jacobian products by hand-written reverse sweeps through the
  * step's own arithmetic).  Writes dJ/dzeta and dJ/dq0 (accumulated in FP64; q0 enters through H and
  * sigma, the initial Q held fixed), dJ/dQ(t0) for the five stored Q components
- * ([5][z][y][x], host FP64, may be NULL) and J itself.  Device memory grows by
- * (ceil(nsteps/ckpt_every) + ckpt_every + 2) states plus 154 values per site, owned by the
- * context until lbcad_destroy.  The paper has no adjoint; this is the differentiation form
+ * ([5][z][y][x], host FP64, may be NULL) and J itself.  Device memory: (ceil(nsteps /
+ * ckpt_every) + ckpt_every + 2) states of 28 values per site, plus 15 values per site for
+ * each of the ckpt_every states of a segment (their sigma, mu and H, computed once in the
+ * replay) and 139 values per site of work; owned by the context until lbcad_destroy and
+ * reused by later calls that fit in them.  The paper has no adjoint; this is the differentiation form
  * of the step (gradient of the droplet's drift with respect to activity, chirality and
  * the initial order). */
 int lbcad_adjoint(lbcad_ctx* c, int64_t nsteps, int32_t ckpt_every, double* dJ_dzeta, double* dJ_dq0,

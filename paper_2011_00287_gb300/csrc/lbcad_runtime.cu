@@ -99,6 +99,9 @@ struct lbcad_ctx {
   bool observe = true;     // fused steps form the a6 sums (lbcad_set_observe)
   bool obs_valid = false;
   void* adj_lam = nullptr;  // cotangent of the initial state of the last lbcad_adjoint
+  // buffers of lbcad_adjoint, kept for the next call (reused when large enough)
+  void* adj_buf[8] = {};
+  size_t adj_bytes[8] = {};
   std::string err;
   size_t elem() const { return prec == LBCAD_FP64 ? sizeof(double) : sizeof(float); }
   // the radius-2 stencils run on the staged path only
@@ -137,6 +140,18 @@ void* dev_alloc(lbcad_ctx* c, size_t bytes) {
     p = nullptr;
   }
   if (p) c->allocs.push_back(p);
+  return p;
+}
+
+// Buffer i of lbcad_adjoint: the one of an earlier call if it is large enough, else a new one
+// (the old one stays with the context until it is destroyed).
+void* adj_buffer(lbcad_ctx* c, int i, size_t bytes) {
+  if (c->adj_buf[i] && c->adj_bytes[i] >= bytes) return c->adj_buf[i];
+  void* p = dev_alloc(c, bytes);
+  if (p) {
+    c->adj_buf[i] = p;
+    c->adj_bytes[i] = bytes;
+  }
   return p;
 }
 
@@ -948,21 +963,21 @@ int adjoint_impl(lbcad_ctx* c, int64_t nsteps, int k, double* dzeta, double* dq0
   const long long N = I.N;
   const int S = (int)((nsteps + k - 1) / k);
   const size_t st = 28 * (size_t)N;  // elements of one stored state
-  // buffers (allocated per call through the context's allocator; released at destroy)
-  T* ck = (T*)dev_alloc(c, (size_t)S * st * sizeof(T));
-  T* seg = (T*)dev_alloc(c, (size_t)k * st * sizeof(T));
-  T* lam = (T*)dev_alloc(c, 2 * st * sizeof(T));
-  T* work = (T*)dev_alloc(c, (88 + 36 + 15 + 15) * (size_t)N * sizeof(T));
+  const size_t fs = 15 * (size_t)N;  // elements of one state's sigma (9), mu, H (5)
+  // buffers through the context's allocator, kept for the next call
+  c->adj_lam = nullptr;
+  T* ck = (T*)adj_buffer(c, 0, (size_t)S * st * sizeof(T));
+  T* seg = (T*)adj_buffer(c, 1, (size_t)k * st * sizeof(T));
+  T* lam = (T*)adj_buffer(c, 2, 2 * st * sizeof(T));
+  T* work = (T*)adj_buffer(c, 3, (88 + 36 + 15) * (size_t)N * sizeof(T));
+  T* fl = (T*)adj_buffer(c, 4, (size_t)k * fs * sizeof(T));
   const int nb = LaunchAdj<T, SHIFT>::blocks(N);
-  double* pg = (double*)dev_alloc(c, (2 * (size_t)nb + 2) * sizeof(double));
-  InstDesc<T>* dd = (InstDesc<T>*)dev_alloc(c, (size_t)k * sizeof(InstDesc<T>));
-  if (!ck || !seg || !lam || !work || !pg || !dd) return fail(c, LBCAD_E_OOM, "adjoint buffers");
+  double* pg = (double*)adj_buffer(c, 5, (2 * (size_t)nb + 2) * sizeof(double));
+  InstDesc<T>* dd = (InstDesc<T>*)adj_buffer(c, 6, (size_t)k * sizeof(InstDesc<T>));
+  if (!ck || !seg || !lam || !work || !fl || !pg || !dd) return fail(c, LBCAD_E_OOM, "adjoint buffers");
   T* A = work;
   T* Bf = A + 88 * N;
   T* ls = Bf + 36 * N;
-  T* sig = ls + 15 * N;
-  T* mu = sig + 9 * N;
-  T* H = mu + N;
   double* total = pg + 2 * nb;
   CK(c, cudaMemsetAsync(total, 0, 2 * sizeof(double), c->stream));
 
@@ -1009,10 +1024,13 @@ int adjoint_impl(lbcad_ctx* c, int64_t nsteps, int k, double* dzeta, double* dq0
     const int len = (int)std::min<int64_t>(k, nsteps - (int64_t)sgi * k);
     // replay the segment: states 0 .. len-1 of this segment into seg (state 0 = checkpoint)
     CK(c, cudaMemcpyAsync(seg, ck + (size_t)sgi * st, st * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+    // state j's sigma, mu, H go to its own slice of fl: the replay step that leaves state j
+    // computes them, and its reverse step reads them there
     for (int j = 0; j < len; ++j) {
       const StateBuf<T> in = state_at<T>(seg + (size_t)j * st, N);
       const StateBuf<T> out = state_at<T>(seg + (size_t)(j + 1 < len ? j + 1 : j) * st, N);
-      hd[j] = desc_for<T>(I, in, out, sig, mu, H);
+      T* f = fl + (size_t)j * fs;
+      hd[j] = desc_for<T>(I, in, out, f, f + 9 * N, f + 10 * N);
     }
     CK(c, cudaMemcpyAsync(dd, hd.data(), len * sizeof(InstDesc<T>), cudaMemcpyHostToDevice, c->stream));
     const long long blocks = (N + kStepBlock - 1) / kStepBlock;
@@ -1022,8 +1040,10 @@ int adjoint_impl(lbcad_ctx* c, int64_t nsteps, int k, double* dzeta, double* dq0
     }
     // reverse steps
     for (int j = len - 1; j >= 0; --j) {
-      e = Launch<T, SHIFT>::fields(dd + j, 1, blocks, kStepBlock, c->stream);
-      if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("adjoint fields: ") + cudaGetErrorString(e));
+      if (j == len - 1) {  // the segment's last state was not stepped from in the replay
+        e = Launch<T, SHIFT>::fields(dd + j, 1, blocks, kStepBlock, c->stream);
+        if (e != cudaSuccess) return fail(c, LBCAD_E_CUDA, std::string("adjoint fields: ") + cudaGetErrorString(e));
+      }
       AdjDescHost<T> h;
       h.I = hd[j];
       h.lg = lcur.g; h.lq = lcur.q; h.lp = lcur.p; h.lu = lcur.u;
