@@ -174,6 +174,37 @@ def test_short_horizon_finite_differences():
     assert abs(ad - fdv) <= 1e-4 * abs(fdv), (ad, fdv)
 
 
+def test_repeated_adjoint_calls_reuse_buffers_exactly():
+    """lbcad_adjoint keeps its buffers for later calls: a call after calls of other sizes
+    (fewer and more checkpoints, a longer segment) gives the result of a fresh context at the
+    same state, and the context's device memory stops growing.  (FP64, 1e-10 relative: the
+    two contexts take the starting centroid from different passes of the a6 sums, the fused
+    one and the separate one, which add in different orders.)"""
+    import torch
+    prm = [L.default_params(SHAPE, precision=L.FP64, **KW)]
+    a = L.Simulation([SHAPE], prm, seed=SEED)
+    a.adjoint(9, 3)
+    a.adjoint(5, 5)
+    free0, _ = torch.cuda.mem_get_info()
+    ra = a.adjoint(8, 3)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    fa = a.adjoint_fields(L.FIELD_Q | L.FIELD_PSI)
+    b = L.Simulation([SHAPE], prm, seed=SEED)
+    b.step(14)
+    rb = b.adjoint(8, 3)
+    fb = b.adjoint_fields(L.FIELD_Q | L.FIELD_PSI)
+    assert a.step_count == b.step_count == 22
+    for x, y in zip(ra[:3], rb[:3]):
+        assert abs(x - y) <= 1e-10 * abs(y), (x, y)
+    assert np.abs(ra[3] - rb[3]).max() <= 1e-10 * np.abs(rb[3]).max()
+    for k in fa:
+        assert np.abs(fa[k] - fb[k]).max() <= 1e-10 * np.abs(fb[k]).max(), k
+    assert free1 == free0, (free0, free1)
+    a.close()
+    b.close()
+
+
 def test_fp32_adjoint_close_to_fp64(adj64):
     _, dz64, dq64, dQ64, _ = adj64
     _, dz32, dq32, dQ32, _ = _adjoint(L.FP32)
