@@ -316,8 +316,8 @@ int lbcad_sync(lbcad_ctx* c);
  * other; serialise them.  The array keeps the last call's contents; nothing needs to
  * start at zero because each call writes every scratch value before reading it.
  * Set-up: the first call on a device looks up the device addresses of the static arrays
- * with cudaGetSymbolAddress and keeps them for that device; make that first call before any
- * stream capture.  The addresses belong to the CUDA runtime's context of the device (its
+ * with cudaGetSymbolAddress (a host-side runtime query, which may also load the library's
+ * kernels) and keeps them for that device.  The addresses belong to the CUDA runtime's context of the device (its
  * primary context): call this only while that context is current, not under a context the
  * caller created with the driver API. */
 #define LBCAD_NOALLOC_SCRATCH_BYTES (16u << 20)

@@ -236,6 +236,13 @@ void init_host(const lbcad_grid& g, const lbcad_params& p, uint64_t seed, int in
       }
 }
 
+// v into p[0 .. n) (the rest populations of the initial state, on the device).
+template <typename T>
+__global__ void k_fill(T* __restrict__ p, long long n, T v) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    p[k] = v;
+}
+
 template <typename T>
 int upload_init(lbcad_ctx* c, Inst& I, uint64_t seed, int idx) {
   std::vector<double> q5, psi;
@@ -244,15 +251,19 @@ int upload_init(lbcad_ctx* c, Inst& I, uint64_t seed, int idx) {
   std::vector<T> tq(5 * N), tp(N);
   for (long long k = 0; k < 5 * N; ++k) tq[k] = (T)q5[k];
   for (long long k = 0; k < N; ++k) tp[k] = (T)psi[k];
+  // populations at rest: w_i rho0, which the shifted FP32 storage holds as 0
   const bool shifted = (c->prec == LBCAD_FP32);
   const int q = c->q();
-  std::vector<T> tg(q * N);
-  for (int i = 0; i < q; ++i) {
-    const double w = (q == 15) ? lat15_w(i) : lat_w(i);
-    const T v = shifted ? T(0) : (T)(w * I.p.rho0);
-    for (long long s = 0; s < N; ++s) tg[i * N + s] = v;
+  T* g0 = (T*)I.gb[0];
+  if (shifted) {
+    CK(c, cudaMemsetAsync(g0, 0, q * N * sizeof(T), c->stream));
+  } else {
+    for (int i = 0; i < q; ++i) {
+      const double w = (q == 15) ? lat15_w(i) : lat_w(i);
+      k_fill<T><<<1024, 256, 0, c->stream>>>(g0 + i * N, N, (T)(w * I.p.rho0));
+      CK(c, cudaGetLastError());
+    }
   }
-  CK(c, cudaMemcpyAsync(I.gb[0], tg.data(), q * N * sizeof(T), cudaMemcpyHostToDevice, c->stream));
   CK(c, cudaMemcpyAsync(I.qb[0], tq.data(), 5 * N * sizeof(T), cudaMemcpyHostToDevice, c->stream));
   CK(c, cudaMemcpyAsync(I.pb[0], tp.data(), N * sizeof(T), cudaMemcpyHostToDevice, c->stream));
   CK(c, cudaMemsetAsync(I.ub[0], 0, 3 * N * sizeof(T), c->stream));

@@ -14,6 +14,10 @@ Workloads:
   L2), and windows of both runs against the oracle.
 - 64 droplets in boxes with edges from {48, 64, 80, 96}, FP32, one persistent launch per step
   replayed from a CUDA graph, autotuned tiles: windows of every instance against the oracle.
+- A 512 x 512 x 456 box (119.5 M sites): the population array holds 19 n > 2^31 elements, so
+  every population's offset past the first 113 M sites exceeds 32 bits.  One step in FP32 (the
+  pipelined kernel the bench times) and in FP64, windows against the oracle, and the fused
+  FP64 sum of psi against the FP64 sum of the stored state.
 """
 import numpy as np
 import pytest
@@ -218,3 +222,76 @@ def test_batch_of_64_uneven_droplets_windows_against_oracle(lib_built):
         before[i] = None
     print("64 uneven droplets, worst window rel L2 after 2 graph-replayed steps:", worst)
     sim.close()
+
+
+# ---------------------------------------------------------------- beyond 2^31 elements
+BIG = (512, 512, 456)
+
+
+def _state_windows(sim, shape, origins, W, shifted, rho0):
+    """Windows of the raw state (lbcad_get_state into device memory), as get_fields would give
+    them: pre-collision populations f_i(x) = stored_i(x - c_i) (+ w_i rho0 when shifted), u, Q,
+    psi.  Also the largest magnitude of every field over the whole instance (FP32 scales)."""
+    import torch
+    nx, ny, nz = shape
+    raw = torch.empty(sim.state_bytes(0), dtype=torch.uint8, device="cuda:0")
+    sim.get_state(0, raw)
+    dt = torch.float32 if sim.precision == L.FP32 else torch.float64
+    v = raw.view(dt).view(28, nz, ny, nx)
+    def amax(t):  # largest magnitude without a copy of the field
+        return max(float(t.max()), -float(t.min()))
+    scale = {"g": amax(v[:19]), "q": amax(v[19:24]), "psi": amax(v[24]), "u": amax(v[25:28])}
+    psi_sum = float(v[24].double().sum())
+    c, w = L.lattice()
+    out = []
+    for o in origins:
+        ix = torch.tensor((o[0] - 1 + np.arange(W + 2)) % nx, device="cuda:0")
+        iy = torch.tensor((o[1] - 1 + np.arange(W + 2)) % ny, device="cuda:0")
+        iz = torch.tensor((o[2] - 1 + np.arange(W + 2)) % nz, device="cuda:0")
+        pad = v.index_select(1, iz).index_select(2, iy).index_select(3, ix).double().cpu().numpy()
+        f = np.empty((19, W, W, W))
+        for i in range(19):
+            cx, cy, cz = c[i]
+            f[i] = pad[i, 1 - cz:W + 1 - cz, 1 - cy:W + 1 - cy, 1 - cx:W + 1 - cx]
+            if shifted:
+                f[i] += w[i] * rho0
+        inner = pad[:, 1:W + 1, 1:W + 1, 1:W + 1]
+        out.append({"g": f, "q": inner[19:24].copy(), "psi": inner[24].copy(), "u": inner[25:28].copy()})
+    del v, raw
+    torch.cuda.empty_cache()
+    return out, scale, psi_sum
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", [L.FP32, L.FP64], ids=["fp32", "fp64"])
+def test_step_beyond_2e31_population_elements(lib_built, prec):
+    import torch
+    nx, ny, nz = BIG
+    R, W = 64.0, 24
+    assert 19 * nx * ny * nz > 2 ** 31
+    kw = dict(R=R, p0=48.0)
+    sim = L.Simulation([BIG], [L.default_params(BIG, precision=prec, **kw)], seed=1)
+    if prec == L.FP32:
+        sim.set_tiles(3)  # the pipelined schedule of the benchmarked step
+    shifted = prec == L.FP32
+    # windows on the droplet interface (mid-box) and across the periodic corner (the last planes,
+    # where the offsets of the high populations are largest)
+    origins = _windows_of(BIG, R)
+    before, _, _ = _state_windows(sim, BIG, origins, W, shifted, 1.0)
+    sim.step(1)
+    after, scale, psi_sum = _state_windows(sim, BIG, origins, W, shifted, 1.0)
+    obs = sim.observables(0)
+    sim.close()
+    torch.cuda.empty_cache()
+    h = REACH
+    perm = _perm()
+    for b, a in zip(before, after):
+        ref = _oracle_window(b, W, 1, perm, **kw)
+        for k in ref:
+            e = float(np.abs(_interior(a[k], h) - _interior(ref[k], h)).max())
+            if prec == L.FP64:
+                assert e <= 1e-12, (k, e)
+            else:
+                assert e <= 1e-5 * scale[k], (k, e, scale[k])
+    # the fused sum of psi of the new state against the FP64 sum of its stored values
+    assert abs(obs[1] - psi_sum) <= 1e-12 * nx * ny * nz, (obs[1], psi_sum)
