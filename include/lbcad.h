@@ -187,7 +187,7 @@ int lbcad_set_path(lbcad_ctx* c, int32_t path);
  * speed), in three rounds that interleave the candidates; a candidate's time is its best
  * round.  Writes the chosen index to *chosen and, if ms_per_cfg is given, the measured
  * milliseconds per launch of up to ncfg candidates (-1 for a shape that does not fit).
- * Candidates: 0 = 32x8 tiles (default), 1 = 32x16, 2 = 64x8, 3 and 4 = 32x8 software-pipelined
+ * Candidates: 0 = 32x8 tiles (the FP64 default), 1 = 32x16, 2 = 64x8, 3 (the FP32 default) and 4 = 32x8 software-pipelined
  * (sigma of plane k+1 on 8 or 6 warps while the other 8 or 10 warps output plane k-1, in
  * one phase), 5 and 6 = 32x6 software-pipelined (9 or 10 sigma warps, one round per
  * plane); 1-6 are FP32 only.  With LBCAD_D3Q15 or LBCAD_LB_STRESS_EQ only 0 and 3 are

@@ -386,9 +386,10 @@ int create_impl(int n, const lbcad_grid* grids, const lbcad_params* params, uint
   c->obs_out = (double*)dev_alloc(c, 12 * sizeof(double));
   if (!c->obs_partial || !c->obs_out) return bail(LBCAD_E_OOM, "device allocation failed");
   if (upload_descs(c) != LBCAD_OK) return bail(LBCAD_E_CUDA, "");
-  const int cfg0 = !c->sync_split() ? 0
-                   : (c->prec == LBCAD_FP64 ? LaunchFused<double, false>::sync_config()
-                                            : LaunchFused<float, true>::sync_config());
+  // default tile shape: the pipelined 32x8 schedule in FP32 (the fastest candidate from 16^3 to
+  // 128^3; the one sync coupling and Heun run on), 32x8 in FP64 (the only one)
+  const int cfg0 = c->prec == LBCAD_FP64 ? LaunchFused<double, false>::sync_config()
+                                         : LaunchFused<float, true>::sync_config();
   if ((code = prepare_fused(c, cfg0)) != LBCAD_OK) return bail(code, "");
   if (c->staged_only() || c->sync_split()) {
     if ((code = ensure_scratch(c)) != LBCAD_OK) return bail(code, "");
