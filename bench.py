@@ -342,6 +342,7 @@ def main():
                     help="skip the sync / Heun, LB-variant and bulk legs")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg (64^3, 500 steps)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-droplet leg")
+    ap.add_argument("--no-large", action="store_true", help="skip the 256^3 droplet leg")
     ap.add_argument("--min-timed-s", type=float, default=1.0,
                     help="repeat the K-step timed region until this much device time has passed")
     ap.add_argument("--workload", default="droplet", choices=["droplet", "batch64"],
@@ -489,6 +490,24 @@ def main():
                 "workload": "bulk active nematic %d^3, psi = 1, zeta = 0.008 (spontaneous-flow regime)" % n}
         sb.close()
 
+    # the larger droplet workload: 256^3, R = 64, pitch 48, FP32 with the fused sums (the step of the
+    # 128^3 line at 8x the sites)
+    large = None
+    if not args.no_large and world == 1:
+        nl = 256
+        sl = L.Simulation([(nl, nl, nl)], [L.default_params((nl, nl, nl), R=64.0, p0=48.0, precision=L.FP32,
+                                                            zeta=0.005)], seed=1 + rank, device=local)
+        sl.set_tiles(tile_cfg)
+        sl.step(3)
+        msl = time_steps(sl, torch, 50)
+        ach = BYTES_PER_SITE["fp32"] * nl ** 3 / (msl * 1e-3) / 1e9
+        pk, _ = measured_peaks()
+        large = {"mlups": nl ** 3 / (msl * 1e-3) / 1e6, "ms_per_step": msl, "achieved_gbs": ach,
+                 "frac_of_hbm_roofline": ach / pk if pk else None,
+                 "workload": "droplet 256^3, R = 64, pitch 48, zeta = 0.005, FP32, a6 sums fused, %s" %
+                             TILE_NAMES[tile_cfg]}
+        sl.close()
+
     # adjoint of J = |centroid drift|^2 / 2 over 500 steps of a 64^3 droplet (R = 16, pitch 16),
     # checkpoints every 50 steps: wall time of the whole gradient against the forward run alone
     adjoint = None
@@ -595,7 +614,7 @@ def main():
                 "tiles": {"chosen": TILE_NAMES[tile_cfg], "ms_per_cfg": dict(zip(TILE_NAMES, tile_ms))},
                 "timing": {"regions": len(region_ms), "steps_per_region": K, "median_ms_per_step": ms,
                            "min_ms_per_step": min(region_ms), "max_ms_per_step": max(region_ms)},
-                "gpu_launches": K, "clocks": csum, "batch64": batch, "step_without_sums": without_sums, "fp64_gpu": fp64, "integrators_fp32": staged, "lb_variants_fp32": variants, "bulk_fp32": bulk, "adjoint_fp32": adjoint,
+                "gpu_launches": K, "clocks": csum, "batch64": batch, "step_without_sums": without_sums, "fp64_gpu": fp64, "integrators_fp32": staged, "lb_variants_fp32": variants, "bulk_fp32": bulk, "droplet_256_fp32": large, "adjoint_fp32": adjoint,
                 "speedup_fp32_vs_fp64": (value / world / fp64["mlups"]) if fp64 else None,
                 "observables_finite": finite}
         print(json.dumps(line))
