@@ -12,12 +12,16 @@
 //      Q/psi plane z+3 and the u plane z+2 for the next iteration;
 //   2. output phase: F = div sigma, lap mu, grad u, upwind Q and psi, pull of the 19
 //      populations from global memory, BGK + Guo collision; store g, Q, psi, u.
-// Every global element of the state is read once per step from HBM and written once
-// (the design floor of 224 B per site in FP32); the halo re-reads of Q, psi and u hit L2.
+// Every global element of the state is read and written once per step by design (224 B per
+// site in FP32); the halo re-reads of Q, psi and u and the x-shifted pulls come on top, as far
+// as L2 does not hold them (tiles that neighbour in x run at different z).
 //
 // The grid is persistent: the flattened space of (tile column, z plane) work is split
 // evenly across the blocks, so load balance does not depend on the box shape and one
 // launch covers every instance of a batch.
+//
+// The end of the file holds the order-parameter half of the sync-coupled and Heun steps, as
+// tiled z-marching kernels on the same tiles and work split.
 #pragma once
 
 #include <type_traits>
