@@ -43,7 +43,7 @@ extern "C" {
 #define LBCAD_E_INVALID_ARG (-1) /* bad pointer, size, parameter or instance index       */
 #define LBCAD_E_OOM (-2)         /* device allocation failed                             */
 #define LBCAD_E_CUDA (-3)        /* a CUDA runtime call failed (message has the reason)  */
-#define LBCAD_E_TIMEOUT (-4)     /* a bounded device wait gave up                        */
+#define LBCAD_E_TIMEOUT (-4)     /* reserved: no kernel of this library waits on another */
 #define LBCAD_E_NAN (-5)         /* a non-finite value was found in a reduction          */
 #define LBCAD_E_UNSUPPORTED (-6) /* option not available on this path                    */
 
