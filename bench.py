@@ -51,25 +51,26 @@ def measured_peaks():
 # the sources that define the step kernels: an ncu figure is current only while these are
 # unchanged since the capture (the profile records their fingerprint)
 STEP_SOURCES = ["lbcad_fused.cuh", "lbcad_kernels.cuh", "lbcad_internal.h", "lbcad_f32.cu"]
+STEP_SOURCES_FP64 = ["lbcad_fused.cuh", "lbcad_kernels.cuh", "lbcad_internal.h", "lbcad_f64.cu"]
 
 
-def kernel_source_sha():
+def kernel_source_sha(sources=None):
     import hashlib
     h = hashlib.sha256()
-    for f in STEP_SOURCES:
+    for f in sources or STEP_SOURCES:
         with open(os.path.join(ROOT, "paper_2011_00287_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profile_is_current(name="lbcad_step_fp32_128cube.md"):
+def profile_is_current(name="lbcad_step_fp32_128cube.md", sources=None):
     """True when the committed ncu summary was taken of the kernels as they are now."""
     p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return False
     for line in open(p):
         if line.startswith("kernel_source_sha:"):
-            return line.split(":", 1)[1].strip().split()[0] == kernel_source_sha()
+            return line.split(":", 1)[1].strip().split()[0] == kernel_source_sha(sources)
     return False
 
 
@@ -423,7 +424,8 @@ def main():
         fp64 = {"mlups": N / (ms64 * 1e-3) / 1e6, "ms_per_step": ms64, "steps": args.fp64_steps}
         # bound by the FP64 pipe: flops per site from the committed ncu counters, peak the FP64
         # FMA throughput measured on this GPU by the FMA-chain probe
-        fl = committed_profile_value("fp64_flops_per_site", "lbcad_step_fp64_128cube.md")
+        fp64_current = profile_is_current("lbcad_step_fp64_128cube.md", STEP_SOURCES_FP64)
+        fl = committed_profile_value("fp64_flops_per_site", "lbcad_step_fp64_128cube.md") if fp64_current else None
         p64, p32 = measured_alu_peaks(local)
         fp64["measured_peak_tflops"] = {"fp64": p64, "fp32": p32,
                                         "how": "FMA-chain probe (csrc/peaks.cu), best of 5 launches on every SM"}
