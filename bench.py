@@ -245,6 +245,31 @@ def cpu_oracle_rate(n, budget_s=12.0, max_steps=None, omp=False):
     return n ** 3 * steps / el, steps, el
 
 
+def config0_leg(L, torch, local):
+    """The small workload in full: FP64 droplet 32^3, R = 8, pitch 16, 200 steps with the a6 sums of
+    every step, on the oracle (one thread, and all cores) and on the GPU's FP64 path."""
+    from oracle import oracle as O
+    n, K = 32, 200
+    out = {"workload": "droplet 32^3, R = 8, pitch 16, zeta = 0.005, FP64, %d steps, a6 sums every step" % K}
+    for omp in (False, True):
+        O.build(omp=omp)
+        s = O.State((n, n, n), O.default_params((n, n, n), R=8.0, p0=16.0, zeta=0.005), seed=1, omp=omp)
+        t0 = time.perf_counter()
+        for _ in range(K):
+            s.step(1)
+            s.observables()
+        el = time.perf_counter() - t0
+        out["oracle_all_cores" if omp else "oracle_single_thread"] = {
+            "seconds": el, "mlups": n ** 3 * K / el / 1e6, "threads": O.num_threads(True) if omp else 1}
+    sim = L.Simulation([(n, n, n)], [L.default_params((n, n, n), R=8.0, p0=16.0, precision=L.FP64, zeta=0.005)],
+                       seed=1, device=local)
+    sim.step(3)
+    ms = time_steps(sim, torch, K)
+    out["gpu_fp64"] = {"seconds": ms * K / 1e3, "mlups": n ** 3 / (ms * 1e-3) / 1e6}
+    sim.close()
+    return out
+
+
 def run_reference(args):
     """--impl reference: the FP64 CPU oracle, as it stands, on all of this host's cores (its
     OpenMP build: the same per-site arithmetic, stage loops split over z)."""
@@ -601,7 +626,8 @@ def main():
                "nproc": os.cpu_count(), "cpu_model": cpu_model(),
                "single_thread": {"value": rate / 1e6, "unit": "MLUPS", "cores": 1,
                                  "sample": "FP64 oracle, single thread, %d step(s) of the same workload (%.1f s)" % (
-                                     steps, el)}}
+                                     steps, el)},
+               "small_workload_in_full": config0_leg(L, torch, local)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": W,
