@@ -524,6 +524,9 @@ __device__ __forceinline__ void op_update(const Coef<T>& c, T lapmu, const T Wg[
   const T cq = -T(2) * c.xi * trQW;
   const T cdiag = -(T(2) * c.xi / T(9)) * trD;
   auto P = [&](int i, int j) { return M[i][0] * Qt[0][j] + M[i][1] * Qt[1][j] + M[i][2] * Qt[2][j]; };
+  // The increments are summed first and added to Q and psi once: every addition at the
+  // magnitude of the field rounds to its storage resolution, and three of them per step
+  // (Q - adv, + S, + Gamma H) added half again to the error that FP32 storage alone causes.
   const int I5[5] = {0, 0, 0, 1, 1};
   const int J5[5] = {0, 1, 2, 1, 2};
 #pragma unroll
@@ -531,11 +534,11 @@ __device__ __forceinline__ void op_update(const Coef<T>& c, T lapmu, const T Wg[
     const int i = I5[k], j = J5[k];
     T S = (i == j ? T(2) * P(i, i) : P(i, j) + P(j, i)) + cq * Qt[i][j];
     if (i == j) S += cdiag;
-    if (RHS) qn[k] = -adv[k] + S + c.gammaQ * Hs[k];
-    else qn[k] = q0[k] - adv[k] + S + c.gammaQ * Hs[k];
+    const T inc = fma(c.gammaQ, Hs[k], S - adv[k]);
+    qn[k] = RHS ? inc : q0[k] + inc;
   }
-  if (RHS) pn = -divJ + c.M * lapmu;
-  else pn = p0 - divJ + c.M * lapmu;
+  const T pinc = fma(c.M, lapmu, -divJ);
+  pn = RHS ? pinc : p0 + pinc;
 }
 
 // a5 at one site: moments of the pulled populations g and the force F, then BGK + Guo

@@ -161,8 +161,9 @@ def test_256cube_fp32_against_fp64_first_100_steps(lib_built):
     print("256^3 after 100 steps, FP32 vs FP64 rel L2:", errs, "rms |u| %.2e" % np.sqrt((f64["u"] ** 2).sum(0).mean()))
     # What the FP32 storage alone costs: the FP64 step with Q and psi rounded to FP32 after every
     # step (on the device), against the plain FP64 run.  Rounding u and the populations as well
-    # adds nothing measurable (32^3 and 128^3), so Q and psi carry it.  The FP32 path may add as
-    # much again through its arithmetic (measured ratios of its error to this one: 1.44-1.51).
+    # adds nothing measurable (32^3 and 128^3), so Q and psi carry it.  The FP32 step adds little
+    # to it through its arithmetic (measured: 3-4% for the populations and u), since it adds each
+    # site's order-parameter increments to Q and psi in one rounding.
     import torch
     sr = L.Simulation([shape], [L.default_params(shape, precision=L.FP64, **kw)], seed=1)
     N = 256 ** 3
@@ -181,11 +182,12 @@ def test_256cube_fp32_against_fp64_first_100_steps(lib_built):
     for k in ("q", "psi", "u"):
         store[k] = _rel_l2(fr[k], f64[k])
     print("256^3 after 100 steps, FP64 with FP32-rounded Q and psi vs FP64 rel L2:", store)
-    # Q and psi within 1e-5.  The populations (shifted) and the velocity within 1e-5 or twice the
-    # storage-only error, whichever is larger.
+    # every field within 1e-5 (measured: populations 7.9e-6, Q 1.3e-7, psi 4.4e-8, u 9.3e-6), and
+    # the populations and u within 1.25 times the storage-only error
     for k, e in errs.items():
-        tol = 1e-5 if k in ("q", "psi") else max(1e-5, 2.0 * store[k])
-        assert e <= tol, (k, errs, store)
+        assert e <= 1e-5, (k, errs, store)
+        if k in ("g", "u"):
+            assert e <= 1.25 * store[k], (k, errs, store)
     del f32, f64, fr
     # windows of both runs, two steps by the oracle
     W, steps = 24, 2
