@@ -283,12 +283,11 @@ def test_500_step_adjoint_on_16cube_matches_oracle(name, kw, tol_dir):
 
 def test_500_step_adjoint_on_64cube_fp32_against_fp64():
     """The differentiation workload itself: 64^3, R = 16, pitch 16, zeta = 0.005, 500 steps,
-    checkpoints every 50.  FP32 against FP64 on the GPU (measured: dJ/dzeta 0.8% and 4.7% for two
-    FP32 variants of the step that group the collision's operations differently, dJ/dQ0 0.7% in
-    norm with cosine 0.99998, dJ/dq0 27%).  dJ/dq0 is the small one: q0 enters only through H and
-    sigma with the initial helix fixed, and its dimensionless size q0 dJ/dq0 is a third of
-    zeta dJ/dzeta, so the FP32 trajectory's difference weighs more in it; it is held to the same
-    sign and 50%, the others to 1e-1.  (Finite differences are no reference at this horizon:
+    checkpoints every 50.  FP32 against FP64 on the GPU, each within 1e-1 (measured: dJ/dzeta 3.0%,
+    dJ/dq0 4.4%, dJ/dQ0 0.9% in norm with cosine 0.99996; before the order-parameter update added
+    its increments in one rounding, dJ/dq0 differed by 27%: q0 enters only through H and sigma with
+    the initial helix fixed, and its dimensionless size q0 dJ/dq0 is a third of zeta dJ/dzeta, so
+    the FP32 trajectory's difference weighs most in it).  (Finite differences are no reference at this horizon:
     central differences of the FP64 forward in zeta give 9.8e-8, 1.5e-8 and -4.6e-10 for steps
     of 1e-4, 1e-3 and 1e-2 relative, against an adjoint of 1.09e-8, because J has upwind kinks
     closer together than any of these steps.)"""
@@ -303,4 +302,4 @@ def test_500_step_adjoint_on_64cube_fp32_against_fp64():
     assert np.isfinite([J32, dz32, dq32]).all() and np.isfinite(dQ32).all()
     assert abs(dz32 - dz64) <= 1e-1 * abs(dz64), (dz32, dz64)
     assert np.linalg.norm(dQ32 - dQ64) <= 1e-1 * np.linalg.norm(dQ64)
-    assert np.sign(dq32) == np.sign(dq64) and abs(dq32 - dq64) <= 0.5 * abs(dq64), (dq32, dq64)
+    assert abs(dq32 - dq64) <= 1e-1 * abs(dq64), (dq32, dq64)
