@@ -1100,7 +1100,7 @@ int lbcad_adjoint(lbcad_ctx* c, int64_t nsteps, int32_t ckpt_every, double* dJ_d
   const int k = (int)std::min<int64_t>(ckpt_every, nsteps);
   const int r = c->prec == LBCAD_FP64 ? adjoint_impl<double, false>(c, nsteps, k, dJ_dzeta, dJ_dq0, dJ_dQ0, J)
                                       : adjoint_impl<float, true>(c, nsteps, k, dJ_dzeta, dJ_dq0, dJ_dQ0, J);
-  c->obs_valid = false;  // the replays reuse the fused step
+  c->obs_valid = false;  // lbcad_observables forms the sums of the final state again (separate pass)
   return r;
 }
 
