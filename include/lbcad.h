@@ -172,9 +172,9 @@ int lbcad_step(lbcad_ctx* c, int64_t n);
  * adjoint return LBCAD_E_UNSUPPORTED there); other contexts may select it as a cross-check
  * (same per-site arithmetic).  Scratch: 15 values per site, 27 with LBCAD_HEUN.
  * LBCAD_SYNC or LBCAD_HEUN on the fused path (their default): the fused kernel on one fixed
- * tile shape does the LB half (u of this step; H and mu into the scratch), then the staged
- * path's order-parameter kernels (sync: the update; Heun: predictor, fields at the predicted
- * state, corrector); tile shapes, autotune, the two-kernel path and the adjoint return
+ * tile shape does the LB half (u of this step; H and mu into the scratch), then tiled
+ * z-marching order-parameter kernels on the same tiles (sync: the update; Heun: predictor,
+ * fields at the predicted state, corrector); tile shapes, autotune, the two-kernel path and the adjoint return
  * LBCAD_E_UNSUPPORTED there.  LBCAD_D3Q15 and LBCAD_LB_STRESS_EQ run on the fused path (tile
  * shapes 0 and 3 only) and the staged path; the two-kernel path and the adjoint return
  * LBCAD_E_UNSUPPORTED for them. */

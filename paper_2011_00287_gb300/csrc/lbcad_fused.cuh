@@ -962,7 +962,7 @@ __global__ void __launch_bounds__(512, 1)
 // The order-parameter half of a sync-coupled or Heun step (after LaunchFused::step_lb), as
 // z-marching kernels on the tiles and work split of the fused step (32 x 8 columns, persistent
 // blocks): rings of planes with a halo of 1 in shared memory, filled by cp.async one plane
-// ahead, one barrier per plane, and the per-site functions of the staged path on them.
+// ahead, one barrier per plane, and the shared per-site functions on them.
 //   k_op_tiled<STAGE>: STAGE 0 the update Q + R(Q) (Euler, sync), 1 the Heun predictor
 //     (rq = R(Q), qp = Q + rq), 2 the Heun corrector Q + (rq + R(qp))/2, R from gather_op and
 //     op_update with u of this step (sync) or of the previous one, H and mu of the scratch;

@@ -1,7 +1,9 @@
 // lbcad_kernels.cuh -- CUDA kernels of the hybrid LB step, templated on the compute
 // type T (float or double) and on SHIFT (populations stored as f_i - w_i rho0).
 //
-// One step (Sec. 3 of Carenza, Gonnella & Negro) runs as two per-site kernels:
+// The per-site device functions every path shares (stencils, local fields, order-parameter
+// update, collision), the a6 pass, and the per-site kernels of the two cross-check paths.
+// On the two-kernel path one step (Sec. 3 of Carenza, Gonnella & Negro) runs as:
 //   k_fields : isotropic D3Q19 stencils of Q and psi -> molecular field H (Eq. 2, 5),
 //              chemical potential mu (Eq. 1, 5) and total stress sigma (Eq. 3, 4)
 //              into scratch;
